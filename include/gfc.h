@@ -1,0 +1,148 @@
+/*
+ * gfc.h -- C ABI of the GB300 Green Function Convolution (GFC) Poisson solver.
+ *
+ * GFC (Beaini et al., arXiv 1902.00176) recovers an image from a gradient
+ * field (possibly non-conservative) or from a Laplacian by one convolution
+ * with a numerical Green's function, done in the Fourier domain:
+ *
+ *   L      = div E                               (Eq. 3)
+ *   G      = F(delta) / F(K_laplace)             (Eq. 19-22, Algorithm A)
+ *   I_c    = Re(F^-1(F(L) o G)) + c              (Eq. 23, Algorithm B)
+ *
+ * Conventions used by every entry point below:
+ *  - Fields are contiguous [batch, C, H, W] arrays (row-major, W fastest) in
+ *    the plan's storage dtype; each (batch, channel) slice is one independent
+ *    solve. Arithmetic is FP32 for every storage dtype.
+ *  - gx is the forward difference along W, gy along H:
+ *      gx[i,j] ~ I[i,j+1] - I[i,j],  gy[i,j] ~ I[i+1,j] - I[i,j].
+ *    The solver accepts any values (non-conservative edits are the point).
+ *  - The field is zero-extended into an M x N padded domain (Algorithm A;
+ *    pad p, default 4) with the image block at offset (p, p). The DFT makes
+ *    that domain a torus; gradients are zero in the pad (zero flux, Sec. 2.2).
+ *  - L[p+i, p+j] = gx[i,j] - gx[i,j-1] + gy[i,j] - gy[i-1,j], out-of-range
+ *    terms are 0 (so L is supported on (H+1) x (W+1) cells).
+ *  - Algorithm A's kernel sign is used (positive Laplacian, -4 centre; Eq. 15
+ *    prints the negated kernel). G[0,0] (0/0 in Algorithm A) is set to 0.
+ *  - The constant of Eq. 23 is Algorithm B's: the solution at the pad's corner
+ *    u[0,0] is subtracted, then the image block is cropped:
+ *      out[i,j] = u[p+i, p+j] - u[0,0].
+ *  - Size policy GFC_SIZE_SMOOTH (default): M, N are the smallest even 7-smooth
+ *    integers >= H + 2p and >= W + 2p; the image stays at (p, p) and the extra
+ *    zero rows/columns go to the bottom/right. This is the same least-squares
+ *    problem (Sec. 2.2) on a slightly larger torus.
+ *
+ * Memory: every tensor pointer is caller-owned DEVICE memory on the plan's
+ * device, 16-byte aligned, not aliasing any other argument of the same call.
+ * The plan owns its tables and its scratch. All solve calls are asynchronous
+ * on the plan's stream; a device-side failure is reported by a later call or
+ * by gfc_plan_sync. A plan is not thread-safe: one plan serves one stream at
+ * a time. Every function returns a gfc_status; on failure gfc_last_error()
+ * returns a thread-local message.
+ */
+#ifndef GFC_H
+#define GFC_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gfc_plan gfc_plan;
+
+typedef enum { GFC_F32 = 0, GFC_F16 = 1, GFC_BF16 = 2 } gfc_dtype;
+
+typedef enum {
+  GFC_OK = 0,
+  GFC_ERR_INVALID_ARG = 1, /* bad size, null or misaligned pointer, bad enum */
+  GFC_ERR_UNSUPPORTED = 2, /* size or feature outside what this build handles */
+  GFC_ERR_ALLOC = 3,       /* device or host allocation failed */
+  GFC_ERR_CUDA = 4,        /* a CUDA runtime call or a launch failed */
+  GFC_ERR_TIMEOUT = 5      /* a bounded device-side wait ran out */
+} gfc_status;
+
+typedef enum { GFC_SIZE_SMOOTH = 0 } gfc_size_policy;
+
+typedef struct {
+  int H, W;          /* image height and width, each >= 2 */
+  int C, batch;      /* channels and batch size, each >= 1 */
+  gfc_dtype dtype;   /* storage dtype of inputs and outputs */
+  int pad;           /* p >= 1; 0 selects Algorithm A's pad of 4 */
+  int size_policy;   /* gfc_size_policy */
+  int chunk;         /* fields per pipeline chunk; 0 lets the plan choose */
+  void* stream;      /* cudaStream_t to run on; NULL = the legacy default stream */
+} gfc_plan_opts;
+
+/* Padded-domain size for an H x W image (Algorithm A: size = image + 2 pad,
+ * rounded up by the size policy). Host-only, needs no GPU. pad <= 0 selects 4.
+ * Writes M, N; returns GFC_ERR_INVALID_ARG for H or W < 2 or null outputs,
+ * GFC_ERR_UNSUPPORTED when M or N would exceed the largest supported length. */
+gfc_status gfc_padded_size(int H, int W, int pad, int size_policy, int* M, int* N);
+
+/* Create a plan for batch x C fields of H x W in `dtype` on the current CUDA
+ * device (Algorithm A: the Green spectrum is built once per size, in FP64 on
+ * the GPU, and stored rounded to FP32; Sec. 3.1.3 keeps it out of the solve
+ * time). Synchronous. On success *plan owns device memory until gfc_destroy. */
+gfc_status gfc_plan_create(gfc_plan** plan, int H, int W, int C, int batch, gfc_dtype dtype);
+
+/* As gfc_plan_create, with the options above. */
+gfc_status gfc_plan_create_ex(gfc_plan** plan, const gfc_plan_opts* opts);
+
+/* Run later calls of this plan on `stream` (a cudaStream_t of the plan's device). */
+gfc_status gfc_plan_set_stream(gfc_plan* plan, void* stream);
+
+/* Report the plan's padded size M x N and pad p (any pointer may be NULL). */
+gfc_status gfc_plan_padded_size(const gfc_plan* plan, int* M, int* N, int* pad);
+
+/* Copy the plan's Green spectrum to host memory `host_out` as M x (N/2+1)
+ * FP32 values, row-major: G[k,l] = 1 / (M N lambda(k,l)) with
+ * lambda = 2cos(2 pi k/M) + 2cos(2 pi l/N) - 4 and G[0,0] = 0 (Eq. 22 with the
+ * 1/(MN) of the inverse transform folded in). Synchronous. */
+gfc_status gfc_plan_copy_green(const gfc_plan* plan, float* host_out);
+
+/* Solve every field from its gradient (Eq. 3 then Eq. 23 and Algorithm B).
+ * gx, gy: [batch, C, H, W] inputs; out: [batch, C, H, W] output, all in the
+ * plan's dtype. out may not alias gx or gy. Asynchronous. */
+gfc_status gfc_solve_from_gradient(gfc_plan* plan, const void* gx, const void* gy, void* out);
+
+/* Solve every field from a given Laplacian (Eq. 23, Algorithm B): lap is
+ * [batch, C, H, W], zero-extended into the padded domain ("padded_L"); its
+ * mean is projected out by G[0,0] = 0. out may not alias lap. Asynchronous. */
+gfc_status gfc_solve_from_laplacian(gfc_plan* plan, const void* lap, void* out);
+
+/* Adjoint (vector-Jacobian product) of gfc_solve_from_gradient, used to make
+ * GFC a network layer (Sec. 4). With y = solve(gx, gy) linear, returns
+ * grad_gx = dy/dgx^T grad_out and grad_gy likewise:
+ *   z = Crop^T(grad_out) - (sum grad_out) e_00,  w = Re(F^-1(F(z) o G)),
+ *   grad_gx[i,j] = w[p+i,p+j] - w[p+i,p+j+1],  grad_gy[i,j] = w[p+i,p+j] - w[p+i+1,p+j].
+ * All three arrays are [batch, C, H, W] in the plan's dtype, pairwise
+ * non-aliasing. Asynchronous. */
+gfc_status gfc_backward(gfc_plan* plan, const void* grad_out, void* grad_gx, void* grad_gy);
+
+/* Batched complex FFT with the library's own mixed-radix engine: `count`
+ * contiguous rows of n complex FP32 values (interleaved re, im) from `in` to
+ * `out` (which may be the same buffer). dir = -1 forward
+ * X[k] = sum x[m] exp(-2 pi i k m / n), dir = +1 unnormalised inverse. n must
+ * be 7-smooth and at most 4096. Device pointers; runs on `stream`
+ * (cudaStream_t). Asynchronous. Exposed to test the transform on its own
+ * (Eq. 17's F). */
+gfc_status gfc_fft_c2c(int n, int count, int dir, const void* in, void* out, void* stream);
+
+/* Wait for the plan's stream and report any device-side error since the last
+ * sync (GFC_ERR_TIMEOUT for a bounded wait that ran out, GFC_ERR_CUDA otherwise). */
+gfc_status gfc_plan_sync(gfc_plan* plan);
+
+/* Free the plan and everything it owns. NULL is accepted. */
+gfc_status gfc_destroy(gfc_plan* plan);
+
+/* Thread-local text of the last failure in this thread ("" if none). */
+const char* gfc_last_error(void);
+
+/* Static name of a status code. */
+const char* gfc_status_string(gfc_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GFC_H */

@@ -1,0 +1,58 @@
+// gfc_internal.h -- plan object and host helpers shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "../../include/gfc.h"
+#include "fft_core.cuh"
+
+struct gfc_plan {
+  // problem
+  int H, W, C, batch, pad;
+  gfc_dtype dtype;
+  int M, N;   // padded (torus) size
+  int Nh;     // N/2 + 1 Hermitian columns
+  int ldS;    // row stride of the spectrum scratch, in complex elements
+  int chunk;  // fields per pipeline chunk
+  int device;
+  cudaStream_t stream;
+  // FFT schedules
+  gfc::FftPlan rowplan;  // length N
+  gfc::FftPlan colplan;  // length M
+  // device tables (owned)
+  float* G;       // [M][Nh] Green spectrum with 1/(MN) folded in
+  float2* twN;    // [N] exp(-2 pi i m / N)
+  float2* twM;    // [M] exp(-2 pi i m / M)
+  float2* spec;   // [chunk][M][ldS] complex spectrum scratch
+  float* partial; // [chunk][kMaxRowBlocks] per-block sums (adjoint)
+  int* dev_err;   // device error word
+};
+
+namespace gfc {
+
+constexpr int kMaxRowBlocks = 1024;
+
+// thread-local error text, set by fail()
+gfc_status fail(gfc_status s, const char* fmt, ...);
+gfc_status cuda_fail(cudaError_t e, const char* what);
+void clear_error();
+
+// mixed-radix schedule for a 7-smooth n (returns false if n is not 7-smooth or too long)
+bool make_fft_plan(int n, FftPlan* pl);
+bool is_7smooth(long n);
+
+// device table builders (FP64 on the GPU, rounded to FP32)
+cudaError_t build_twiddles(float2* tw, int n, cudaStream_t s);
+cudaError_t build_green(float* G, int M, int N, int Nh, cudaStream_t s);
+
+inline size_t dtype_size(gfc_dtype d) { return d == GFC_F32 ? 4 : 2; }
+
+}  // namespace gfc
+
+#define GFC_CUDA_TRY(expr)                                   \
+  do {                                                       \
+    cudaError_t e_ = (expr);                                 \
+    if (e_ != cudaSuccess) return gfc::cuda_fail(e_, #expr); \
+  } while (0)

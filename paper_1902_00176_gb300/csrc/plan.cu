@@ -1,0 +1,265 @@
+// plan.cu -- plan creation, size policy, FP64 table builders, status/error plumbing.
+//
+// Algorithm A of the paper builds the Green spectrum once per image size as
+// fft(dirac)/fft(laplace) with both kernels centred at [1,1]. The phases
+// cancel, so the spectrum is real: G[k,l] = 1/lambda(k,l) with
+// lambda = 2cos(2 pi k/M) + 2cos(2 pi l/N) - 4 = -4 (sin^2(pi k/M) + sin^2(pi l/N)).
+// The plan evaluates the sin^2 form in FP64 on the GPU (no cancellation near
+// DC), folds in the inverse transform's 1/(MN), stores FP32, and sets the DC
+// bin (0/0 in Algorithm A) to 0.
+#include <cuda_runtime.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "gfc_internal.h"
+
+namespace gfc {
+
+static thread_local char g_err[512] = "";
+
+void clear_error() { g_err[0] = '\0'; }
+
+gfc_status fail(gfc_status s, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return s;
+}
+
+gfc_status cuda_fail(cudaError_t e, const char* what) {
+  return fail(e == cudaErrorMemoryAllocation ? GFC_ERR_ALLOC : GFC_ERR_CUDA, "%s: %s (%s)", what,
+              cudaGetErrorString(e), cudaGetErrorName(e));
+}
+
+bool is_7smooth(long n) {
+  if (n < 1) return false;
+  for (long f : {2L, 3L, 5L, 7L})
+    while (n % f == 0) n /= f;
+  return n == 1;
+}
+
+// Stage order: the power of two as radix-8 stages plus one radix-4 or radix-2
+// stage, then 3s, 5s and 7s. Any order is a valid Stockham schedule.
+bool make_fft_plan(int n, FftPlan* pl) {
+  if (n < 1 || n > kMaxFftLen || !is_7smooth(n)) return false;
+  int m = n, e2 = 0;
+  while (m % 2 == 0) { m /= 2; ++e2; }
+  int ns = 0;
+  while (e2 >= 3) { pl->radix[ns++] = 8; e2 -= 3; }
+  if (e2 == 2) pl->radix[ns++] = 4;
+  if (e2 == 1) pl->radix[ns++] = 2;
+  for (int f : {3, 5, 7})
+    while (m % f == 0) {
+      if (ns >= kMaxStages) return false;
+      pl->radix[ns++] = f;
+      m /= f;
+    }
+  pl->n = n;
+  pl->nst = ns;
+  return true;
+}
+
+__global__ void k_build_twiddles(float2* tw, int n) {
+  for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < n; m += gridDim.x * blockDim.x) {
+    double s, c;
+    sincospi(2.0 * (double)m / (double)n, &s, &c);
+    tw[m] = make_float2((float)c, (float)(-s));
+  }
+}
+
+__global__ void k_build_green(float* G, int M, int N, int Nh) {
+  const long total = (long)M * Nh;
+  for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
+    const int k = (int)(idx / Nh), l = (int)(idx % Nh);
+    const double sk = sinpi((double)k / (double)M), sl = sinpi((double)l / (double)N);
+    const double lam = -4.0 * (sk * sk + sl * sl);
+    G[idx] = (k == 0 && l == 0) ? 0.0f : (float)(1.0 / (lam * (double)M * (double)N));
+  }
+}
+
+cudaError_t build_twiddles(float2* tw, int n, cudaStream_t s) {
+  k_build_twiddles<<<(n + 255) / 256, 256, 0, s>>>(tw, n);
+  return cudaGetLastError();
+}
+
+cudaError_t build_green(float* G, int M, int N, int Nh, cudaStream_t s) {
+  long total = (long)M * Nh;
+  int blocks = (int)((total + 255) / 256);
+  if (blocks > 4096) blocks = 4096;
+  k_build_green<<<blocks, 256, 0, s>>>(G, M, N, Nh);
+  return cudaGetLastError();
+}
+
+static int smooth_even_at_least(int x) {
+  int n = x + (x & 1);
+  while (!is_7smooth(n)) n += 2;
+  return n;
+}
+
+}  // namespace gfc
+
+using namespace gfc;
+
+static void destroy_plan(gfc_plan* p);
+
+extern "C" {
+
+const char* gfc_last_error(void) { return g_err; }
+
+const char* gfc_status_string(gfc_status s) {
+  switch (s) {
+    case GFC_OK: return "GFC_OK";
+    case GFC_ERR_INVALID_ARG: return "GFC_ERR_INVALID_ARG";
+    case GFC_ERR_UNSUPPORTED: return "GFC_ERR_UNSUPPORTED";
+    case GFC_ERR_ALLOC: return "GFC_ERR_ALLOC";
+    case GFC_ERR_CUDA: return "GFC_ERR_CUDA";
+    case GFC_ERR_TIMEOUT: return "GFC_ERR_TIMEOUT";
+  }
+  return "GFC_ERR_UNKNOWN";
+}
+
+gfc_status gfc_padded_size(int H, int W, int pad, int size_policy, int* M, int* N) {
+  clear_error();
+  if (!M || !N) return fail(GFC_ERR_INVALID_ARG, "gfc_padded_size: null output pointer");
+  if (H < 2 || W < 2) return fail(GFC_ERR_INVALID_ARG, "gfc_padded_size: H=%d W=%d (need >= 2)", H, W);
+  if (pad <= 0) pad = 4;
+  if (size_policy != GFC_SIZE_SMOOTH)
+    return fail(GFC_ERR_INVALID_ARG, "gfc_padded_size: unknown size policy %d", size_policy);
+  if ((long)H + 2L * pad > kMaxFftLen || (long)W + 2L * pad > kMaxFftLen)
+    return fail(GFC_ERR_UNSUPPORTED, "gfc_padded_size: H+2p=%ld or W+2p=%ld exceeds %d", (long)H + 2L * pad,
+                (long)W + 2L * pad, kMaxFftLen);
+  int m = smooth_even_at_least(H + 2 * pad), n = smooth_even_at_least(W + 2 * pad);
+  if (m > kMaxFftLen || n > kMaxFftLen)
+    return fail(GFC_ERR_UNSUPPORTED, "gfc_padded_size: padded size %dx%d exceeds %d", m, n, kMaxFftLen);
+  *M = m;
+  *N = n;
+  return GFC_OK;
+}
+
+gfc_status gfc_plan_create_ex(gfc_plan** out, const gfc_plan_opts* o) {
+  clear_error();
+  if (!out || !o) return fail(GFC_ERR_INVALID_ARG, "gfc_plan_create: null argument");
+  *out = nullptr;
+  if (o->C < 1 || o->batch < 1)
+    return fail(GFC_ERR_INVALID_ARG, "gfc_plan_create: C=%d batch=%d (need >= 1)", o->C, o->batch);
+  if (o->dtype != GFC_F32 && o->dtype != GFC_F16 && o->dtype != GFC_BF16)
+    return fail(GFC_ERR_INVALID_ARG, "gfc_plan_create: unknown dtype %d", (int)o->dtype);
+  if (o->chunk < 0) return fail(GFC_ERR_INVALID_ARG, "gfc_plan_create: chunk=%d", o->chunk);
+  int M, N;
+  gfc_status st = gfc_padded_size(o->H, o->W, o->pad, o->size_policy, &M, &N);
+  if (st != GFC_OK) return st;
+  const int pad = o->pad <= 0 ? 4 : o->pad;
+
+  gfc_plan* p = (gfc_plan*)calloc(1, sizeof(gfc_plan));
+  if (!p) return fail(GFC_ERR_ALLOC, "gfc_plan_create: host allocation failed");
+  p->H = o->H; p->W = o->W; p->C = o->C; p->batch = o->batch; p->pad = pad; p->dtype = o->dtype;
+  p->M = M; p->N = N; p->Nh = N / 2 + 1; p->ldS = (p->Nh + 3) & ~3;
+  p->stream = (cudaStream_t)o->stream;
+  if (!make_fft_plan(N, &p->rowplan) || !make_fft_plan(M, &p->colplan)) {
+    free(p);
+    return fail(GFC_ERR_UNSUPPORTED, "gfc_plan_create: no FFT schedule for %dx%d", M, N);
+  }
+  const long fields = (long)o->batch * o->C;
+  const size_t per_field = (size_t)M * p->ldS * sizeof(float2);
+  long chunk = o->chunk;
+  if (chunk == 0) {
+    // keep the spectrum of one chunk well inside L2 (about 64 MB)
+    chunk = (long)((64u << 20) / per_field);
+    if (chunk < 1) chunk = 1;
+  }
+  if (chunk > fields) chunk = fields;
+  p->chunk = (int)chunk;
+
+  cudaError_t e = cudaGetDevice(&p->device);
+  if (e == cudaSuccess) e = cudaMalloc(&p->G, (size_t)M * p->Nh * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&p->twN, (size_t)N * sizeof(float2));
+  if (e == cudaSuccess) e = cudaMalloc(&p->twM, (size_t)M * sizeof(float2));
+  if (e == cudaSuccess) e = cudaMalloc(&p->spec, per_field * (size_t)chunk);
+  if (e == cudaSuccess) e = cudaMalloc(&p->partial, (size_t)chunk * kMaxRowBlocks * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&p->dev_err, sizeof(int));
+  cudaStream_t bs = nullptr;
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaMemsetAsync(p->dev_err, 0, sizeof(int), bs);
+  if (e == cudaSuccess) e = build_twiddles(p->twN, N, bs);
+  if (e == cudaSuccess) e = build_twiddles(p->twM, M, bs);
+  if (e == cudaSuccess) e = build_green(p->G, M, N, p->Nh, bs);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(bs);
+  if (bs) cudaStreamDestroy(bs);
+  if (e != cudaSuccess) {
+    gfc_status s = cuda_fail(e, "gfc_plan_create");
+    destroy_plan(p);
+    return s;
+  }
+  *out = p;
+  return GFC_OK;
+}
+
+gfc_status gfc_plan_create(gfc_plan** plan, int H, int W, int C, int batch, gfc_dtype dtype) {
+  gfc_plan_opts o;
+  memset(&o, 0, sizeof(o));
+  o.H = H; o.W = W; o.C = C; o.batch = batch; o.dtype = dtype;
+  return gfc_plan_create_ex(plan, &o);
+}
+
+gfc_status gfc_plan_set_stream(gfc_plan* plan, void* stream) {
+  clear_error();
+  if (!plan) return fail(GFC_ERR_INVALID_ARG, "gfc_plan_set_stream: null plan");
+  plan->stream = (cudaStream_t)stream;
+  return GFC_OK;
+}
+
+gfc_status gfc_plan_padded_size(const gfc_plan* plan, int* M, int* N, int* pad) {
+  clear_error();
+  if (!plan) return fail(GFC_ERR_INVALID_ARG, "gfc_plan_padded_size: null plan");
+  if (M) *M = plan->M;
+  if (N) *N = plan->N;
+  if (pad) *pad = plan->pad;
+  return GFC_OK;
+}
+
+gfc_status gfc_plan_copy_green(const gfc_plan* plan, float* host_out) {
+  clear_error();
+  if (!plan || !host_out) return fail(GFC_ERR_INVALID_ARG, "gfc_plan_copy_green: null argument");
+  GFC_CUDA_TRY(cudaStreamSynchronize(plan->stream));
+  GFC_CUDA_TRY(cudaMemcpy(host_out, plan->G, (size_t)plan->M * plan->Nh * sizeof(float), cudaMemcpyDeviceToHost));
+  return GFC_OK;
+}
+
+gfc_status gfc_plan_sync(gfc_plan* plan) {
+  clear_error();
+  if (!plan) return fail(GFC_ERR_INVALID_ARG, "gfc_plan_sync: null plan");
+  GFC_CUDA_TRY(cudaStreamSynchronize(plan->stream));
+  int h = 0;
+  GFC_CUDA_TRY(cudaMemcpy(&h, plan->dev_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (h != 0) {
+    cudaMemset(plan->dev_err, 0, sizeof(int));
+    return fail(GFC_ERR_TIMEOUT, "gfc_plan_sync: device reported error code %d", h);
+  }
+  return GFC_OK;
+}
+
+}  // extern "C"
+
+static void destroy_plan(gfc_plan* p) {
+  if (!p) return;
+  cudaFree(p->G);
+  cudaFree(p->twN);
+  cudaFree(p->twM);
+  cudaFree(p->spec);
+  cudaFree(p->partial);
+  cudaFree(p->dev_err);
+  free(p);
+}
+
+extern "C" {
+
+gfc_status gfc_destroy(gfc_plan* p) {
+  clear_error();
+  destroy_plan(p);
+  return GFC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,457 @@
+// solve.cu -- the GFC solve (Eq. 23, Algorithm B) and its adjoint as three passes.
+//
+//   pass A  rows:    L = div E fused into the loads (Eq. 3), zero padding, real
+//                    row transforms of length N, two rows per complex transform
+//   pass B  columns: column transform of length M, multiply by the real Green
+//                    spectrum G (Eq. 22), inverse column transform
+//   pass C  rows:    inverse real row transforms, subtract u[0,0], crop the
+//                    image block, cast to the storage dtype (Algorithm B)
+//
+// The spectrum between passes lives in the plan's scratch, [field][M][ldS]
+// complex, of which only the Hermitian half (N/2+1 columns) is kept. Fields
+// are processed in chunks sized so that one chunk's scratch stays in L2.
+//
+// Two real rows a, b share one complex transform: z = a + i b, Z = F(z), then
+//   A[k] = (Z[k] + conj Z[N-k]) / 2,   B[k] = -i (Z[k] - conj Z[N-k]) / 2,
+// and on the way back z = F^-1(A + i B) with the Hermitian extension of A and
+// B, whose real and imaginary parts are the rows a and b.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include "gfc_internal.h"
+
+namespace gfc {
+
+enum Mode { kGrad = 0, kLap = 1, kAdj = 2 };
+
+struct PassArgs {
+  int H, W, p, M, N, Nh, ldS;
+  int nrows, ncols;  // support of pass A's input rows (from torus row/col p)
+  int pairs;         // row pairs handled by the row pass
+  int ppb;           // row pairs per block
+  int nparts;        // pass A blocks per field (adjoint partial sums)
+  FftPlan plan;      // the transform this pass runs
+};
+
+__device__ __forceinline__ float to_f(float x) { return x; }
+__device__ __forceinline__ float to_f(__half x) { return __half2float(x); }
+__device__ __forceinline__ float to_f(__nv_bfloat16 x) { return __bfloat162float(x); }
+template <typename T> __device__ __forceinline__ T from_f(float x);
+template <> __device__ __forceinline__ float from_f<float>(float x) { return x; }
+template <> __device__ __forceinline__ __half from_f<__half>(float x) { return __float2half_rn(x); }
+template <> __device__ __forceinline__ __nv_bfloat16 from_f<__nv_bfloat16>(float x) { return __float2bfloat16_rn(x); }
+
+template <typename T>
+__device__ __forceinline__ float ld(const T* __restrict__ g, int i, int j, int H, int W) {
+  return (i >= 0 && i < H && j >= 0 && j < W) ? to_f(g[(size_t)i * W + j]) : 0.0f;
+}
+
+// Deterministic block sum: fixed per-thread order, fixed tree. All threads get the result.
+__device__ float block_sum(float v, float* red) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  float s = 0.0f;
+  for (int w = 0; w < nw; ++w) s += red[w];
+  __syncthreads();
+  return s;
+}
+
+// ---------------------------------------------------------------------------
+// pass A
+// ---------------------------------------------------------------------------
+template <typename T, int MODE>
+__global__ void __launch_bounds__(256) k_pass_a(const T* __restrict__ in0, const T* __restrict__ in1,
+                                                float2* __restrict__ spec, float* __restrict__ partial,
+                                                const float2* __restrict__ twg, PassArgs A) {
+  extern __shared__ float2 sm[];
+  __shared__ float red[32];
+  float2* tw = sm;
+  float2* b0 = sm + A.N;
+  float2* b1 = b0 + A.N;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const size_t fe = (size_t)A.H * A.W;
+  const T* a = in0 + blockIdx.y * fe;
+  const T* b = (MODE == kGrad) ? in1 + blockIdx.y * fe : nullptr;
+  float2* S = spec + (size_t)blockIdx.y * A.M * A.ldS;
+  for (int m = tid; m < A.N; m += nthr) tw[m] = twg[m];
+  float acc = 0.0f;
+  const int q0 = blockIdx.x * A.ppb;
+  const int q1 = min(q0 + A.ppb, A.pairs);
+  for (int q = q0; q < q1; ++q) {
+    const int i0 = 2 * q, i1 = 2 * q + 1;
+    const bool has1 = i1 < A.nrows;
+    __syncthreads();
+    for (int c = tid; c < A.N; c += nthr) {
+      const int j = c - A.p;
+      float va = 0.0f, vb = 0.0f;
+      if (j >= 0 && j < A.ncols) {
+        if (MODE == kGrad) {
+          va = ld(a, i0, j, A.H, A.W) - ld(a, i0, j - 1, A.H, A.W) + ld(b, i0, j, A.H, A.W) - ld(b, i0 - 1, j, A.H, A.W);
+          if (has1)
+            vb = ld(a, i1, j, A.H, A.W) - ld(a, i1, j - 1, A.H, A.W) + ld(b, i1, j, A.H, A.W) - ld(b, i1 - 1, j, A.H, A.W);
+        } else {
+          va = ld(a, i0, j, A.H, A.W);
+          if (has1) vb = ld(a, i1, j, A.H, A.W);
+        }
+      }
+      if (MODE == kAdj) acc += va + vb;
+      b0[c] = make_float2(va, vb);
+    }
+    __syncthreads();
+    const float2* X = fft_smem<-1>(b0, b1, A.plan, 1, 1, tw, tid, nthr);
+    for (int k = tid; k < A.Nh; k += nthr) {
+      const float2 zk = X[k], zm = X[k == 0 ? 0 : A.N - k];
+      S[(size_t)(A.p + i0) * A.ldS + k] = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
+      if (has1) S[(size_t)(A.p + i1) * A.ldS + k] = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
+    }
+  }
+  if (MODE == kAdj) {
+    const float s = block_sum(acc, red);
+    if (tid == 0) partial[(size_t)blockIdx.y * kMaxRowBlocks + blockIdx.x] = s;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// pass B: S columns per block, interleaved in shared memory (element m of
+// column f at m*S + f)
+// ---------------------------------------------------------------------------
+template <int S, int MODE>
+__global__ void __launch_bounds__(256) k_pass_b(float2* __restrict__ spec, const float* __restrict__ G,
+                                                const float2* __restrict__ twg, const float* __restrict__ partial,
+                                                PassArgs A) {
+  extern __shared__ float2 sm[];
+  float2* tw = sm;
+  float2* b0 = sm + A.M;
+  float2* b1 = b0 + (size_t)A.M * S;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int l0 = blockIdx.x * S;
+  float2* Sp = spec + (size_t)blockIdx.y * A.M * A.ldS;
+  for (int m = tid; m < A.M; m += nthr) tw[m] = twg[m];
+  float tot = 0.0f;
+  if (MODE == kAdj) {
+    const float* pp = partial + (size_t)blockIdx.y * kMaxRowBlocks;
+    for (int i = 0; i < A.nparts; ++i) tot += pp[i];
+  }
+  for (int t = tid; t < A.M * S; t += nthr) {
+    const int f = t % S, r = t / S, l = l0 + f;
+    float2 v = make_float2(0.0f, 0.0f);
+    if (l < A.Nh) {
+      if (r >= A.p && r < A.p + A.nrows) v = Sp[(size_t)r * A.ldS + l];
+      else if (MODE == kAdj && r == 0) v = make_float2(-tot, 0.0f);  // row DFT of -(sum) e_00
+    }
+    b0[t] = v;
+  }
+  __syncthreads();
+  float2* X = fft_smem<-1>(b0, b1, A.plan, S, S, tw, tid, nthr);
+  float2* Y = (X == b0) ? b1 : b0;
+  for (int t = tid; t < A.M * S; t += nthr) {
+    const int f = t % S, k = t / S, l = l0 + f;
+    const float g = (l < A.Nh) ? G[(size_t)k * A.Nh + l] : 0.0f;
+    X[t] = cscale(X[t], g);
+  }
+  __syncthreads();
+  const float2* Z = fft_smem<+1>(X, Y, A.plan, S, S, tw, tid, nthr);
+  for (int t = tid; t < A.M * S; t += nthr) {
+    const int f = t % S, r = t / S, l = l0 + f;
+    if (l >= A.Nh) continue;
+    const bool keep = (MODE == kAdj) ? (r >= A.p && r <= A.p + A.H) : (r == 0 || (r >= A.p && r < A.p + A.H));
+    if (keep) Sp[(size_t)r * A.ldS + l] = Z[t];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// pass C
+// ---------------------------------------------------------------------------
+// Build z = A + i B over the full length N from Hermitian halves of rows ra, rb
+// (rb < 0: zero row). The imaginary parts of bins 0 and N/2 are dropped, as a
+// real inverse transform does.
+__device__ __forceinline__ void load_pair_hermitian(const float2* __restrict__ Sp, int ldS, int N, int ra, int rb,
+                                                    float2* __restrict__ dst, int tid, int nthr) {
+  const int half = N / 2;
+  for (int l = tid; l < N; l += nthr) {
+    const bool lo = l <= half;
+    const int src = lo ? l : N - l;
+    float2 ya = Sp[(size_t)ra * ldS + src];
+    float2 yb = rb >= 0 ? Sp[(size_t)rb * ldS + src] : make_float2(0.0f, 0.0f);
+    if (src == 0 || src == half) { ya.y = 0.0f; yb.y = 0.0f; }
+    dst[l] = lo ? make_float2(ya.x - yb.y, ya.y + yb.x) : make_float2(ya.x + yb.y, yb.x - ya.y);
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_pass_c(const float2* __restrict__ spec, T* __restrict__ out,
+                                                const float2* __restrict__ twg, PassArgs A) {
+  extern __shared__ float2 sm[];
+  __shared__ float red[32];
+  float2* tw = sm;
+  float2* b0 = sm + A.N;
+  float2* b1 = b0 + A.N;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const float2* Sp = spec + (size_t)blockIdx.y * A.M * A.ldS;
+  T* o = out + (size_t)blockIdx.y * A.H * A.W;
+  for (int m = tid; m < A.N; m += nthr) tw[m] = twg[m];
+  // u[0,0] = sum over the full row-0 spectrum = Re Y[0] + Re Y[N/2] + 2 sum_{0<l<N/2} Re Y[l]
+  float s = 0.0f;
+  for (int l = tid; l <= A.N / 2; l += nthr) {
+    const float x = Sp[l].x;
+    s += (l == 0 || l == A.N / 2) ? x : 2.0f * x;
+  }
+  const float u00 = block_sum(s, red);
+  const int q0 = blockIdx.x * A.ppb;
+  const int q1 = min(q0 + A.ppb, A.pairs);
+  for (int q = q0; q < q1; ++q) {
+    const int i0 = 2 * q, i1 = 2 * q + 1;
+    const bool has1 = i1 < A.H;
+    __syncthreads();
+    load_pair_hermitian(Sp, A.ldS, A.N, A.p + i0, has1 ? A.p + i1 : -1, b0, tid, nthr);
+    __syncthreads();
+    const float2* Z = fft_smem<+1>(b0, b1, A.plan, 1, 1, tw, tid, nthr);
+    for (int j = tid; j < A.W; j += nthr) {
+      const float2 z = Z[A.p + j];
+      o[(size_t)i0 * A.W + j] = from_f<T>(z.x - u00);
+      if (has1) o[(size_t)i1 * A.W + j] = from_f<T>(z.y - u00);
+    }
+  }
+}
+
+// Adjoint pass C: w rows 0..H (torus p..p+H) come back from pass B; the
+// transpose of the divergence gives
+//   grad_gx[i,j] = w[i,j] - w[i,j+1],   grad_gy[i,j] = w[i,j] - w[i+1,j].
+// A block owns output rows [2 q0, 2 q1) and also transforms pair q1 to get the
+// row below its last one.
+template <typename T>
+__global__ void __launch_bounds__(256) k_pass_c_adj(const float2* __restrict__ spec, T* __restrict__ ggx,
+                                                    T* __restrict__ ggy, const float2* __restrict__ twg,
+                                                    PassArgs A) {
+  extern __shared__ float2 sm[];
+  float2* tw = sm;
+  float2* b0 = sm + A.N;
+  float2* b1 = b0 + A.N;
+  float* prev = reinterpret_cast<float*>(b1 + A.N);  // [W] row 2q-1 of w from the previous pair
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const float2* Sp = spec + (size_t)blockIdx.y * A.M * A.ldS;
+  T* gx = ggx + (size_t)blockIdx.y * A.H * A.W;
+  T* gy = ggy + (size_t)blockIdx.y * A.H * A.W;
+  for (int m = tid; m < A.N; m += nthr) tw[m] = twg[m];
+  const int q0 = blockIdx.x * A.ppb;
+  const int q1 = min(q0 + A.ppb, A.pairs);
+  const int wrows = A.H + 1;
+  for (int q = q0; q <= q1; ++q) {
+    const int i0 = 2 * q, i1 = 2 * q + 1;
+    if (i0 >= wrows) break;
+    const bool has1 = i1 < wrows;
+    __syncthreads();
+    load_pair_hermitian(Sp, A.ldS, A.N, A.p + i0, has1 ? A.p + i1 : -1, b0, tid, nthr);
+    __syncthreads();
+    const float2* Z = fft_smem<+1>(b0, b1, A.plan, 1, 1, tw, tid, nthr);
+    for (int j = tid; j < A.W; j += nthr) {
+      const float2 z = Z[A.p + j], zr = Z[A.p + j + 1];
+      if (q > q0 && i0 - 1 < A.H) gy[(size_t)(i0 - 1) * A.W + j] = from_f<T>(prev[j] - z.x);
+      if (q < q1) {
+        if (i0 < A.H) {
+          gx[(size_t)i0 * A.W + j] = from_f<T>(z.x - zr.x);
+          gy[(size_t)i0 * A.W + j] = from_f<T>(z.x - z.y);
+        }
+        if (i1 < A.H) gx[(size_t)i1 * A.W + j] = from_f<T>(z.y - zr.y);
+        prev[j] = z.y;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// standalone batched complex transform (test entry point)
+// ---------------------------------------------------------------------------
+template <int DIR>
+__global__ void __launch_bounds__(256) k_fft_rows(const float2* __restrict__ in, float2* __restrict__ out,
+                                                  FftPlan pl) {
+  extern __shared__ float2 sm[];
+  float2* tw = sm;
+  float2* b0 = sm + pl.n;
+  float2* b1 = b0 + pl.n;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  for (int m = tid; m < pl.n; m += nthr) {
+    double s, c;
+    sincospi(2.0 * (double)m / (double)pl.n, &s, &c);
+    tw[m] = make_float2((float)c, (float)(-s));
+  }
+  const size_t row = blockIdx.x;
+  for (int m = tid; m < pl.n; m += nthr) b0[m] = in[row * pl.n + m];
+  __syncthreads();
+  const float2* X = fft_smem<DIR>(b0, b1, pl, 1, 1, tw, tid, nthr);
+  for (int m = tid; m < pl.n; m += nthr) out[row * pl.n + m] = X[m];
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+static int pick_strip(int M) {
+  // columns per pass-B block: largest power of two with (M + 2 M S) * 8 B <= 200 KB
+  for (int S = 8; S > 1; S >>= 1)
+    if ((size_t)(M + 2 * M * S) * sizeof(float2) <= 200u * 1024u) return S;
+  return 1;
+}
+
+static PassArgs base_args(const gfc_plan* P) {
+  PassArgs a;
+  a.H = P->H; a.W = P->W; a.p = P->pad; a.M = P->M; a.N = P->N; a.Nh = P->Nh; a.ldS = P->ldS;
+  a.nrows = a.ncols = a.pairs = a.ppb = a.nparts = 0;
+  a.plan = P->rowplan;
+  return a;
+}
+
+static int ceil_div(int a, int b) { return (a + b - 1) / b; }
+
+template <int S, int MODE>
+static cudaError_t launch_b(const gfc_plan* P, PassArgs B, int nf, cudaStream_t st) {
+  const size_t smem = (size_t)(P->M + 2 * (size_t)P->M * S) * sizeof(float2);
+  auto k = k_pass_b<S, MODE>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k<<<dim3(ceil_div(P->Nh, S), nf), 256, smem, st>>>(P->spec, P->G, P->twM, P->partial, B);
+  return cudaGetLastError();
+}
+
+template <int MODE>
+static cudaError_t launch_b_any(const gfc_plan* P, PassArgs B, int nf, cudaStream_t st) {
+  switch (pick_strip(P->M)) {
+    case 8: return launch_b<8, MODE>(P, B, nf, st);
+    case 4: return launch_b<4, MODE>(P, B, nf, st);
+    case 2: return launch_b<2, MODE>(P, B, nf, st);
+    default: return launch_b<1, MODE>(P, B, nf, st);
+  }
+}
+
+template <typename T, int MODE>
+static cudaError_t run_chunk(const gfc_plan* P, const T* in0, const T* in1, T* out0, T* out1, int nf) {
+  cudaStream_t st = P->stream;
+  // pass A
+  PassArgs A = base_args(P);
+  A.nrows = (MODE == kGrad) ? P->H + 1 : P->H;
+  A.ncols = (MODE == kGrad) ? P->W + 1 : P->W;
+  A.pairs = ceil_div(A.nrows, 2);
+  A.ppb = 4;
+  if (ceil_div(A.pairs, A.ppb) > kMaxRowBlocks) A.ppb = ceil_div(A.pairs, kMaxRowBlocks);
+  A.nparts = ceil_div(A.pairs, A.ppb);
+  {
+    const size_t smem = 3 * (size_t)P->N * sizeof(float2);
+    auto k = k_pass_a<T, MODE>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k<<<dim3(A.nparts, nf), 256, smem, st>>>(in0, in1, P->spec, P->partial, P->twN, A);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  // pass B
+  PassArgs B = A;
+  B.plan = P->colplan;
+  cudaError_t e = launch_b_any<MODE>(P, B, nf, st);
+  if (e != cudaSuccess) return e;
+  // pass C
+  PassArgs C = base_args(P);
+  C.ppb = 4;
+  if (MODE == kAdj) {
+    C.pairs = ceil_div(P->H, 2);  // output row pairs
+    const size_t smem = 3 * (size_t)P->N * sizeof(float2) + (size_t)P->W * sizeof(float);
+    auto k = k_pass_c_adj<T>;
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k<<<dim3(ceil_div(C.pairs, C.ppb), nf), 256, smem, st>>>(P->spec, out0, out1, P->twN, C);
+  } else {
+    C.pairs = ceil_div(P->H, 2);
+    const size_t smem = 3 * (size_t)P->N * sizeof(float2);
+    auto k = k_pass_c<T>;
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k<<<dim3(ceil_div(C.pairs, C.ppb), nf), 256, smem, st>>>(P->spec, out0, P->twN, C);
+  }
+  return cudaGetLastError();
+}
+
+template <typename T, int MODE>
+static gfc_status run_all(gfc_plan* P, const void* a, const void* b, void* o0, void* o1) {
+  const long fields = (long)P->batch * P->C;
+  const size_t fe = (size_t)P->H * P->W;
+  for (long f0 = 0; f0 < fields; f0 += P->chunk) {
+    const int nf = (int)((fields - f0 < P->chunk) ? fields - f0 : P->chunk);
+    const T* in0 = static_cast<const T*>(a) + f0 * fe;
+    const T* in1 = b ? static_cast<const T*>(b) + f0 * fe : nullptr;
+    T* out0 = static_cast<T*>(o0) + f0 * fe;
+    T* out1 = o1 ? static_cast<T*>(o1) + f0 * fe : nullptr;
+    cudaError_t e = run_chunk<T, MODE>(P, in0, in1, out0, out1, nf);
+    if (e != cudaSuccess) return cuda_fail(e, "gfc solve launch");
+  }
+  return GFC_OK;
+}
+
+template <int MODE>
+static gfc_status dispatch(gfc_plan* P, const void* a, const void* b, void* o0, void* o1) {
+  switch (P->dtype) {
+    case GFC_F32: return run_all<float, MODE>(P, a, b, o0, o1);
+    case GFC_F16: return run_all<__half, MODE>(P, a, b, o0, o1);
+    default: return run_all<__nv_bfloat16, MODE>(P, a, b, o0, o1);
+  }
+}
+
+static bool misaligned(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) != 0; }
+
+}  // namespace gfc
+
+using namespace gfc;
+
+extern "C" {
+
+gfc_status gfc_solve_from_gradient(gfc_plan* plan, const void* gx, const void* gy, void* out) {
+  clear_error();
+  if (!plan || !gx || !gy || !out) return fail(GFC_ERR_INVALID_ARG, "gfc_solve_from_gradient: null argument");
+  if (misaligned(gx) || misaligned(gy) || misaligned(out))
+    return fail(GFC_ERR_INVALID_ARG, "gfc_solve_from_gradient: pointers must be 16-byte aligned");
+  if (out == gx || out == gy) return fail(GFC_ERR_INVALID_ARG, "gfc_solve_from_gradient: out aliases an input");
+  return dispatch<kGrad>(plan, gx, gy, out, nullptr);
+}
+
+gfc_status gfc_solve_from_laplacian(gfc_plan* plan, const void* lap, void* out) {
+  clear_error();
+  if (!plan || !lap || !out) return fail(GFC_ERR_INVALID_ARG, "gfc_solve_from_laplacian: null argument");
+  if (misaligned(lap) || misaligned(out))
+    return fail(GFC_ERR_INVALID_ARG, "gfc_solve_from_laplacian: pointers must be 16-byte aligned");
+  if (out == lap) return fail(GFC_ERR_INVALID_ARG, "gfc_solve_from_laplacian: out aliases lap");
+  return dispatch<kLap>(plan, lap, nullptr, out, nullptr);
+}
+
+gfc_status gfc_backward(gfc_plan* plan, const void* grad_out, void* grad_gx, void* grad_gy) {
+  clear_error();
+  if (!plan || !grad_out || !grad_gx || !grad_gy) return fail(GFC_ERR_INVALID_ARG, "gfc_backward: null argument");
+  if (misaligned(grad_out) || misaligned(grad_gx) || misaligned(grad_gy))
+    return fail(GFC_ERR_INVALID_ARG, "gfc_backward: pointers must be 16-byte aligned");
+  if (grad_gx == grad_gy || grad_gx == grad_out || grad_gy == grad_out)
+    return fail(GFC_ERR_INVALID_ARG, "gfc_backward: arguments alias");
+  return dispatch<kAdj>(plan, grad_out, nullptr, grad_gx, grad_gy);
+}
+
+gfc_status gfc_fft_c2c(int n, int count, int dir, const void* in, void* out, void* stream) {
+  clear_error();
+  if (!in || !out || count < 0 || (dir != -1 && dir != 1))
+    return fail(GFC_ERR_INVALID_ARG, "gfc_fft_c2c: bad argument (count=%d dir=%d)", count, dir);
+  if (misaligned(in) || misaligned(out)) return fail(GFC_ERR_INVALID_ARG, "gfc_fft_c2c: pointers must be 16-byte aligned");
+  FftPlan pl;
+  if (!make_fft_plan(n, &pl)) return fail(GFC_ERR_UNSUPPORTED, "gfc_fft_c2c: n=%d is not 7-smooth or > %d", n, kMaxFftLen);
+  if (count == 0) return GFC_OK;
+  const size_t smem = 3 * (size_t)n * sizeof(float2);
+  cudaStream_t st = (cudaStream_t)stream;
+  if (dir < 0) {
+    GFC_CUDA_TRY(cudaFuncSetAttribute(k_fft_rows<-1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_fft_rows<-1><<<count, 256, smem, st>>>((const float2*)in, (float2*)out, pl);
+  } else {
+    GFC_CUDA_TRY(cudaFuncSetAttribute(k_fft_rows<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_fft_rows<1><<<count, 256, smem, st>>>((const float2*)in, (float2*)out, pl);
+  }
+  GFC_CUDA_TRY(cudaGetLastError());
+  return GFC_OK;
+}
+
+}  // extern "C"

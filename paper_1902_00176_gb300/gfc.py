@@ -1,0 +1,258 @@
+"""Python binding of the GFC C ABI (``include/gfc.h``): argument marshalling only.
+
+Every step of the solve runs in the CUDA library ``libgfc.so`` built in-tree
+by ``__graft_entry__.build()``; this module only checks tensors, passes their
+device pointers and the current torch stream, and maps status codes to
+exceptions. If the library is missing it raises: there is no CPU fallback.
+
+Layout: fields are ``[batch, C, H, W]`` contiguous CUDA tensors (a ``[H, W]``
+or ``[C, H, W]`` tensor is read as batch 1 / C 1), in float32, float16 or
+bfloat16 storage; arithmetic is FP32.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgfc.so")
+
+GFC_F32, GFC_F16, GFC_BF16 = 0, 1, 2
+_DTYPES = {torch.float32: GFC_F32, torch.float16: GFC_F16, torch.bfloat16: GFC_BF16}
+_STATUS = {0: "GFC_OK", 1: "GFC_ERR_INVALID_ARG", 2: "GFC_ERR_UNSUPPORTED", 3: "GFC_ERR_ALLOC",
+           4: "GFC_ERR_CUDA", 5: "GFC_ERR_TIMEOUT"}
+
+
+class GFCError(RuntimeError):
+    """A non-OK gfc_status, with the library's message."""
+
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class _Opts(ctypes.Structure):
+    _fields_ = [("H", ctypes.c_int), ("W", ctypes.c_int), ("C", ctypes.c_int), ("batch", ctypes.c_int),
+                ("dtype", ctypes.c_int), ("pad", ctypes.c_int), ("size_policy", ctypes.c_int),
+                ("chunk", ctypes.c_int), ("stream", ctypes.c_void_p)]
+
+
+_lib = None
+_lib_lock = threading.Lock()
+
+# (name, argtypes) of every function declared in include/gfc.h
+_SIGNATURES = {
+    "gfc_padded_size": [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                        ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
+    "gfc_plan_create": [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                        ctypes.c_int],
+    "gfc_plan_create_ex": [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(_Opts)],
+    "gfc_plan_set_stream": [ctypes.c_void_p, ctypes.c_void_p],
+    "gfc_plan_padded_size": [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                             ctypes.POINTER(ctypes.c_int)],
+    "gfc_plan_copy_green": [ctypes.c_void_p, ctypes.c_void_p],
+    "gfc_solve_from_gradient": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
+    "gfc_solve_from_laplacian": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
+    "gfc_backward": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
+    "gfc_fft_c2c": [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
+    "gfc_plan_sync": [ctypes.c_void_p],
+    "gfc_destroy": [ctypes.c_void_p],
+    "gfc_last_error": [],
+    "gfc_status_string": [ctypes.c_int],
+}
+
+
+def lib() -> ctypes.CDLL:
+    """Load ``libgfc.so`` (raises if it has not been built)."""
+    global _lib
+    with _lib_lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"GFC CUDA library not built ({LIB_PATH} missing): "
+                                   "run __graft_entry__.build() first")
+            L = ctypes.CDLL(LIB_PATH)
+            for name, argt in _SIGNATURES.items():
+                fn = getattr(L, name)
+                fn.argtypes = argt
+                fn.restype = ctypes.c_char_p if name in ("gfc_last_error", "gfc_status_string") else ctypes.c_int
+            _lib = L
+    return _lib
+
+
+def _check(status: int):
+    if status != 0:
+        raise GFCError(status, lib().gfc_last_error().decode(errors="replace"))
+
+
+def padded_size(H: int, W: int, pad: int = 4):
+    """(M, N) of the padded torus for an H x W image (host-only, no GPU needed)."""
+    M, N = ctypes.c_int(), ctypes.c_int()
+    _check(lib().gfc_padded_size(H, W, pad, 0, ctypes.byref(M), ctypes.byref(N)))
+    return M.value, N.value
+
+
+def _stream_ptr(device) -> int:
+    return torch.cuda.current_stream(device).cuda_stream
+
+
+def _as_bchw(t: torch.Tensor) -> torch.Tensor:
+    if t.dim() == 2:
+        return t.view(1, 1, *t.shape)
+    if t.dim() == 3:
+        return t.view(1, *t.shape)
+    if t.dim() == 4:
+        return t
+    raise ValueError(f"expected a [H,W], [C,H,W] or [B,C,H,W] tensor, got shape {tuple(t.shape)}")
+
+
+class Plan:
+    """A GFC plan: Green spectrum, transform tables and scratch for one problem shape."""
+
+    def __init__(self, H: int, W: int, C: int = 1, batch: int = 1, dtype=torch.float32, pad: int = 4,
+                 chunk: int = 0, device=None):
+        if dtype not in _DTYPES:
+            raise ValueError(f"unsupported dtype {dtype}")
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else
+                                   torch.device(device).index or 0)
+        self.H, self.W, self.C, self.batch, self.dtype = H, W, C, batch, dtype
+        o = _Opts(H, W, C, batch, _DTYPES[dtype], pad, 0, chunk, None)
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            _check(lib().gfc_plan_create_ex(ctypes.byref(h), ctypes.byref(o)))
+        self._h = h
+        M, N, p = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(lib().gfc_plan_padded_size(h, ctypes.byref(M), ctypes.byref(N), ctypes.byref(p)))
+        self.M, self.N, self.pad = M.value, N.value, p.value
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().gfc_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _bind_stream(self):
+        _check(lib().gfc_plan_set_stream(self._h, ctypes.c_void_p(_stream_ptr(self.device))))
+
+    def _check_field(self, t: torch.Tensor, name: str) -> torch.Tensor:
+        t = _as_bchw(t)
+        if not t.is_cuda or t.device != self.device:
+            raise ValueError(f"{name} must be a CUDA tensor on {self.device}")
+        if t.dtype != self.dtype:
+            raise ValueError(f"{name} has dtype {t.dtype}, plan expects {self.dtype}")
+        if tuple(t.shape) != (self.batch, self.C, self.H, self.W):
+            raise ValueError(f"{name} has shape {tuple(t.shape)}, plan expects "
+                             f"{(self.batch, self.C, self.H, self.W)}")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+        return t
+
+    def _empty(self):
+        return torch.empty((self.batch, self.C, self.H, self.W), dtype=self.dtype, device=self.device)
+
+    def solve_from_gradient(self, gx, gy, out=None):
+        gx, gy = self._check_field(gx, "gx"), self._check_field(gy, "gy")
+        out = self._empty() if out is None else self._check_field(out, "out")
+        self._bind_stream()
+        _check(lib().gfc_solve_from_gradient(self._h, gx.data_ptr(), gy.data_ptr(), out.data_ptr()))
+        return out
+
+    def solve_from_laplacian(self, lap, out=None):
+        lap = self._check_field(lap, "lap")
+        out = self._empty() if out is None else self._check_field(out, "out")
+        self._bind_stream()
+        _check(lib().gfc_solve_from_laplacian(self._h, lap.data_ptr(), out.data_ptr()))
+        return out
+
+    def backward(self, grad_out, grad_gx=None, grad_gy=None):
+        grad_out = self._check_field(grad_out, "grad_out")
+        grad_gx = self._empty() if grad_gx is None else self._check_field(grad_gx, "grad_gx")
+        grad_gy = self._empty() if grad_gy is None else self._check_field(grad_gy, "grad_gy")
+        self._bind_stream()
+        _check(lib().gfc_backward(self._h, grad_out.data_ptr(), grad_gx.data_ptr(), grad_gy.data_ptr()))
+        return grad_gx, grad_gy
+
+    def green(self):
+        """The plan's FP32 Green spectrum, M x (N/2+1), as a CPU tensor (1/(MN) folded in)."""
+        g = torch.empty((self.M, self.N // 2 + 1), dtype=torch.float32)
+        self._bind_stream()
+        _check(lib().gfc_plan_copy_green(self._h, g.data_ptr()))
+        return g
+
+    def sync(self):
+        _check(lib().gfc_plan_sync(self._h))
+
+
+_plans: dict = {}
+
+
+def get_plan(H, W, C, batch, dtype, device) -> Plan:
+    """Cached plan for a problem shape on a device."""
+    dev = torch.device(device)
+    key = (H, W, C, batch, dtype, dev.index)
+    p = _plans.get(key)
+    if p is None:
+        p = Plan(H, W, C, batch, dtype, device=dev)
+        _plans[key] = p
+    return p
+
+
+def solve(gx: torch.Tensor, gy: torch.Tensor) -> torch.Tensor:
+    """GFC solve from a gradient field; returns a tensor shaped like gx."""
+    b = _as_bchw(gx)
+    p = get_plan(b.shape[2], b.shape[3], b.shape[1], b.shape[0], gx.dtype, gx.device)
+    return p.solve_from_gradient(gx, gy).view(gx.shape)
+
+
+def solve_laplacian(lap: torch.Tensor) -> torch.Tensor:
+    """GFC solve from a Laplacian; returns a tensor shaped like lap."""
+    b = _as_bchw(lap)
+    p = get_plan(b.shape[2], b.shape[3], b.shape[1], b.shape[0], lap.dtype, lap.device)
+    return p.solve_from_laplacian(lap).view(lap.shape)
+
+
+def fft_c2c(x: torch.Tensor, inverse: bool = False) -> torch.Tensor:
+    """Batched complex transform along the last axis with the library's own FFT engine."""
+    if x.dtype != torch.complex64 or not x.is_cuda:
+        raise ValueError("fft_c2c expects a complex64 CUDA tensor")
+    x = x.contiguous()
+    out = torch.empty_like(x)
+    n = x.shape[-1]
+    count = x.numel() // n if n else 0
+    _check(lib().gfc_fft_c2c(n, count, 1 if inverse else -1, x.data_ptr(), out.data_ptr(),
+                             ctypes.c_void_p(_stream_ptr(x.device))))
+    return out
+
+
+class GFCFunction(torch.autograd.Function):
+    """GFC as a differentiable layer: forward solves from (gx, gy), backward runs the
+    hand-written adjoint kernels. Nothing but the plan is saved between the two."""
+
+    @staticmethod
+    def forward(ctx, gx, gy):
+        b = _as_bchw(gx)
+        p = get_plan(b.shape[2], b.shape[3], b.shape[1], b.shape[0], gx.dtype, gx.device)
+        ctx.plan = p
+        ctx.shape = gx.shape
+        return p.solve_from_gradient(gx.contiguous(), gy.contiguous()).view(gx.shape)
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        ggx, ggy = ctx.plan.backward(grad_out.contiguous())
+        return ggx.view(ctx.shape), ggy.view(ctx.shape)
+
+
+def gfc_layer(gx: torch.Tensor, gy: torch.Tensor) -> torch.Tensor:
+    """Differentiable GFC solve (see GFCFunction)."""
+    return GFCFunction.apply(gx, gy)

@@ -9,3 +9,15 @@ if ROOT not in sys.path:
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (sm_103a) and the built library")
     config.addinivalue_line("markers", "slow: long-running CPU test")
+
+
+import pytest  # noqa: E402
+
+
+@pytest.fixture(scope="session")
+def gfc_lib():
+    """Build (incrementally) and load the in-tree CUDA library."""
+    from paper_1902_00176_gb300 import _build, gfc
+
+    _build.build_library()
+    return gfc.lib()

@@ -1,0 +1,219 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances (FP32 arithmetic): relative L2 <= 1e-5 and max-abs <= 1e-4 for
+data on a [0, 1] range; for 16-bit storage, relative L2 <= 2e-3 against the
+oracle run on the dequantised 16-bit inputs. Expected FP32 error is far
+below this: FFT round-off (~1e-7 relative per bin) amplified by at most
+|G| ~ (M / 2 pi)^2 on the few lowest bins, averaged over the field.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle.gfc_oracle as O
+from paper_1902_00176_gb300 import gfc, synth
+
+pytestmark = pytest.mark.gpu
+
+DEV = torch.device("cuda:0")
+REL_F32, MAXABS_F32, REL_16 = 1e-5, 1e-4, 2e-3
+
+
+def _rel(got, ref):
+    return float(np.linalg.norm(got - ref) / max(np.linalg.norm(ref), 1e-300))
+
+
+def _to_dev(a, dtype=torch.float32):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV).to(dtype)
+
+
+def _np(t):
+    return t.double().cpu().numpy()
+
+
+@pytest.fixture(autouse=True)
+def _lib(gfc_lib):
+    yield
+
+
+# ---------------------------------------------------------------- tables, FFT
+
+@pytest.mark.parametrize("H,W", [(64, 96), (801, 1200), (256, 256), (13, 7)])
+def test_green_table_matches_closed_form(H, W):
+    p = gfc.Plan(H, W, device=DEV)
+    got = p.green().numpy().astype(np.float64)
+    ref = O.green_spectrum(p.M, p.N)[:, : p.N // 2 + 1] / (p.M * p.N)
+    assert got[0, 0] == 0.0
+    assert np.abs(got - ref).max() <= 2e-7 * np.abs(ref).max()
+    p.close()
+
+
+@pytest.mark.parametrize("n", [2, 3, 4, 5, 7, 8, 6, 10, 12, 16, 30, 49, 64, 72, 105, 108, 210, 270, 343, 625,
+                               729, 810, 1024, 1050, 1250, 1568, 2048, 2187, 2401, 4096])
+def test_fft_engine_matches_dft(n):
+    rng = np.random.default_rng(n)
+    count = 3
+    x = (rng.standard_normal((count, n)) + 1j * rng.standard_normal((count, n))).astype(np.complex64)
+    xd = torch.from_numpy(x).to(DEV)
+    fwd = gfc.fft_c2c(xd).cpu().numpy().astype(np.complex128)
+    inv = gfc.fft_c2c(xd, inverse=True).cpu().numpy().astype(np.complex128)
+    x64 = x.astype(np.complex128)
+    ref_f = np.stack([O.dft_matrix(n, -1) @ r for r in x64])
+    ref_i = np.stack([O.dft_matrix(n, +1) @ r for r in x64])
+    tol = 4e-7 * np.sqrt(n) * max(1.0, np.log2(n))
+    assert np.linalg.norm(fwd - ref_f) / np.linalg.norm(ref_f) < tol
+    assert np.linalg.norm(inv - ref_i) / np.linalg.norm(ref_i) < tol
+
+
+def test_fft_engine_impulse_and_in_place():
+    n = 1250
+    x = torch.zeros((2, n), dtype=torch.complex64, device=DEV)
+    x[0, 0] = 1.0
+    x[1, 3] = 1.0
+    X = gfc.fft_c2c(x).cpu().numpy()
+    assert np.abs(X[0] - 1.0).max() < 1e-6
+    k = np.arange(n)
+    assert np.abs(X[1] - np.exp(-2j * np.pi * 3 * k / n)).max() < 1e-5
+
+
+# ---------------------------------------------------------------- forward
+
+def test_gradient_removal_field_matches_oracle():
+    img, gx, gy = synth.gradient_removal_image(seed=0, H=64, W=96)
+    p = gfc.Plan(64, 96, device=DEV)
+    out = _np(p.solve_from_gradient(_to_dev(gx), _to_dev(gy)))[0, 0]
+    ref = O.solve_from_gradient(gx.astype(np.float64), gy.astype(np.float64), p.M, p.N, p.pad)
+    assert _rel(out, ref) <= REL_F32 and np.abs(out - ref).max() <= MAXABS_F32
+    p.close()
+
+
+@pytest.mark.parametrize("H,W", [(2, 2), (3, 5), (7, 2), (17, 31), (33, 40), (100, 37), (129, 255), (300, 64)])
+def test_ragged_sizes_match_oracle(H, W):
+    rng = np.random.default_rng(H * 7 + W)
+    B, C = 2, 1
+    gx = rng.uniform(-0.1, 0.1, (B, C, H, W)).astype(np.float32)  # non-zero last row/col too
+    gy = rng.uniform(-0.1, 0.1, (B, C, H, W)).astype(np.float32)
+    p = gfc.Plan(H, W, C, B, device=DEV)
+    out = _np(p.solve_from_gradient(_to_dev(gx), _to_dev(gy)))
+    ref = O.solve_from_gradient_batch(gx.astype(np.float64), gy.astype(np.float64), p.M, p.N, p.pad)
+    scale = max(1.0, np.abs(ref).max())
+    assert _rel(out, ref) <= REL_F32
+    assert np.abs(out - ref).max() <= MAXABS_F32 * scale
+    p.close()
+
+
+def test_conservative_gradient_recovers_image_on_gpu():
+    rng = np.random.default_rng(21)
+    img, c = synth.constant_border_image(rng, 120, 90)
+    gx, gy = synth.forward_gradient(img)
+    p = gfc.Plan(120, 90, device=DEV)
+    out = _np(p.solve_from_gradient(_to_dev(gx), _to_dev(gy)))[0, 0]
+    assert _rel(out, img - c) <= REL_F32
+    p.close()
+
+
+def test_laplacian_entry_matches_oracle():
+    rng = np.random.default_rng(5)
+    H, W, B, C = 70, 45, 2, 3
+    lap = rng.standard_normal((B, C, H, W)).astype(np.float32) * 0.01
+    p = gfc.Plan(H, W, C, B, device=DEV)
+    out = _np(p.solve_from_laplacian(_to_dev(lap)))
+    ref = O.solve_from_laplacian_batch(lap.astype(np.float64), p.M, p.N, p.pad)
+    assert _rel(out, ref) <= REL_F32
+    p.close()
+
+
+def test_chunking_is_bitwise_invariant_and_deterministic():
+    H, W, B = 96, 80, 7
+    gx, gy = synth.perturbed_gradient_batch(batch=B, H=H, W=W, seed=77)
+    tx, ty = _to_dev(gx), _to_dev(gy)
+    outs = []
+    for chunk in (0, 1, 3):
+        p = gfc.Plan(H, W, 1, B, chunk=chunk, device=DEV)
+        outs.append(p.solve_from_gradient(tx, ty).clone())
+        outs.append(p.solve_from_gradient(tx, ty).clone())
+        p.close()
+    for o in outs[1:]:
+        assert torch.equal(o, outs[0])
+
+
+def test_full_size_batch_sampled_fields_match_oracle():
+    """801x1200, batch 100, one call as the benchmark times it; three fields checked in full."""
+    B, H, W = 100, 801, 1200
+    gx, gy = synth.perturbed_gradient_batch(batch=B, H=H, W=W)
+    p = gfc.Plan(H, W, 1, B, device=DEV)
+    out = p.solve_from_gradient(_to_dev(gx), _to_dev(gy))
+    torch.cuda.synchronize()
+    for b in (0, 57, 99):
+        ref = O.solve_from_gradient(gx[b, 0].astype(np.float64), gy[b, 0].astype(np.float64), p.M, p.N, p.pad)
+        got = _np(out[b, 0])
+        assert _rel(got, ref) <= REL_F32, b
+        assert np.abs(got - ref).max() <= MAXABS_F32, b
+    p.close()
+
+
+@pytest.mark.parametrize("dtype", [torch.float16, torch.bfloat16])
+def test_16bit_storage_matches_oracle_on_dequantised_inputs(dtype):
+    gx, gy, _ = synth.poisson_blend_batch(batch=1, C=3, H=160, W=224, patch=(60, 80), seed=5)
+    tx, ty = _to_dev(gx, dtype), _to_dev(gy, dtype)
+    p = gfc.Plan(160, 224, 3, 1, dtype, device=DEV)
+    out = _np(p.solve_from_gradient(tx, ty))
+    ref = O.solve_from_gradient_batch(_np(tx), _np(ty), p.M, p.N, p.pad)
+    assert _rel(out, ref) <= REL_16
+    p.close()
+
+
+# ---------------------------------------------------------------- adjoint
+
+@pytest.mark.parametrize("H,W,C,B", [(16, 16, 3, 2), (17, 9, 1, 1), (64, 96, 2, 1), (2, 3, 1, 1)])
+def test_backward_matches_oracle_adjoint(H, W, C, B):
+    gout = synth.upstream_gradient((B, C, H, W), seed=H + W)
+    p = gfc.Plan(H, W, C, B, device=DEV)
+    bx, by = p.backward(_to_dev(gout))
+    rx, ry = O.backward_batch(gout.astype(np.float64), p.M, p.N, p.pad)
+    assert _rel(_np(bx), rx) <= REL_F32
+    assert _rel(_np(by), ry) <= REL_F32
+    p.close()
+
+
+def test_autograd_layer_matches_oracle():
+    H, W, C, B = 20, 24, 2, 2
+    gx, gy = synth.feature_gradients(batch=B, C=C, H=H, W=W, seed=8)
+    tx = _to_dev(gx).requires_grad_(True)
+    ty = _to_dev(gy).requires_grad_(True)
+    out = gfc.gfc_layer(tx, ty)
+    gout = synth.upstream_gradient(out.shape, seed=9)
+    out.backward(_to_dev(gout))
+    M, N = gfc.padded_size(H, W)
+    ref_out = O.solve_from_gradient_batch(gx.astype(np.float64), gy.astype(np.float64), M, N, 4)
+    rx, ry = O.backward_batch(gout.astype(np.float64), M, N, 4)
+    assert _rel(_np(out.detach()), ref_out) <= REL_F32
+    assert _rel(_np(tx.grad), rx) <= REL_F32
+    assert _rel(_np(ty.grad), ry) <= REL_F32
+
+
+def test_adjoint_dot_product_identity_on_gpu():
+    H, W, C, B = 40, 33, 1, 3
+    rng = np.random.default_rng(12)
+    gx = _to_dev(rng.standard_normal((B, C, H, W)).astype(np.float32))
+    gy = _to_dev(rng.standard_normal((B, C, H, W)).astype(np.float32))
+    gout = _to_dev(rng.standard_normal((B, C, H, W)).astype(np.float32))
+    p = gfc.Plan(H, W, C, B, device=DEV)
+    y = p.solve_from_gradient(gx, gy)
+    bx, by = p.backward(gout)
+    lhs = float((y.double() * gout.double()).sum())
+    rhs = float((gx.double() * bx.double()).sum() + (gy.double() * by.double()).sum())
+    assert abs(lhs - rhs) <= 1e-5 * (abs(lhs) + abs(rhs) + 1.0)
+    p.close()
+
+
+def test_bad_tensor_arguments_raise():
+    p = gfc.Plan(16, 16, device=DEV)
+    x = torch.zeros((1, 1, 16, 16), device=DEV)
+    with pytest.raises(ValueError):
+        p.solve_from_gradient(x, x.half())
+    with pytest.raises(ValueError):
+        p.solve_from_gradient(x, torch.zeros((1, 1, 16, 15), device=DEV))
+    with pytest.raises(gfc.GFCError):
+        p.solve_from_gradient(x, x, out=x)  # out aliases an input
+    p.close()
