@@ -128,6 +128,36 @@ gfc_status gfc_backward(gfc_plan* plan, const void* grad_out, void* grad_gx, voi
  * (Eq. 17's F). */
 gfc_status gfc_fft_c2c(int n, int count, int dir, const void* in, void* out, void* stream);
 
+/* Solve from gradients held in HOST memory (Eq. 3, Eq. 23, Algorithm B), the
+ * same computation as gfc_solve_from_gradient with the transfers included:
+ * per chunk of fields, gx and gy are copied host-to-device, solved, and the
+ * result copied device-to-host, with the copies of one chunk overlapping the
+ * solve of the next (two staging buffers, two copy streams owned by the plan,
+ * allocated on the first call). gx, gy, out: [batch, C, H, W] host arrays in
+ * the plan's dtype; page-locked memory gives asynchronous, overlapped copies.
+ * Asynchronous on the plan's stream: `out` is complete once the plan's stream
+ * (or gfc_plan_sync) has completed. */
+gfc_status gfc_solve_from_gradient_host(gfc_plan* plan, const void* gx, const void* gy, void* out);
+
+/* Per-pass device time and launch counts, for tracing. pass index 0 = row
+ * pass (divergence + row transforms), 1 = column pass (column transforms and
+ * Green multiply), 2 = inverse row pass (offset, crop, cast), 3 = other. */
+typedef struct {
+  double pass_ms[4];  /* device time summed over launches (only while profiling is on) */
+  long launches[4];   /* kernel launches issued (always counted) */
+  long calls;         /* solve / backward calls */
+  long dropped;       /* launches not timed because the event pool was full */
+} gfc_profile;
+
+/* Turn per-launch CUDA-event timing on (enable != 0) or off. Events are
+ * recorded on the plan's stream around every kernel launch, from a pool of
+ * 65536 event pairs created here. Synchronous when turning on. */
+gfc_status gfc_plan_set_profiling(gfc_plan* plan, int enable);
+
+/* Synchronize the plan's stream and return the accumulated profile; reset != 0
+ * clears it afterwards. */
+gfc_status gfc_plan_get_profile(gfc_plan* plan, gfc_profile* out, int reset);
+
 /* Wait for the plan's stream and report any device-side error since the last
  * sync (GFC_ERR_TIMEOUT for a bounded wait that ran out, GFC_ERR_CUDA otherwise). */
 gfc_status gfc_plan_sync(gfc_plan* plan);

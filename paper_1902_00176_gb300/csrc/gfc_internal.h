@@ -28,6 +28,19 @@ struct gfc_plan {
   float2* spec;   // [chunk][M][ldS] complex spectrum scratch
   float* partial; // [chunk][kMaxRowBlocks] per-block sums (adjoint)
   int* dev_err;   // device error word
+  // host-buffer path (allocated on first use)
+  void* stage_in[2][2];   // [buffer][gx, gy] device staging for one chunk
+  void* stage_out[2];
+  cudaStream_t copy_in, copy_out;
+  cudaEvent_t ev_in[2], ev_comp[2], ev_out[2];
+  bool host_ready;
+  // tracing
+  gfc_profile prof;
+  bool profiling;
+  int ev_cap, ev_used;
+  cudaEvent_t* ev_start;
+  cudaEvent_t* ev_stop;
+  int* ev_pass;
 };
 
 namespace gfc {
@@ -48,6 +61,12 @@ cudaError_t build_twiddles(float2* tw, int n, cudaStream_t s);
 cudaError_t build_green(float* G, int M, int N, int Nh, cudaStream_t s);
 
 inline size_t dtype_size(gfc_dtype d) { return d == GFC_F32 ? 4 : 2; }
+
+// tracing around one kernel launch on the plan's stream
+void prof_begin(gfc_plan* P, int pass);
+void prof_end(gfc_plan* P);
+// free the host-buffer pipeline and the profiling event pool (plan teardown)
+void release_host_state(gfc_plan* P);
 
 }  // namespace gfc
 

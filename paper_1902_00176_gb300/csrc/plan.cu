@@ -245,6 +245,7 @@ gfc_status gfc_plan_sync(gfc_plan* plan) {
 
 static void destroy_plan(gfc_plan* p) {
   if (!p) return;
+  release_host_state(p);
   cudaFree(p->G);
   cudaFree(p->twN);
   cudaFree(p->twM);

@@ -18,6 +18,8 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
+#include <stdlib.h>
+#include <string.h>
 
 #include "gfc_internal.h"
 
@@ -290,6 +292,32 @@ __global__ void __launch_bounds__(256) k_fft_rows(const float2* __restrict__ in,
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
+// Raise a kernel's dynamic shared-memory limit once per size it is launched with.
+template <typename K>
+static cudaError_t ensure_smem(K kernel, size_t smem, int* done) {
+  if ((int)smem <= *done) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess) *done = (int)smem;
+  return e;
+}
+
+void prof_begin(gfc_plan* P, int pass) {
+  P->prof.launches[pass] += 1;
+  if (!P->profiling) return;
+  if (P->ev_used >= P->ev_cap) {
+    P->prof.dropped += 1;
+    return;
+  }
+  P->ev_pass[P->ev_used] = pass;
+  cudaEventRecord(P->ev_start[P->ev_used], P->stream);
+}
+
+void prof_end(gfc_plan* P) {
+  if (!P->profiling || P->ev_used >= P->ev_cap) return;
+  cudaEventRecord(P->ev_stop[P->ev_used], P->stream);
+  P->ev_used += 1;
+}
+
 static int pick_strip(int M) {
   // columns per pass-B block: largest power of two with (M + 2 M S) * 8 B <= 200 KB
   for (int S = 8; S > 1; S >>= 1)
@@ -308,17 +336,20 @@ static PassArgs base_args(const gfc_plan* P) {
 static int ceil_div(int a, int b) { return (a + b - 1) / b; }
 
 template <int S, int MODE>
-static cudaError_t launch_b(const gfc_plan* P, PassArgs B, int nf, cudaStream_t st) {
+static cudaError_t launch_b(gfc_plan* P, PassArgs B, int nf, cudaStream_t st) {
+  static int done = 0;
   const size_t smem = (size_t)(P->M + 2 * (size_t)P->M * S) * sizeof(float2);
   auto k = k_pass_b<S, MODE>;
-  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = ensure_smem(k, smem, &done);
   if (e != cudaSuccess) return e;
+  prof_begin(P, 1);
   k<<<dim3(ceil_div(P->Nh, S), nf), 256, smem, st>>>(P->spec, P->G, P->twM, P->partial, B);
+  prof_end(P);
   return cudaGetLastError();
 }
 
 template <int MODE>
-static cudaError_t launch_b_any(const gfc_plan* P, PassArgs B, int nf, cudaStream_t st) {
+static cudaError_t launch_b_any(gfc_plan* P, PassArgs B, int nf, cudaStream_t st) {
   switch (pick_strip(P->M)) {
     case 8: return launch_b<8, MODE>(P, B, nf, st);
     case 4: return launch_b<4, MODE>(P, B, nf, st);
@@ -328,8 +359,7 @@ static cudaError_t launch_b_any(const gfc_plan* P, PassArgs B, int nf, cudaStrea
 }
 
 template <typename T, int MODE>
-static cudaError_t run_chunk(const gfc_plan* P, const T* in0, const T* in1, T* out0, T* out1, int nf) {
-  cudaStream_t st = P->stream;
+static cudaError_t run_chunk(gfc_plan* P, const T* in0, const T* in1, T* out0, T* out1, int nf, cudaStream_t st) {
   // pass A
   PassArgs A = base_args(P);
   A.nrows = (MODE == kGrad) ? P->H + 1 : P->H;
@@ -338,36 +368,41 @@ static cudaError_t run_chunk(const gfc_plan* P, const T* in0, const T* in1, T* o
   A.ppb = 4;
   if (ceil_div(A.pairs, A.ppb) > kMaxRowBlocks) A.ppb = ceil_div(A.pairs, kMaxRowBlocks);
   A.nparts = ceil_div(A.pairs, A.ppb);
+  cudaError_t e;
   {
+    static int done = 0;
     const size_t smem = 3 * (size_t)P->N * sizeof(float2);
     auto k = k_pass_a<T, MODE>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
+    if ((e = ensure_smem(k, smem, &done)) != cudaSuccess) return e;
+    prof_begin(P, 0);
     k<<<dim3(A.nparts, nf), 256, smem, st>>>(in0, in1, P->spec, P->partial, P->twN, A);
+    prof_end(P);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   // pass B
   PassArgs B = A;
   B.plan = P->colplan;
-  cudaError_t e = launch_b_any<MODE>(P, B, nf, st);
-  if (e != cudaSuccess) return e;
+  if ((e = launch_b_any<MODE>(P, B, nf, st)) != cudaSuccess) return e;
   // pass C
   PassArgs C = base_args(P);
   C.ppb = 4;
+  C.pairs = ceil_div(P->H, 2);
   if (MODE == kAdj) {
-    C.pairs = ceil_div(P->H, 2);  // output row pairs
+    static int done = 0;
     const size_t smem = 3 * (size_t)P->N * sizeof(float2) + (size_t)P->W * sizeof(float);
     auto k = k_pass_c_adj<T>;
-    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
+    if ((e = ensure_smem(k, smem, &done)) != cudaSuccess) return e;
+    prof_begin(P, 2);
     k<<<dim3(ceil_div(C.pairs, C.ppb), nf), 256, smem, st>>>(P->spec, out0, out1, P->twN, C);
+    prof_end(P);
   } else {
-    C.pairs = ceil_div(P->H, 2);
+    static int done = 0;
     const size_t smem = 3 * (size_t)P->N * sizeof(float2);
     auto k = k_pass_c<T>;
-    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
+    if ((e = ensure_smem(k, smem, &done)) != cudaSuccess) return e;
+    prof_begin(P, 2);
     k<<<dim3(ceil_div(C.pairs, C.ppb), nf), 256, smem, st>>>(P->spec, out0, P->twN, C);
+    prof_end(P);
   }
   return cudaGetLastError();
 }
@@ -376,13 +411,14 @@ template <typename T, int MODE>
 static gfc_status run_all(gfc_plan* P, const void* a, const void* b, void* o0, void* o1) {
   const long fields = (long)P->batch * P->C;
   const size_t fe = (size_t)P->H * P->W;
+  P->prof.calls += 1;
   for (long f0 = 0; f0 < fields; f0 += P->chunk) {
     const int nf = (int)((fields - f0 < P->chunk) ? fields - f0 : P->chunk);
     const T* in0 = static_cast<const T*>(a) + f0 * fe;
     const T* in1 = b ? static_cast<const T*>(b) + f0 * fe : nullptr;
     T* out0 = static_cast<T*>(o0) + f0 * fe;
     T* out1 = o1 ? static_cast<T*>(o1) + f0 * fe : nullptr;
-    cudaError_t e = run_chunk<T, MODE>(P, in0, in1, out0, out1, nf);
+    cudaError_t e = run_chunk<T, MODE>(P, in0, in1, out0, out1, nf, P->stream);
     if (e != cudaSuccess) return cuda_fail(e, "gfc solve launch");
   }
   return GFC_OK;
@@ -398,6 +434,96 @@ static gfc_status dispatch(gfc_plan* P, const void* a, const void* b, void* o0, 
 }
 
 static bool misaligned(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) != 0; }
+
+// Host-buffer pipeline: chunk c uses staging buffer c % 2. copy_in waits until
+// the solve of chunk c-2 has consumed that buffer's inputs, the compute stream
+// waits for the inputs and for the copy-out of chunk c-2 to free the output
+// buffer, copy_out waits for the solve.
+static gfc_status host_setup(gfc_plan* P) {
+  if (P->host_ready) return GFC_OK;
+  const size_t bytes = (size_t)P->chunk * P->H * P->W * dtype_size(P->dtype);
+  for (int b = 0; b < 2; ++b) {
+    GFC_CUDA_TRY(cudaMalloc(&P->stage_in[b][0], bytes));
+    GFC_CUDA_TRY(cudaMalloc(&P->stage_in[b][1], bytes));
+    GFC_CUDA_TRY(cudaMalloc(&P->stage_out[b], bytes));
+    GFC_CUDA_TRY(cudaEventCreateWithFlags(&P->ev_in[b], cudaEventDisableTiming));
+    GFC_CUDA_TRY(cudaEventCreateWithFlags(&P->ev_comp[b], cudaEventDisableTiming));
+    GFC_CUDA_TRY(cudaEventCreateWithFlags(&P->ev_out[b], cudaEventDisableTiming));
+  }
+  GFC_CUDA_TRY(cudaStreamCreateWithFlags(&P->copy_in, cudaStreamNonBlocking));
+  GFC_CUDA_TRY(cudaStreamCreateWithFlags(&P->copy_out, cudaStreamNonBlocking));
+  P->host_ready = true;
+  return GFC_OK;
+}
+
+template <typename T>
+static gfc_status run_host(gfc_plan* P, const void* gx, const void* gy, void* out) {
+  gfc_status st = host_setup(P);
+  if (st != GFC_OK) return st;
+  const long fields = (long)P->batch * P->C;
+  const size_t fe = (size_t)P->H * P->W;
+  cudaStream_t cs = P->stream;
+  // the copy streams start after everything already queued on the plan's stream
+  cudaEvent_t start = P->ev_comp[1];
+  GFC_CUDA_TRY(cudaEventRecord(start, cs));
+  GFC_CUDA_TRY(cudaStreamWaitEvent(P->copy_in, start, 0));
+  GFC_CUDA_TRY(cudaStreamWaitEvent(P->copy_out, start, 0));
+  P->prof.calls += 1;
+  long c = 0;
+  for (long f0 = 0; f0 < fields; f0 += P->chunk, ++c) {
+    const int b = (int)(c & 1);
+    const int nf = (int)((fields - f0 < P->chunk) ? fields - f0 : P->chunk);
+    const size_t bytes = (size_t)nf * fe * sizeof(T);
+    if (c >= 2) GFC_CUDA_TRY(cudaStreamWaitEvent(P->copy_in, P->ev_comp[b], 0));
+    GFC_CUDA_TRY(cudaMemcpyAsync(P->stage_in[b][0], static_cast<const T*>(gx) + f0 * fe, bytes,
+                                 cudaMemcpyHostToDevice, P->copy_in));
+    GFC_CUDA_TRY(cudaMemcpyAsync(P->stage_in[b][1], static_cast<const T*>(gy) + f0 * fe, bytes,
+                                 cudaMemcpyHostToDevice, P->copy_in));
+    GFC_CUDA_TRY(cudaEventRecord(P->ev_in[b], P->copy_in));
+    GFC_CUDA_TRY(cudaStreamWaitEvent(cs, P->ev_in[b], 0));
+    if (c >= 2) GFC_CUDA_TRY(cudaStreamWaitEvent(cs, P->ev_out[b], 0));
+    cudaError_t e = run_chunk<T, kGrad>(P, static_cast<const T*>(P->stage_in[b][0]),
+                                        static_cast<const T*>(P->stage_in[b][1]), static_cast<T*>(P->stage_out[b]),
+                                        nullptr, nf, cs);
+    if (e != cudaSuccess) return cuda_fail(e, "gfc host solve launch");
+    GFC_CUDA_TRY(cudaEventRecord(P->ev_comp[b], cs));
+    GFC_CUDA_TRY(cudaStreamWaitEvent(P->copy_out, P->ev_comp[b], 0));
+    GFC_CUDA_TRY(cudaMemcpyAsync(static_cast<T*>(out) + f0 * fe, P->stage_out[b], bytes, cudaMemcpyDeviceToHost,
+                                 P->copy_out));
+    GFC_CUDA_TRY(cudaEventRecord(P->ev_out[b], P->copy_out));
+  }
+  // the plan's stream completes only after the last copy-out
+  const int last = (int)((c - 1) & 1);
+  GFC_CUDA_TRY(cudaStreamWaitEvent(cs, P->ev_out[last], 0));
+  if (c >= 2) GFC_CUDA_TRY(cudaStreamWaitEvent(cs, P->ev_out[last ^ 1], 0));
+  return GFC_OK;
+}
+
+void release_host_state(gfc_plan* P) {
+  if (P->host_ready) {
+    for (int b = 0; b < 2; ++b) {
+      cudaFree(P->stage_in[b][0]);
+      cudaFree(P->stage_in[b][1]);
+      cudaFree(P->stage_out[b]);
+      cudaEventDestroy(P->ev_in[b]);
+      cudaEventDestroy(P->ev_comp[b]);
+      cudaEventDestroy(P->ev_out[b]);
+    }
+    cudaStreamDestroy(P->copy_in);
+    cudaStreamDestroy(P->copy_out);
+    P->host_ready = false;
+  }
+  if (P->ev_cap) {
+    for (int i = 0; i < P->ev_cap; ++i) {
+      cudaEventDestroy(P->ev_start[i]);
+      cudaEventDestroy(P->ev_stop[i]);
+    }
+    free(P->ev_start);
+    free(P->ev_stop);
+    free(P->ev_pass);
+    P->ev_cap = P->ev_used = 0;
+  }
+}
 
 }  // namespace gfc
 
@@ -431,6 +557,52 @@ gfc_status gfc_backward(gfc_plan* plan, const void* grad_out, void* grad_gx, voi
   if (grad_gx == grad_gy || grad_gx == grad_out || grad_gy == grad_out)
     return fail(GFC_ERR_INVALID_ARG, "gfc_backward: arguments alias");
   return dispatch<kAdj>(plan, grad_out, nullptr, grad_gx, grad_gy);
+}
+
+gfc_status gfc_solve_from_gradient_host(gfc_plan* plan, const void* gx, const void* gy, void* out) {
+  clear_error();
+  if (!plan || !gx || !gy || !out) return fail(GFC_ERR_INVALID_ARG, "gfc_solve_from_gradient_host: null argument");
+  if (out == gx || out == gy) return fail(GFC_ERR_INVALID_ARG, "gfc_solve_from_gradient_host: out aliases an input");
+  switch (plan->dtype) {
+    case GFC_F32: return run_host<float>(plan, gx, gy, out);
+    case GFC_F16: return run_host<__half>(plan, gx, gy, out);
+    default: return run_host<__nv_bfloat16>(plan, gx, gy, out);
+  }
+}
+
+gfc_status gfc_plan_set_profiling(gfc_plan* plan, int enable) {
+  clear_error();
+  if (!plan) return fail(GFC_ERR_INVALID_ARG, "gfc_plan_set_profiling: null plan");
+  if (enable && plan->ev_cap == 0) {
+    const int cap = 65536;
+    plan->ev_start = (cudaEvent_t*)calloc(cap, sizeof(cudaEvent_t));
+    plan->ev_stop = (cudaEvent_t*)calloc(cap, sizeof(cudaEvent_t));
+    plan->ev_pass = (int*)calloc(cap, sizeof(int));
+    if (!plan->ev_start || !plan->ev_stop || !plan->ev_pass)
+      return fail(GFC_ERR_ALLOC, "gfc_plan_set_profiling: host allocation failed");
+    for (int i = 0; i < cap; ++i) {
+      GFC_CUDA_TRY(cudaEventCreate(&plan->ev_start[i]));
+      GFC_CUDA_TRY(cudaEventCreate(&plan->ev_stop[i]));
+      plan->ev_cap = i + 1;
+    }
+  }
+  plan->profiling = enable != 0;
+  return GFC_OK;
+}
+
+gfc_status gfc_plan_get_profile(gfc_plan* plan, gfc_profile* out, int reset) {
+  clear_error();
+  if (!plan || !out) return fail(GFC_ERR_INVALID_ARG, "gfc_plan_get_profile: null argument");
+  GFC_CUDA_TRY(cudaStreamSynchronize(plan->stream));
+  for (int i = 0; i < plan->ev_used; ++i) {
+    float ms = 0.0f;
+    GFC_CUDA_TRY(cudaEventElapsedTime(&ms, plan->ev_start[i], plan->ev_stop[i]));
+    if (plan->ev_pass[i] >= 0) plan->prof.pass_ms[plan->ev_pass[i]] += ms;
+  }
+  plan->ev_used = 0;
+  *out = plan->prof;
+  if (reset) memset(&plan->prof, 0, sizeof(plan->prof));
+  return GFC_OK;
 }
 
 gfc_status gfc_fft_c2c(int n, int count, int dir, const void* in, void* out, void* stream) {

@@ -40,6 +40,16 @@ class _Opts(ctypes.Structure):
                 ("chunk", ctypes.c_int), ("stream", ctypes.c_void_p)]
 
 
+class Profile(ctypes.Structure):
+    """Mirror of gfc_profile: per-pass device time (ms) and launch counts."""
+    _fields_ = [("pass_ms", ctypes.c_double * 4), ("launches", ctypes.c_long * 4), ("calls", ctypes.c_long),
+                ("dropped", ctypes.c_long)]
+
+    def as_dict(self):
+        return {"pass_ms": list(self.pass_ms), "launches": list(self.launches), "calls": self.calls,
+                "dropped": self.dropped}
+
+
 _lib = None
 _lib_lock = threading.Lock()
 
@@ -58,6 +68,9 @@ _SIGNATURES = {
     "gfc_solve_from_laplacian": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
     "gfc_backward": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
     "gfc_fft_c2c": [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
+    "gfc_solve_from_gradient_host": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
+    "gfc_plan_set_profiling": [ctypes.c_void_p, ctypes.c_int],
+    "gfc_plan_get_profile": [ctypes.c_void_p, ctypes.POINTER(Profile), ctypes.c_int],
     "gfc_plan_sync": [ctypes.c_void_p],
     "gfc_destroy": [ctypes.c_void_p],
     "gfc_last_error": [],
@@ -182,6 +195,28 @@ class Plan:
         self._bind_stream()
         _check(lib().gfc_backward(self._h, grad_out.data_ptr(), grad_gx.data_ptr(), grad_gy.data_ptr()))
         return grad_gx, grad_gy
+
+    def solve_from_gradient_host(self, gx, gy, out):
+        """Host-memory solve through the C ABI: CPU tensors (pinned for overlap), result in ``out``.
+        Asynchronous on the current stream; synchronize before reading ``out``."""
+        for t, n in ((gx, "gx"), (gy, "gy"), (out, "out")):
+            if t.is_cuda or t.dtype != self.dtype or not t.is_contiguous() or \
+                    t.numel() != self.batch * self.C * self.H * self.W:
+                raise ValueError(f"{n} must be a contiguous CPU tensor of {self.batch}x{self.C}x{self.H}x{self.W} "
+                                 f"{self.dtype}")
+        self._bind_stream()
+        _check(lib().gfc_solve_from_gradient_host(self._h, gx.data_ptr(), gy.data_ptr(), out.data_ptr()))
+        return out
+
+    def set_profiling(self, enable: bool = True):
+        _check(lib().gfc_plan_set_profiling(self._h, 1 if enable else 0))
+
+    def profile(self, reset: bool = True) -> dict:
+        """Synchronize and return accumulated per-pass times and launch counts."""
+        pr = Profile()
+        self._bind_stream()
+        _check(lib().gfc_plan_get_profile(self._h, ctypes.byref(pr), 1 if reset else 0))
+        return pr.as_dict()
 
     def green(self):
         """The plan's FP32 Green spectrum, M x (N/2+1), as a CPU tensor (1/(MN) folded in)."""
