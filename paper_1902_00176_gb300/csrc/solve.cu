@@ -21,6 +21,8 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <mutex>
+
 #include "gfc_internal.h"
 
 namespace gfc {
@@ -292,13 +294,34 @@ __global__ void __launch_bounds__(256) k_fft_rows(const float2* __restrict__ in,
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
-// Raise a kernel's dynamic shared-memory limit once per size it is launched with.
+// Raise a kernel's dynamic shared-memory cap to at least `smem`. The cap is
+// tracked per kernel function (several launch sites share a kernel) and is
+// never lowered, since a launch above the current cap is rejected.
+struct SmemCap {
+  const void* fn;
+  int bytes;
+};
+static SmemCap g_smem_caps[256];
+static int g_smem_ncaps = 0;
+static std::mutex g_smem_mu;
+
 template <typename K>
-static cudaError_t ensure_smem(K kernel, size_t smem, int* done) {
-  if ((int)smem <= *done) return cudaSuccess;
+static cudaError_t ensure_smem(K kernel, size_t smem) {
+  const void* fn = reinterpret_cast<const void*>(kernel);
+  std::lock_guard<std::mutex> lock(g_smem_mu);
+  int i = 0;
+  for (; i < g_smem_ncaps; ++i)
+    if (g_smem_caps[i].fn == fn) break;
+  if (i < g_smem_ncaps && (int)smem <= g_smem_caps[i].bytes) return cudaSuccess;
   cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e == cudaSuccess) *done = (int)smem;
-  return e;
+  if (e != cudaSuccess) return e;
+  if (i == g_smem_ncaps) {
+    if (g_smem_ncaps == 256) return cudaSuccess;  // table full: the attribute is still set for this launch
+    g_smem_caps[g_smem_ncaps++] = SmemCap{fn, (int)smem};
+  } else {
+    g_smem_caps[i].bytes = (int)smem;
+  }
+  return cudaSuccess;
 }
 
 void prof_begin(gfc_plan* P, int pass) {
@@ -337,10 +360,9 @@ static int ceil_div(int a, int b) { return (a + b - 1) / b; }
 
 template <int S, int MODE>
 static cudaError_t launch_b(gfc_plan* P, PassArgs B, int nf, cudaStream_t st) {
-  static int done = 0;
   const size_t smem = (size_t)(P->M + 2 * (size_t)P->M * S) * sizeof(float2);
   auto k = k_pass_b<S, MODE>;
-  cudaError_t e = ensure_smem(k, smem, &done);
+  cudaError_t e = ensure_smem(k, smem);
   if (e != cudaSuccess) return e;
   prof_begin(P, 1);
   k<<<dim3(ceil_div(P->Nh, S), nf), 256, smem, st>>>(P->spec, P->G, P->twM, P->partial, B);
@@ -370,10 +392,9 @@ static cudaError_t run_chunk(gfc_plan* P, const T* in0, const T* in1, T* out0, T
   A.nparts = ceil_div(A.pairs, A.ppb);
   cudaError_t e;
   {
-    static int done = 0;
-    const size_t smem = 3 * (size_t)P->N * sizeof(float2);
+      const size_t smem = 3 * (size_t)P->N * sizeof(float2);
     auto k = k_pass_a<T, MODE>;
-    if ((e = ensure_smem(k, smem, &done)) != cudaSuccess) return e;
+    if ((e = ensure_smem(k, smem)) != cudaSuccess) return e;
     prof_begin(P, 0);
     k<<<dim3(A.nparts, nf), 256, smem, st>>>(in0, in1, P->spec, P->partial, P->twN, A);
     prof_end(P);
@@ -388,18 +409,16 @@ static cudaError_t run_chunk(gfc_plan* P, const T* in0, const T* in1, T* out0, T
   C.ppb = 4;
   C.pairs = ceil_div(P->H, 2);
   if (MODE == kAdj) {
-    static int done = 0;
-    const size_t smem = 3 * (size_t)P->N * sizeof(float2) + (size_t)P->W * sizeof(float);
+      const size_t smem = 3 * (size_t)P->N * sizeof(float2) + (size_t)P->W * sizeof(float);
     auto k = k_pass_c_adj<T>;
-    if ((e = ensure_smem(k, smem, &done)) != cudaSuccess) return e;
+    if ((e = ensure_smem(k, smem)) != cudaSuccess) return e;
     prof_begin(P, 2);
     k<<<dim3(ceil_div(C.pairs, C.ppb), nf), 256, smem, st>>>(P->spec, out0, out1, P->twN, C);
     prof_end(P);
   } else {
-    static int done = 0;
-    const size_t smem = 3 * (size_t)P->N * sizeof(float2);
+      const size_t smem = 3 * (size_t)P->N * sizeof(float2);
     auto k = k_pass_c<T>;
-    if ((e = ensure_smem(k, smem, &done)) != cudaSuccess) return e;
+    if ((e = ensure_smem(k, smem)) != cudaSuccess) return e;
     prof_begin(P, 2);
     k<<<dim3(ceil_div(C.pairs, C.ppb), nf), 256, smem, st>>>(P->spec, out0, P->twN, C);
     prof_end(P);
@@ -616,10 +635,10 @@ gfc_status gfc_fft_c2c(int n, int count, int dir, const void* in, void* out, voi
   const size_t smem = 3 * (size_t)n * sizeof(float2);
   cudaStream_t st = (cudaStream_t)stream;
   if (dir < 0) {
-    GFC_CUDA_TRY(cudaFuncSetAttribute(k_fft_rows<-1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    GFC_CUDA_TRY(ensure_smem(k_fft_rows<-1>, smem));
     k_fft_rows<-1><<<count, 256, smem, st>>>((const float2*)in, (float2*)out, pl);
   } else {
-    GFC_CUDA_TRY(cudaFuncSetAttribute(k_fft_rows<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    GFC_CUDA_TRY(ensure_smem(k_fft_rows<1>, smem));
     k_fft_rows<1><<<count, 256, smem, st>>>((const float2*)in, (float2*)out, pl);
   }
   GFC_CUDA_TRY(cudaGetLastError());

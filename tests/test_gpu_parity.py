@@ -123,6 +123,23 @@ def test_laplacian_entry_matches_oracle():
     p.close()
 
 
+def test_modes_and_sizes_sharing_a_kernel_can_alternate():
+    """The row-inverse kernel serves gradient and Laplacian solves; a small launch of one
+    mode must not leave the kernel unable to run a larger launch of the other."""
+    rng = np.random.default_rng(3)
+    for (H, W, mode) in [(300, 700, "grad"), (20, 30, "lap"), (96, 80, "grad"), (500, 900, "lap")]:
+        a = rng.uniform(-0.1, 0.1, (1, 1, H, W)).astype(np.float32)
+        p = gfc.Plan(H, W, device=DEV)
+        if mode == "grad":
+            out = _np(p.solve_from_gradient(_to_dev(a), _to_dev(a[..., ::-1].copy())))
+            ref = O.solve_from_gradient_batch(a.astype(np.float64), a[..., ::-1].astype(np.float64), p.M, p.N, p.pad)
+        else:
+            out = _np(p.solve_from_laplacian(_to_dev(a)))
+            ref = O.solve_from_laplacian_batch(a.astype(np.float64), p.M, p.N, p.pad)
+        assert _rel(out, ref) <= REL_F32
+        p.close()
+
+
 def test_chunking_is_bitwise_invariant_and_deterministic():
     H, W, B = 96, 80, 7
     gx, gy = synth.perturbed_gradient_batch(batch=B, H=H, W=W, seed=77)
