@@ -158,6 +158,28 @@ gfc_status gfc_plan_set_profiling(gfc_plan* plan, int enable);
  * clears it afterwards. */
 gfc_status gfc_plan_get_profile(gfc_plan* plan, gfc_profile* out, int reset);
 
+/* Allocation-free solve from gradients, for callers that cannot allocate
+ * device memory: plug-ins whose host application owns all device memory,
+ * fixed-budget real-time or embedded pipelines, and latency-bound loops where
+ * cudaMalloc/cudaFree would synchronise the device. The paper has no
+ * counterpart; it computes exactly what gfc_solve_from_gradient computes for
+ * FP32 storage, pad 4 and the SMOOTH size policy, without a plan.
+ * gx, gy, out: `fields` contiguous H x W FP32 fields in device memory (the
+ * caller still owns inputs and outputs), 16-byte aligned; runs on `stream`
+ * (cudaStream_t), asynchronously, one field at a time.
+ * Working memory is one library-owned static device array of about 24 MiB that
+ * every GPU loading this library holds until the process exits. It limits the
+ * padded size to M x (N/2+1) <= 2^21 (about 2040 x 2040 images); larger sizes
+ * return GFC_ERR_UNSUPPORTED. The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress, which may load the module), so make
+ * that first call before any stream capture. Every call rebuilds the Green
+ * spectrum and twiddle tables in the array and clears its error word; all
+ * calls share the array, so calls that overlap on the GPU (other streams,
+ * other threads) race and must be serialised by the caller. Calls no
+ * cudaMalloc, cudaFree or allocating library routine. */
+gfc_status gfc_solve_from_gradient_noalloc(int H, int W, int fields, const void* gx, const void* gy, void* out,
+                                           void* stream);
+
 /* Wait for the plan's stream and report any device-side error since the last
  * sync (GFC_ERR_TIMEOUT for a bounded wait that ran out, GFC_ERR_CUDA otherwise). */
 gfc_status gfc_plan_sync(gfc_plan* plan);

@@ -646,3 +646,109 @@ gfc_status gfc_fft_c2c(int n, int count, int dir, const void* in, void* out, voi
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free entry point.
+//
+// Some callers cannot allocate device memory at all: plug-ins inside a host
+// application that owns every device allocation, fixed-budget embedded or
+// real-time pipelines whose memory is reserved at start-up, and latency-bound
+// loops where cudaMalloc/cudaFree would implicitly synchronise the device and
+// stall other streams. They cannot create a plan (a plan allocates its tables
+// and scratch), so this entry point takes its working memory from one
+// file-scope device array instead. The array is created with the module on
+// every GPU that loads this library and lives until the process exits.
+//
+// Layout of the array (each region 256-byte aligned): the complex spectrum of
+// ONE field (M x ldS <= kNoAllocSpecElems), the Green spectrum
+// (M x (N/2+1) <= kNoAllocGreenElems floats), the two twiddle tables, the
+// adjoint partial sums and an error word.
+// ---------------------------------------------------------------------------
+namespace gfc {
+
+constexpr size_t kNoAllocSpecElems = size_t(1) << 21;   // complex64: 16 MiB
+constexpr size_t kNoAllocGreenElems = size_t(1) << 21;  // float: 8 MiB
+constexpr size_t kOffSpec = 0;
+constexpr size_t kOffGreen = kOffSpec + kNoAllocSpecElems * sizeof(float2);
+constexpr size_t kOffTwN = kOffGreen + kNoAllocGreenElems * sizeof(float);
+constexpr size_t kOffTwM = kOffTwN + size_t(kMaxFftLen) * sizeof(float2);
+constexpr size_t kOffPartial = kOffTwM + size_t(kMaxFftLen) * sizeof(float2);
+constexpr size_t kOffErr = kOffPartial + size_t(kMaxRowBlocks) * sizeof(float);
+constexpr size_t kNoAllocBytes = kOffErr + 256;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+constexpr int kNoAllocMaxDevices = 64;
+static void* g_noalloc_base[kNoAllocMaxDevices];
+
+// Device address of g_noalloc_scratch on the current device, looked up once
+// per device (the host-side name of the array is only a stand-in; kernels must
+// be given this address).
+static gfc_status noalloc_base(void** out) {
+  int dev = 0;
+  GFC_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kNoAllocMaxDevices)
+    return fail(GFC_ERR_UNSUPPORTED, "gfc_solve_from_gradient_noalloc: device %d out of range", dev);
+  if (!g_noalloc_base[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "gfc_solve_from_gradient_noalloc: cudaGetSymbolAddress");
+    g_noalloc_base[dev] = p;
+  }
+  *out = g_noalloc_base[dev];
+  return GFC_OK;
+}
+
+}  // namespace gfc
+
+extern "C" gfc_status gfc_solve_from_gradient_noalloc(int H, int W, int fields, const void* gx, const void* gy,
+                                                      void* out, void* stream) {
+  clear_error();
+  if (!gx || !gy || !out || fields < 0)
+    return fail(GFC_ERR_INVALID_ARG, "gfc_solve_from_gradient_noalloc: null pointer or fields < 0");
+  if (misaligned(gx) || misaligned(gy) || misaligned(out))
+    return fail(GFC_ERR_INVALID_ARG, "gfc_solve_from_gradient_noalloc: pointers must be 16-byte aligned");
+  if (out == gx || out == gy) return fail(GFC_ERR_INVALID_ARG, "gfc_solve_from_gradient_noalloc: out aliases an input");
+  int M = 0, N = 0;
+  gfc_status st = gfc_padded_size(H, W, 4, GFC_SIZE_SMOOTH, &M, &N);
+  if (st != GFC_OK) return st;
+  gfc_plan P;
+  memset(&P, 0, sizeof(P));
+  P.H = H; P.W = W; P.C = 1; P.batch = fields; P.pad = 4; P.dtype = GFC_F32;
+  P.M = M; P.N = N; P.Nh = N / 2 + 1; P.ldS = (P.Nh + 3) & ~3; P.chunk = 1;
+  if ((size_t)M * P.ldS > kNoAllocSpecElems || (size_t)M * P.Nh > kNoAllocGreenElems)
+    return fail(GFC_ERR_UNSUPPORTED,
+                "gfc_solve_from_gradient_noalloc: padded size %dx%d needs %zu spectrum elements, the static "
+                "scratch holds %zu (about 2040x2040 images at most)",
+                M, N, (size_t)M * P.ldS, kNoAllocSpecElems);
+  if (!make_fft_plan(N, &P.rowplan) || !make_fft_plan(M, &P.colplan))
+    return fail(GFC_ERR_UNSUPPORTED, "gfc_solve_from_gradient_noalloc: no FFT schedule for %dx%d", M, N);
+  if (fields == 0) return GFC_OK;
+  void* base = nullptr;
+  if ((st = noalloc_base(&base)) != GFC_OK) return st;
+  unsigned char* b = static_cast<unsigned char*>(base);
+  P.spec = reinterpret_cast<float2*>(b + kOffSpec);
+  P.G = reinterpret_cast<float*>(b + kOffGreen);
+  P.twN = reinterpret_cast<float2*>(b + kOffTwN);
+  P.twM = reinterpret_cast<float2*>(b + kOffTwM);
+  P.partial = reinterpret_cast<float*>(b + kOffPartial);
+  P.dev_err = reinterpret_cast<int*>(b + kOffErr);
+  P.stream = (cudaStream_t)stream;
+  GFC_CUDA_TRY(cudaGetDevice(&P.device));
+  // The tables are rebuilt on every call (the array keeps whatever the last
+  // call, possibly of another size, left in it); the error word is cleared.
+  // Nothing else needs to start at zero: every spectrum row a pass reads was
+  // written by the previous pass of the same field.
+  GFC_CUDA_TRY(cudaMemsetAsync(P.dev_err, 0, sizeof(int), P.stream));
+  GFC_CUDA_TRY(build_twiddles(P.twN, N, P.stream));
+  GFC_CUDA_TRY(build_twiddles(P.twM, M, P.stream));
+  GFC_CUDA_TRY(build_green(P.G, M, N, P.Nh, P.stream));
+  const size_t fe = (size_t)H * W;
+  for (int f = 0; f < fields; ++f) {
+    cudaError_t e = run_chunk<float, kGrad>(&P, static_cast<const float*>(gx) + f * fe,
+                                            static_cast<const float*>(gy) + f * fe, static_cast<float*>(out) + f * fe,
+                                            nullptr, 1, P.stream);
+    if (e != cudaSuccess) return cuda_fail(e, "gfc_solve_from_gradient_noalloc launch");
+  }
+  return GFC_OK;
+}

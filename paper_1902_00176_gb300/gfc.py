@@ -71,6 +71,8 @@ _SIGNATURES = {
     "gfc_solve_from_gradient_host": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
     "gfc_plan_set_profiling": [ctypes.c_void_p, ctypes.c_int],
     "gfc_plan_get_profile": [ctypes.c_void_p, ctypes.POINTER(Profile), ctypes.c_int],
+    "gfc_solve_from_gradient_noalloc": [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_void_p, ctypes.c_void_p],
     "gfc_plan_sync": [ctypes.c_void_p],
     "gfc_destroy": [ctypes.c_void_p],
     "gfc_last_error": [],
@@ -255,6 +257,18 @@ def solve_laplacian(lap: torch.Tensor) -> torch.Tensor:
     b = _as_bchw(lap)
     p = get_plan(b.shape[2], b.shape[3], b.shape[1], b.shape[0], lap.dtype, lap.device)
     return p.solve_from_laplacian(lap).view(lap.shape)
+
+
+def solve_noalloc(gx: torch.Tensor, gy: torch.Tensor, out: torch.Tensor) -> torch.Tensor:
+    """FP32 solve through the allocation-free entry point (no plan; ``out`` preallocated by the caller)."""
+    b = _as_bchw(gx)
+    for t in (gx, gy, out):
+        if not t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous() or t.shape != gx.shape:
+            raise ValueError("gx, gy, out must be contiguous float32 CUDA tensors of one shape")
+    _check(lib().gfc_solve_from_gradient_noalloc(b.shape[2], b.shape[3], b.shape[0] * b.shape[1], gx.data_ptr(),
+                                                 gy.data_ptr(), out.data_ptr(),
+                                                 ctypes.c_void_p(_stream_ptr(gx.device))))
+    return out
 
 
 def fft_c2c(x: torch.Tensor, inverse: bool = False) -> torch.Tensor:
