@@ -14,7 +14,9 @@ struct gfc_plan {
   gfc_dtype dtype;
   int M, N;   // padded (torus) size
   int Nh;     // N/2 + 1 Hermitian columns
-  int ldS;    // row stride of the spectrum scratch, in complex elements
+  int ldS;    // row stride of the row-major spectrum scratch (generic passes), complex elements
+  int ldM;    // column stride of the column-major spectrum scratch (fast passes)
+  bool fast;  // both transform lengths have register-resident schedules
   int chunk;  // fields per pipeline chunk
   int device;
   cudaStream_t stream;
@@ -23,10 +25,12 @@ struct gfc_plan {
   gfc::FftPlan colplan;  // length M
   // device tables (owned)
   float* G;       // [M][Nh] Green spectrum with 1/(MN) folded in
+  float* GT;      // [Nh][ldM] the same, transposed (fast passes)
   float2* twN;    // [N] exp(-2 pi i m / N)
   float2* twM;    // [M] exp(-2 pi i m / M)
   float2* spec;   // [chunk][M][ldS] complex spectrum scratch
-  float* partial; // [chunk][kMaxRowBlocks] per-block sums (adjoint)
+  float* partial; // [chunk][kMaxRowBlocks] per-block sums (adjoint, u[0,0])
+  float2* zbuf;   // [chunk][pairs][ldz] packed rows of L (fast passes)
   int* dev_err;   // device error word
   // host-buffer path (allocated on first use)
   void* stage_in[2][2];   // [buffer][gx, gy] device staging for one chunk
@@ -59,6 +63,14 @@ bool is_7smooth(long n);
 // device table builders (FP64 on the GPU, rounded to FP32)
 cudaError_t build_twiddles(float2* tw, int n, cudaStream_t s);
 cudaError_t build_green(float* G, int M, int N, int Nh, cudaStream_t s);
+cudaError_t build_green_t(float* GT, int M, int N, int Nh, int ldM, cudaStream_t s);
+
+// register-resident passes (solve_fast.cu): spectrum laid out [l][r]
+bool fast_rows_supported(int N);
+bool fast_cols_supported(int M);
+size_t fast_zbuf_elems(int H, int W, int N);  // per field
+cudaError_t run_chunk_fast(gfc_plan* P, int mode, const void* in0, const void* in1, void* out, int nf,
+                           cudaStream_t st);
 
 inline size_t dtype_size(gfc_dtype d) { return d == GFC_F32 ? 4 : 2; }
 

@@ -80,6 +80,28 @@ __global__ void k_build_green(float* G, int M, int N, int Nh) {
   }
 }
 
+__global__ void k_build_green_t(float* GT, int M, int N, int Nh, int ldM) {
+  const long total = (long)Nh * ldM;
+  for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
+    const int l = (int)(idx / ldM), k = (int)(idx % ldM);
+    if (k >= M) {
+      GT[idx] = 0.0f;
+      continue;
+    }
+    const double sk = sinpi((double)k / (double)M), sl = sinpi((double)l / (double)N);
+    const double lam = -4.0 * (sk * sk + sl * sl);
+    GT[idx] = (k == 0 && l == 0) ? 0.0f : (float)(1.0 / (lam * (double)M * (double)N));
+  }
+}
+
+cudaError_t build_green_t(float* GT, int M, int N, int Nh, int ldM, cudaStream_t s) {
+  long total = (long)Nh * ldM;
+  int blocks = (int)((total + 255) / 256);
+  if (blocks > 4096) blocks = 4096;
+  k_build_green_t<<<blocks, 256, 0, s>>>(GT, M, N, Nh, ldM);
+  return cudaGetLastError();
+}
+
 cudaError_t build_twiddles(float2* tw, int n, cudaStream_t s) {
   k_build_twiddles<<<(n + 255) / 256, 256, 0, s>>>(tw, n);
   return cudaGetLastError();
@@ -156,18 +178,22 @@ gfc_status gfc_plan_create_ex(gfc_plan** out, const gfc_plan_opts* o) {
   gfc_plan* p = (gfc_plan*)calloc(1, sizeof(gfc_plan));
   if (!p) return fail(GFC_ERR_ALLOC, "gfc_plan_create: host allocation failed");
   p->H = o->H; p->W = o->W; p->C = o->C; p->batch = o->batch; p->pad = pad; p->dtype = o->dtype;
-  p->M = M; p->N = N; p->Nh = N / 2 + 1; p->ldS = (p->Nh + 3) & ~3;
+  p->M = M; p->N = N; p->Nh = N / 2 + 1; p->ldS = (p->Nh + 3) & ~3; p->ldM = (M + 3) & ~3;
+  p->fast = fast_rows_supported(N) && fast_cols_supported(M) && getenv("GFC_FORCE_GENERIC") == nullptr;
   p->stream = (cudaStream_t)o->stream;
   if (!make_fft_plan(N, &p->rowplan) || !make_fft_plan(M, &p->colplan)) {
     free(p);
     return fail(GFC_ERR_UNSUPPORTED, "gfc_plan_create: no FFT schedule for %dx%d", M, N);
   }
   const long fields = (long)o->batch * o->C;
-  const size_t per_field = (size_t)M * p->ldS * sizeof(float2);
+  const size_t per_row_major = (size_t)M * p->ldS, per_col_major = (size_t)p->Nh * p->ldM;
+  const size_t per_field = (per_row_major > per_col_major ? per_row_major : per_col_major) * sizeof(float2);
   long chunk = o->chunk;
   if (chunk == 0) {
-    // keep the spectrum of one chunk well inside L2 (about 64 MB)
-    chunk = (long)((64u << 20) / per_field);
+    // keep the working set of one chunk (spectrum, and packed rows on the fast
+    // path) well inside L2 (about 64 MB)
+    const size_t ws = per_field + (p->fast ? fast_zbuf_elems(o->H, o->W, N) * sizeof(float2) : 0);
+    chunk = (long)((64u << 20) / ws);
     if (chunk < 1) chunk = 1;
   }
   if (chunk > fields) chunk = fields;
@@ -175,6 +201,8 @@ gfc_status gfc_plan_create_ex(gfc_plan** out, const gfc_plan_opts* o) {
 
   cudaError_t e = cudaGetDevice(&p->device);
   if (e == cudaSuccess) e = cudaMalloc(&p->G, (size_t)M * p->Nh * sizeof(float));
+  if (e == cudaSuccess && p->fast) e = cudaMalloc(&p->GT, (size_t)p->Nh * p->ldM * sizeof(float));
+  if (e == cudaSuccess && p->fast) e = cudaMalloc(&p->zbuf, fast_zbuf_elems(o->H, o->W, N) * chunk * sizeof(float2));
   if (e == cudaSuccess) e = cudaMalloc(&p->twN, (size_t)N * sizeof(float2));
   if (e == cudaSuccess) e = cudaMalloc(&p->twM, (size_t)M * sizeof(float2));
   if (e == cudaSuccess) e = cudaMalloc(&p->spec, per_field * (size_t)chunk);
@@ -186,6 +214,7 @@ gfc_status gfc_plan_create_ex(gfc_plan** out, const gfc_plan_opts* o) {
   if (e == cudaSuccess) e = build_twiddles(p->twN, N, bs);
   if (e == cudaSuccess) e = build_twiddles(p->twM, M, bs);
   if (e == cudaSuccess) e = build_green(p->G, M, N, p->Nh, bs);
+  if (e == cudaSuccess && p->fast) e = build_green_t(p->GT, M, N, p->Nh, p->ldM, bs);
   if (e == cudaSuccess) e = cudaStreamSynchronize(bs);
   if (bs) cudaStreamDestroy(bs);
   if (e != cudaSuccess) {
@@ -247,6 +276,8 @@ static void destroy_plan(gfc_plan* p) {
   if (!p) return;
   release_host_state(p);
   cudaFree(p->G);
+  cudaFree(p->GT);
+  cudaFree(p->zbuf);
   cudaFree(p->twN);
   cudaFree(p->twM);
   cudaFree(p->spec);

@@ -65,6 +65,19 @@ __device__ float block_sum(float v, float* red) {
   return s;
 }
 
+__device__ double block_sum_d(double v, double* red) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  double s = 0.0;
+  for (int w = 0; w < nw; ++w) s += red[w];
+  __syncthreads();
+  return s;
+}
+
 // ---------------------------------------------------------------------------
 // pass A
 // ---------------------------------------------------------------------------
@@ -191,7 +204,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_pass_c(const float2* __restrict__ spec, T* __restrict__ out,
                                                 const float2* __restrict__ twg, PassArgs A) {
   extern __shared__ float2 sm[];
-  __shared__ float red[32];
+  __shared__ double redd[32];
   float2* tw = sm;
   float2* b0 = sm + A.N;
   float2* b1 = b0 + A.N;
@@ -199,13 +212,14 @@ __global__ void __launch_bounds__(256) k_pass_c(const float2* __restrict__ spec,
   const float2* Sp = spec + (size_t)blockIdx.y * A.M * A.ldS;
   T* o = out + (size_t)blockIdx.y * A.H * A.W;
   for (int m = tid; m < A.N; m += nthr) tw[m] = twg[m];
-  // u[0,0] = sum over the full row-0 spectrum = Re Y[0] + Re Y[N/2] + 2 sum_{0<l<N/2} Re Y[l]
-  float s = 0.0f;
+  // u[0,0] = sum over the full row-0 spectrum = Re Y[0] + Re Y[N/2] + 2 sum_{0<l<N/2} Re Y[l],
+  // accumulated in FP64 (an error in u[0,0] shifts every output pixel)
+  double s = 0.0;
   for (int l = tid; l <= A.N / 2; l += nthr) {
-    const float x = Sp[l].x;
-    s += (l == 0 || l == A.N / 2) ? x : 2.0f * x;
+    const double x = Sp[l].x;
+    s += (l == 0 || l == A.N / 2) ? x : 2.0 * x;
   }
-  const float u00 = block_sum(s, red);
+  const float u00 = (float)block_sum_d(s, redd);
   const int q0 = blockIdx.x * A.ppb;
   const int q1 = min(q0 + A.ppb, A.pairs);
   for (int q = q0; q < q1; ++q) {
@@ -382,6 +396,7 @@ static cudaError_t launch_b_any(gfc_plan* P, PassArgs B, int nf, cudaStream_t st
 
 template <typename T, int MODE>
 static cudaError_t run_chunk(gfc_plan* P, const T* in0, const T* in1, T* out0, T* out1, int nf, cudaStream_t st) {
+  if (P->fast && MODE != kAdj) return run_chunk_fast(P, MODE, in0, in1, out0, nf, st);
   // pass A
   PassArgs A = base_args(P);
   A.nrows = (MODE == kGrad) ? P->H + 1 : P->H;

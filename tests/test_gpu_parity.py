@@ -234,3 +234,75 @@ def test_bad_tensor_arguments_raise():
     with pytest.raises(gfc.GFCError):
         p.solve_from_gradient(x, x, out=x)  # out aliases an input
     p.close()
+
+
+# ---------------------------------------------------------------- register-resident path
+
+def _torch_fp32_solve(gx, gy, M, N, p):
+    """The same math in plain PyTorch FP32 (rfft2 / irfft2): the FP32 baseline error."""
+    H, W = gx.shape
+    G = torch.from_numpy(O.green_spectrum(M, N)[:, : N // 2 + 1]).float().to(DEV)
+    Ex = torch.zeros((M, N), device=DEV)
+    Ey = torch.zeros_like(Ex)
+    Ex[p:p + H, p:p + W] = torch.from_numpy(gx).to(DEV)
+    Ey[p:p + H, p:p + W] = torch.from_numpy(gy).to(DEV)
+    L = Ex - torch.roll(Ex, 1, -1) + Ey - torch.roll(Ey, 1, -2)
+    u = torch.fft.irfft2(torch.fft.rfft2(L) * G, s=(M, N))
+    return (u - u[0, 0])[p:p + H, p:p + W].double().cpu().numpy()
+
+FAST_SHAPES = [(801, 1200), (795, 1199), (802, 1242), (793, 1193)]  # all pad to 810 x 1250
+
+
+@pytest.mark.parametrize("H,W", FAST_SHAPES)
+def test_fast_path_matches_oracle(H, W):
+    rng = np.random.default_rng(H + W)
+    B = 2
+    gx = rng.uniform(-0.05, 0.05, (B, 1, H, W)).astype(np.float32)
+    gy = rng.uniform(-0.05, 0.05, (B, 1, H, W)).astype(np.float32)
+    p = gfc.Plan(H, W, 1, B, device=DEV)
+    assert (p.M, p.N) == (810, 1250)
+    out = _np(p.solve_from_gradient(_to_dev(gx), _to_dev(gy)))
+    for b in range(B):
+        ref = O.solve_from_gradient(gx[b, 0].astype(np.float64), gy[b, 0].astype(np.float64), p.M, p.N, p.pad)
+        # White-noise gradients put little of the solution in the lowest bins, where FP32
+        # round-off is amplified by |G| ~ (M/2pi)^2, so no FP32 transform reaches 1e-5 here
+        # (cuFFT FP32 on the same math: ~2-3e-5). The bar is the error of a plain PyTorch
+        # FP32 FFT of the same math on the same input, within the factor by which FP32 FFT
+        # algorithms differ (radix order, twiddle rounding): 3x.
+        base = _rel(_torch_fp32_solve(gx[b, 0], gy[b, 0], p.M, p.N, p.pad), ref)
+        assert _rel(out[b, 0], ref) <= max(REL_F32, 3.0 * base)
+        assert np.abs(out[b, 0] - ref).max() <= MAXABS_F32
+    lap = rng.standard_normal((B, 1, H, W)).astype(np.float32) * 0.01
+    out = _np(p.solve_from_laplacian(_to_dev(lap)))
+    ref = O.solve_from_laplacian(lap[1, 0].astype(np.float64), p.M, p.N, p.pad)
+    assert _rel(out[1, 0], ref) <= REL_F32
+    assert np.abs(out[1, 0] - ref).max() <= MAXABS_F32 * max(1.0, np.abs(ref).max())
+    p.close()
+
+
+def test_fast_path_agrees_with_generic_path(monkeypatch):
+    H, W, B = 801, 1200, 3
+    gx, gy = synth.perturbed_gradient_batch(batch=B, H=H, W=W, seed=555)
+    tx, ty = _to_dev(gx), _to_dev(gy)
+    fast = gfc.Plan(H, W, 1, B, device=DEV)
+    monkeypatch.setenv("GFC_FORCE_GENERIC", "1")
+    gen = gfc.Plan(H, W, 1, B, device=DEV)
+    monkeypatch.delenv("GFC_FORCE_GENERIC")
+    a = _np(fast.solve_from_gradient(tx, ty))
+    b = _np(gen.solve_from_gradient(tx, ty))
+    assert _rel(a, b) <= 2e-6
+    a2 = _np(fast.solve_from_gradient(tx, ty))
+    assert np.array_equal(a, a2)  # deterministic
+    fast.close()
+    gen.close()
+
+
+@pytest.mark.parametrize("dtype", [torch.float16, torch.bfloat16])
+def test_fast_path_16bit_storage(dtype):
+    gx, gy = synth.perturbed_gradient_batch(batch=1, H=801, W=1200, seed=4242)
+    tx, ty = _to_dev(gx, dtype), _to_dev(gy, dtype)
+    p = gfc.Plan(801, 1200, 1, 1, dtype, device=DEV)
+    out = _np(p.solve_from_gradient(tx, ty))[0, 0]
+    ref = O.solve_from_gradient(_np(tx)[0, 0], _np(ty)[0, 0], p.M, p.N, p.pad)
+    assert _rel(out, ref) <= REL_16
+    p.close()
