@@ -71,6 +71,8 @@ typedef struct {
   int size_policy;   /* gfc_size_policy */
   int chunk;         /* fields per pipeline chunk; 0 lets the plan choose */
   void* stream;      /* cudaStream_t to run on; NULL = the legacy default stream */
+  int streams;       /* chunks in flight at once (1..4), each on an internal stream
+                        forked from and joined back into the plan's stream; 0 = auto */
 } gfc_plan_opts;
 
 /* Padded-domain size for an H x W image (Algorithm A: size = image + 2 pad,

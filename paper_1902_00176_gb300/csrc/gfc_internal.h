@@ -8,6 +8,16 @@
 #include "../../include/gfc.h"
 #include "fft_core.cuh"
 
+namespace gfc {
+// scratch of one chunk in flight
+struct Bufs {
+  float2* spec;    // spectrum
+  float2* zbuf;    // packed rows of L / row-major spectrum (fast passes)
+  float* partial;  // per-block sums
+};
+constexpr int kMaxSlots = 4;
+}  // namespace gfc
+
 struct gfc_plan {
   // problem
   int H, W, C, batch, pad;
@@ -28,9 +38,14 @@ struct gfc_plan {
   float* GT;      // [Nh][ldM] the same, transposed (fast passes)
   float2* twN;    // [N] exp(-2 pi i m / N)
   float2* twM;    // [M] exp(-2 pi i m / M)
-  float2* spec;   // [chunk][M][ldS] complex spectrum scratch
-  float* partial; // [chunk][kMaxRowBlocks] per-block sums (adjoint, u[0,0])
-  float2* zbuf;   // [chunk][pairs][ldz] packed rows of L (fast passes)
+  float2* spec;   // [slots][chunk] spectrum scratch (per field: max(M ldS, Nh ldM) complex)
+  float* partial; // [slots][chunk][kMaxRowBlocks] per-block sums (adjoint, u[0,0])
+  float2* zbuf;   // [slots][chunk] packed rows of L / row-major spectrum (fast passes)
+  size_t spec_field, zbuf_field;  // elements per field of spec and zbuf
+  int nslots;                     // chunks in flight
+  cudaStream_t slot_stream[gfc::kMaxSlots];
+  cudaEvent_t slot_done[gfc::kMaxSlots];
+  cudaEvent_t ev_fork;
   int* dev_err;   // device error word
   // host-buffer path (allocated on first use)
   void* stage_in[2][2];   // [buffer][gx, gy] device staging for one chunk
@@ -69,14 +84,21 @@ cudaError_t build_green_t(float* GT, int M, int N, int Nh, int ldM, cudaStream_t
 bool fast_rows_supported(int N);
 bool fast_cols_supported(int M);
 size_t fast_zbuf_elems(int H, int W, int N);  // per field
-cudaError_t run_chunk_fast(gfc_plan* P, int mode, const void* in0, const void* in1, void* out, int nf,
-                           cudaStream_t st);
+cudaError_t run_chunk_fast(gfc_plan* P, const Bufs& B, int mode, const void* in0, const void* in1, void* out,
+                           int nf, cudaStream_t st);
+inline Bufs slot_bufs(const gfc_plan* P, int s) {
+  Bufs b;
+  b.spec = P->spec + (size_t)s * P->chunk * P->spec_field;
+  b.zbuf = P->zbuf ? P->zbuf + (size_t)s * P->chunk * P->zbuf_field : nullptr;
+  b.partial = P->partial + (size_t)s * P->chunk * kMaxRowBlocks;
+  return b;
+}
 
 inline size_t dtype_size(gfc_dtype d) { return d == GFC_F32 ? 4 : 2; }
 
 // tracing around one kernel launch on the plan's stream
-void prof_begin(gfc_plan* P, int pass);
-void prof_end(gfc_plan* P);
+void prof_begin(gfc_plan* P, int pass, cudaStream_t st);
+void prof_end(gfc_plan* P, cudaStream_t st);
 // free the host-buffer pipeline and the profiling event pool (plan teardown)
 void release_host_state(gfc_plan* P);
 

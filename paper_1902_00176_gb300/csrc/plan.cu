@@ -179,34 +179,53 @@ gfc_status gfc_plan_create_ex(gfc_plan** out, const gfc_plan_opts* o) {
   if (!p) return fail(GFC_ERR_ALLOC, "gfc_plan_create: host allocation failed");
   p->H = o->H; p->W = o->W; p->C = o->C; p->batch = o->batch; p->pad = pad; p->dtype = o->dtype;
   p->M = M; p->N = N; p->Nh = N / 2 + 1; p->ldS = (p->Nh + 3) & ~3; p->ldM = (M + 3) & ~3;
-  p->fast = fast_rows_supported(N) && fast_cols_supported(M) && getenv("GFC_FORCE_GENERIC") == nullptr;
+  p->fast = fast_rows_supported(N) && fast_cols_supported(M) && pad == 4 && getenv("GFC_FORCE_GENERIC") == nullptr;
   p->stream = (cudaStream_t)o->stream;
   if (!make_fft_plan(N, &p->rowplan) || !make_fft_plan(M, &p->colplan)) {
     free(p);
     return fail(GFC_ERR_UNSUPPORTED, "gfc_plan_create: no FFT schedule for %dx%d", M, N);
   }
+  if (o->streams < 0 || o->streams > kMaxSlots) {
+    free(p);
+    return fail(GFC_ERR_INVALID_ARG, "gfc_plan_create: streams=%d (0..%d)", o->streams, kMaxSlots);
+  }
   const long fields = (long)o->batch * o->C;
   const size_t per_row_major = (size_t)M * p->ldS, per_col_major = (size_t)p->Nh * p->ldM;
-  const size_t per_field = (per_row_major > per_col_major ? per_row_major : per_col_major) * sizeof(float2);
+  p->spec_field = per_row_major > per_col_major ? per_row_major : per_col_major;
+  p->zbuf_field = p->fast ? fast_zbuf_elems(o->H, o->W, N) : 0;
+  const size_t per_field = p->spec_field * sizeof(float2);
+  const size_t ws = per_field + p->zbuf_field * sizeof(float2);
   long chunk = o->chunk;
+  int nslots = o->streams;
+  if (nslots == 0) nslots = 1;
   if (chunk == 0) {
-    // keep the working set of one chunk (spectrum, and packed rows on the fast
-    // path) well inside L2 (about 64 MB)
-    const size_t ws = per_field + (p->fast ? fast_zbuf_elems(o->H, o->W, N) * sizeof(float2) : 0);
-    chunk = (long)((64u << 20) / ws);
+    // Measured on GB300 (801x1200 fields): the passes are bound by arithmetic
+    // and latency rather than by where the intermediates live, and large
+    // grids beat L2-sized chunks (1.11 ms per 100 fields in one chunk, 1.29 -
+    // 1.41 ms with 2 - 12 field chunks on 2 - 4 streams). So one chunk holds as
+    // many fields as 2 GB of scratch allows.
+    chunk = (long)((size_t(2) << 30) / (ws * nslots));
     if (chunk < 1) chunk = 1;
   }
   if (chunk > fields) chunk = fields;
+  const long nchunks = (fields + chunk - 1) / chunk;
+  if (nslots > nchunks) nslots = (int)nchunks;
   p->chunk = (int)chunk;
+  p->nslots = nslots;
 
   cudaError_t e = cudaGetDevice(&p->device);
   if (e == cudaSuccess) e = cudaMalloc(&p->G, (size_t)M * p->Nh * sizeof(float));
   if (e == cudaSuccess && p->fast) e = cudaMalloc(&p->GT, (size_t)p->Nh * p->ldM * sizeof(float));
-  if (e == cudaSuccess && p->fast) e = cudaMalloc(&p->zbuf, fast_zbuf_elems(o->H, o->W, N) * chunk * sizeof(float2));
+  if (e == cudaSuccess && p->fast) e = cudaMalloc(&p->zbuf, p->zbuf_field * chunk * nslots * sizeof(float2));
   if (e == cudaSuccess) e = cudaMalloc(&p->twN, (size_t)N * sizeof(float2));
   if (e == cudaSuccess) e = cudaMalloc(&p->twM, (size_t)M * sizeof(float2));
-  if (e == cudaSuccess) e = cudaMalloc(&p->spec, per_field * (size_t)chunk);
-  if (e == cudaSuccess) e = cudaMalloc(&p->partial, (size_t)chunk * kMaxRowBlocks * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&p->spec, per_field * (size_t)chunk * nslots);
+  if (e == cudaSuccess) e = cudaMalloc(&p->partial, (size_t)chunk * nslots * kMaxRowBlocks * sizeof(float));
+  for (int sl = 0; sl < nslots && e == cudaSuccess; ++sl) {
+    e = cudaStreamCreateWithFlags(&p->slot_stream[sl], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->slot_done[sl], cudaEventDisableTiming);
+  }
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaMalloc(&p->dev_err, sizeof(int));
   cudaStream_t bs = nullptr;
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking);
@@ -282,6 +301,11 @@ static void destroy_plan(gfc_plan* p) {
   cudaFree(p->twM);
   cudaFree(p->spec);
   cudaFree(p->partial);
+  for (int sl = 0; sl < kMaxSlots; ++sl) {
+    if (p->slot_stream[sl]) cudaStreamDestroy(p->slot_stream[sl]);
+    if (p->slot_done[sl]) cudaEventDestroy(p->slot_done[sl]);
+  }
+  if (p->ev_fork) cudaEventDestroy(p->ev_fork);
   cudaFree(p->dev_err);
   free(p);
 }

@@ -338,7 +338,7 @@ static cudaError_t ensure_smem(K kernel, size_t smem) {
   return cudaSuccess;
 }
 
-void prof_begin(gfc_plan* P, int pass) {
+void prof_begin(gfc_plan* P, int pass, cudaStream_t st) {
   P->prof.launches[pass] += 1;
   if (!P->profiling) return;
   if (P->ev_used >= P->ev_cap) {
@@ -346,12 +346,12 @@ void prof_begin(gfc_plan* P, int pass) {
     return;
   }
   P->ev_pass[P->ev_used] = pass;
-  cudaEventRecord(P->ev_start[P->ev_used], P->stream);
+  cudaEventRecord(P->ev_start[P->ev_used], st);
 }
 
-void prof_end(gfc_plan* P) {
+void prof_end(gfc_plan* P, cudaStream_t st) {
   if (!P->profiling || P->ev_used >= P->ev_cap) return;
-  cudaEventRecord(P->ev_stop[P->ev_used], P->stream);
+  cudaEventRecord(P->ev_stop[P->ev_used], st);
   P->ev_used += 1;
 }
 
@@ -373,30 +373,31 @@ static PassArgs base_args(const gfc_plan* P) {
 static int ceil_div(int a, int b) { return (a + b - 1) / b; }
 
 template <int S, int MODE>
-static cudaError_t launch_b(gfc_plan* P, PassArgs B, int nf, cudaStream_t st) {
+static cudaError_t launch_b(gfc_plan* P, const Bufs& bf, PassArgs B, int nf, cudaStream_t st) {
   const size_t smem = (size_t)(P->M + 2 * (size_t)P->M * S) * sizeof(float2);
   auto k = k_pass_b<S, MODE>;
   cudaError_t e = ensure_smem(k, smem);
   if (e != cudaSuccess) return e;
-  prof_begin(P, 1);
-  k<<<dim3(ceil_div(P->Nh, S), nf), 256, smem, st>>>(P->spec, P->G, P->twM, P->partial, B);
-  prof_end(P);
+  prof_begin(P, 1, st);
+  k<<<dim3(ceil_div(P->Nh, S), nf), 256, smem, st>>>(bf.spec, P->G, P->twM, bf.partial, B);
+  prof_end(P, st);
   return cudaGetLastError();
 }
 
 template <int MODE>
-static cudaError_t launch_b_any(gfc_plan* P, PassArgs B, int nf, cudaStream_t st) {
+static cudaError_t launch_b_any(gfc_plan* P, const Bufs& bf, PassArgs B, int nf, cudaStream_t st) {
   switch (pick_strip(P->M)) {
-    case 8: return launch_b<8, MODE>(P, B, nf, st);
-    case 4: return launch_b<4, MODE>(P, B, nf, st);
-    case 2: return launch_b<2, MODE>(P, B, nf, st);
-    default: return launch_b<1, MODE>(P, B, nf, st);
+    case 8: return launch_b<8, MODE>(P, bf, B, nf, st);
+    case 4: return launch_b<4, MODE>(P, bf, B, nf, st);
+    case 2: return launch_b<2, MODE>(P, bf, B, nf, st);
+    default: return launch_b<1, MODE>(P, bf, B, nf, st);
   }
 }
 
 template <typename T, int MODE>
-static cudaError_t run_chunk(gfc_plan* P, const T* in0, const T* in1, T* out0, T* out1, int nf, cudaStream_t st) {
-  if (P->fast && MODE != kAdj) return run_chunk_fast(P, MODE, in0, in1, out0, nf, st);
+static cudaError_t run_chunk(gfc_plan* P, const Bufs& bf, const T* in0, const T* in1, T* out0, T* out1, int nf,
+                             cudaStream_t st) {
+  if (P->fast && MODE != kAdj) return run_chunk_fast(P, bf, MODE, in0, in1, out0, nf, st);
   // pass A
   PassArgs A = base_args(P);
   A.nrows = (MODE == kGrad) ? P->H + 1 : P->H;
@@ -410,15 +411,15 @@ static cudaError_t run_chunk(gfc_plan* P, const T* in0, const T* in1, T* out0, T
       const size_t smem = 3 * (size_t)P->N * sizeof(float2);
     auto k = k_pass_a<T, MODE>;
     if ((e = ensure_smem(k, smem)) != cudaSuccess) return e;
-    prof_begin(P, 0);
-    k<<<dim3(A.nparts, nf), 256, smem, st>>>(in0, in1, P->spec, P->partial, P->twN, A);
-    prof_end(P);
+    prof_begin(P, 0, st);
+    k<<<dim3(A.nparts, nf), 256, smem, st>>>(in0, in1, bf.spec, bf.partial, P->twN, A);
+    prof_end(P, st);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   // pass B
   PassArgs B = A;
   B.plan = P->colplan;
-  if ((e = launch_b_any<MODE>(P, B, nf, st)) != cudaSuccess) return e;
+  if ((e = launch_b_any<MODE>(P, bf, B, nf, st)) != cudaSuccess) return e;
   // pass C
   PassArgs C = base_args(P);
   C.ppb = 4;
@@ -427,33 +428,49 @@ static cudaError_t run_chunk(gfc_plan* P, const T* in0, const T* in1, T* out0, T
       const size_t smem = 3 * (size_t)P->N * sizeof(float2) + (size_t)P->W * sizeof(float);
     auto k = k_pass_c_adj<T>;
     if ((e = ensure_smem(k, smem)) != cudaSuccess) return e;
-    prof_begin(P, 2);
-    k<<<dim3(ceil_div(C.pairs, C.ppb), nf), 256, smem, st>>>(P->spec, out0, out1, P->twN, C);
-    prof_end(P);
+    prof_begin(P, 2, st);
+    k<<<dim3(ceil_div(C.pairs, C.ppb), nf), 256, smem, st>>>(bf.spec, out0, out1, P->twN, C);
+    prof_end(P, st);
   } else {
       const size_t smem = 3 * (size_t)P->N * sizeof(float2);
     auto k = k_pass_c<T>;
     if ((e = ensure_smem(k, smem)) != cudaSuccess) return e;
-    prof_begin(P, 2);
-    k<<<dim3(ceil_div(C.pairs, C.ppb), nf), 256, smem, st>>>(P->spec, out0, P->twN, C);
-    prof_end(P);
+    prof_begin(P, 2, st);
+    k<<<dim3(ceil_div(C.pairs, C.ppb), nf), 256, smem, st>>>(bf.spec, out0, P->twN, C);
+    prof_end(P, st);
   }
   return cudaGetLastError();
 }
 
+// Chunk c runs on slot c mod nslots: its own scratch and internal stream, forked
+// from the plan's stream and joined back into it at the end of the call.
 template <typename T, int MODE>
 static gfc_status run_all(gfc_plan* P, const void* a, const void* b, void* o0, void* o1) {
   const long fields = (long)P->batch * P->C;
   const size_t fe = (size_t)P->H * P->W;
   P->prof.calls += 1;
-  for (long f0 = 0; f0 < fields; f0 += P->chunk) {
+  const bool fork = P->nslots > 1;
+  if (fork) {
+    GFC_CUDA_TRY(cudaEventRecord(P->ev_fork, P->stream));
+    for (int s = 0; s < P->nslots; ++s) GFC_CUDA_TRY(cudaStreamWaitEvent(P->slot_stream[s], P->ev_fork, 0));
+  }
+  long c = 0;
+  for (long f0 = 0; f0 < fields; f0 += P->chunk, ++c) {
     const int nf = (int)((fields - f0 < P->chunk) ? fields - f0 : P->chunk);
     const T* in0 = static_cast<const T*>(a) + f0 * fe;
     const T* in1 = b ? static_cast<const T*>(b) + f0 * fe : nullptr;
     T* out0 = static_cast<T*>(o0) + f0 * fe;
     T* out1 = o1 ? static_cast<T*>(o1) + f0 * fe : nullptr;
-    cudaError_t e = run_chunk<T, MODE>(P, in0, in1, out0, out1, nf, P->stream);
+    const int s = fork ? (int)(c % P->nslots) : 0;
+    cudaError_t e = run_chunk<T, MODE>(P, slot_bufs(P, s), in0, in1, out0, out1, nf,
+                                       fork ? P->slot_stream[s] : P->stream);
     if (e != cudaSuccess) return cuda_fail(e, "gfc solve launch");
+  }
+  if (fork) {
+    for (int s = 0; s < P->nslots; ++s) {
+      GFC_CUDA_TRY(cudaEventRecord(P->slot_done[s], P->slot_stream[s]));
+      GFC_CUDA_TRY(cudaStreamWaitEvent(P->stream, P->slot_done[s], 0));
+    }
   }
   return GFC_OK;
 }
@@ -516,7 +533,7 @@ static gfc_status run_host(gfc_plan* P, const void* gx, const void* gy, void* ou
     GFC_CUDA_TRY(cudaEventRecord(P->ev_in[b], P->copy_in));
     GFC_CUDA_TRY(cudaStreamWaitEvent(cs, P->ev_in[b], 0));
     if (c >= 2) GFC_CUDA_TRY(cudaStreamWaitEvent(cs, P->ev_out[b], 0));
-    cudaError_t e = run_chunk<T, kGrad>(P, static_cast<const T*>(P->stage_in[b][0]),
+    cudaError_t e = run_chunk<T, kGrad>(P, slot_bufs(P, 0), static_cast<const T*>(P->stage_in[b][0]),
                                         static_cast<const T*>(P->stage_in[b][1]), static_cast<T*>(P->stage_out[b]),
                                         nullptr, nf, cs);
     if (e != cudaSuccess) return cuda_fail(e, "gfc host solve launch");
@@ -730,7 +747,8 @@ extern "C" gfc_status gfc_solve_from_gradient_noalloc(int H, int W, int fields, 
   gfc_plan P;
   memset(&P, 0, sizeof(P));
   P.H = H; P.W = W; P.C = 1; P.batch = fields; P.pad = 4; P.dtype = GFC_F32;
-  P.M = M; P.N = N; P.Nh = N / 2 + 1; P.ldS = (P.Nh + 3) & ~3; P.chunk = 1;
+  P.M = M; P.N = N; P.Nh = N / 2 + 1; P.ldS = (P.Nh + 3) & ~3; P.chunk = 1; P.nslots = 1;
+  P.spec_field = (size_t)M * P.ldS;
   if ((size_t)M * P.ldS > kNoAllocSpecElems || (size_t)M * P.Nh > kNoAllocGreenElems)
     return fail(GFC_ERR_UNSUPPORTED,
                 "gfc_solve_from_gradient_noalloc: padded size %dx%d needs %zu spectrum elements, the static "
@@ -760,7 +778,7 @@ extern "C" gfc_status gfc_solve_from_gradient_noalloc(int H, int W, int fields, 
   GFC_CUDA_TRY(build_green(P.G, M, N, P.Nh, P.stream));
   const size_t fe = (size_t)H * W;
   for (int f = 0; f < fields; ++f) {
-    cudaError_t e = run_chunk<float, kGrad>(&P, static_cast<const float*>(gx) + f * fe,
+    cudaError_t e = run_chunk<float, kGrad>(&P, slot_bufs(&P, 0), static_cast<const float*>(gx) + f * fe,
                                             static_cast<const float*>(gy) + f * fe, static_cast<float*>(out) + f * fe,
                                             nullptr, 1, P.stream);
     if (e != cudaSuccess) return cuda_fail(e, "gfc_solve_from_gradient_noalloc launch");

@@ -31,10 +31,27 @@
 
 namespace gfc {
 
+// The register-resident schedules assume Algorithm A's pad of 4.
+constexpr int kP = 4;
+
+constexpr bool cx_smooth7(int n) {
+  if (n < 1) return false;
+  for (int f : {2, 3, 5, 7})
+    while (n % f == 0) n /= f;
+  return n == 1;
+}
+// smallest image width that pads to N under the SMOOTH policy (pad kP)
+constexpr int cx_min_width(int N) {
+  int prev = N - 2;
+  while (prev > 0 && !cx_smooth7(prev)) prev -= 2;
+  return prev - 2 * kP + 1;
+}
+
 struct FastArgs {
   int H, W, p, M, N, Nh, ldM;
   int nrows, ncols;  // support of L (from torus row/col p): H+1, W+1 (gradient) or H, W
-  int npairs, ldz;   // packed row pairs of L and their stride (complex elements)
+  int npairs, ldz;   // packed row pairs of L, and the stride of a packed row (>= N, zero padded)
+  int zpairs;        // packed rows per field (npairs rounded up to whole groups, extra rows zero)
   int ngroups;       // row-pair groups per field (pass A) / output row-pair groups (pass C)
   int nparts;        // pass B column blocks per field (u[0,0] partial sums)
   int nf;            // fields in this chunk
@@ -84,6 +101,7 @@ struct RowShape {
   static constexpr int THREADS = ((F * T + 31) / 32) * 32;
   static_assert(R1 % R2 == 0, "row schedule needs R2 | R1");
   static constexpr int NO = N + 1;        // stage-2 output buffer stride (natural order)
+  static constexpr int WMIN = cx_min_width(N);
   static constexpr size_t smem_bytes() { return (size_t)(R1 * R2 + F * NP) * sizeof(float2); }
   static constexpr size_t smem_bytes_fwd() { return (size_t)(R1 * R2 + F * NP + F * NO) * sizeof(float2); }
   // padded index: one spare slot every R1 elements (conflict-free stage-1 writes)
@@ -116,17 +134,20 @@ struct ColShape {
 template <typename T, int MODE>
 __global__ void __launch_bounds__(256) k_fast_div(const T* __restrict__ in0, const T* __restrict__ in1,
                                                   float2* __restrict__ z, FastArgs A) {
-  // grid: x = 4-column groups (blockDim.x per block), y = row pairs, z = fields
+  // grid: x = groups of 4 padded columns, y = packed rows (zpairs), z = fields.
+  // Packed row `pair`, padded column c holds L[2 pair][c - p] + i L[2 pair + 1][c - p],
+  // zero outside the support, so the row pass can load it without range checks.
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   const int pair = blockIdx.y, field = blockIdx.z;
   if (q >= A.ldz / 4) return;
-  const bool vec4 = (A.W % 4) == 0;
-  const size_t fe = (size_t)A.H * A.W;
-  {
+  const int c0 = 4 * q, j0 = c0 - kP;
+  float la[4] = {0.0f, 0.0f, 0.0f, 0.0f}, lb[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+  if (pair < A.npairs && j0 + 3 >= 0 && j0 < A.ncols) {
+    const bool vec4 = (A.W % 4) == 0 && j0 >= 0;
+    const size_t fe = (size_t)A.H * A.W;
     const T* a = in0 + field * fe;
     const T* b = (MODE == 0) ? in1 + field * fe : nullptr;
-    const int ia = 2 * pair, ib = ia + 1, j0 = 4 * q;
-    float la[4] = {0.0f, 0.0f, 0.0f, 0.0f}, lb[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    const int ia = 2 * pair, ib = ia + 1;
     if (MODE == 0) {
       float xa[5], xb[5], ya[4], yb[4], ym[4];  // gx rows ia, ib at j0-1..j0+3; gy rows ia, ib, ia-1
       const bool ina = ia < A.H, inb = ib < A.H, inm = ia >= 1 && ia - 1 < A.H;
@@ -173,14 +194,14 @@ __global__ void __launch_bounds__(256) k_fast_div(const T* __restrict__ in0, con
     }
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
-      const bool inj = j0 + e < A.ncols;
+      const bool inj = j0 + e >= 0 && j0 + e < A.ncols;
       la[e] = (inj && ia < A.nrows) ? la[e] : 0.0f;
       lb[e] = (inj && ib < A.nrows) ? lb[e] : 0.0f;
     }
-    float4* dst = reinterpret_cast<float4*>(z + ((size_t)field * A.npairs + pair) * A.ldz + j0);
-    dst[0] = make_float4(la[0], lb[0], la[1], lb[1]);
-    dst[1] = make_float4(la[2], lb[2], la[3], lb[3]);
   }
+  float4* dst = reinterpret_cast<float4*>(z + ((size_t)field * A.zpairs + pair) * A.ldz + c0);
+  dst[0] = make_float4(la[0], lb[0], la[1], lb[1]);
+  dst[1] = make_float4(la[2], lb[2], la[3], lb[3]);
 }
 
 // ---------------------------------------------------------------------------
@@ -209,15 +230,12 @@ __global__ void __launch_bounds__(S::THREADS) k_fast_rows_fwd(const float2* __re
   const int items = A.nf * A.ngroups;
   // the packed-row inputs of the next item are loaded while this one is transformed
   auto load_item = [&](int w, float2 (&dst)[S::R1]) {
+    // packed rows are zero padded to the full transform length: no range checks
     const int field = w / A.ngroups, g = w - field * A.ngroups;
-    const int pair = g * S::F + f;
-    const bool live = act && w < items && pair < A.npairs;
-    const float2* zrow = z + ((size_t)(live ? field : 0) * A.npairs + (live ? pair : 0)) * A.ldz;
+    const bool live = act && w < items;
+    const float2* zrow = z + ((size_t)(live ? field : 0) * A.zpairs + (live ? g * S::F + f : 0)) * A.ldz + t;
 #pragma unroll
-    for (int r = 0; r < S::R1; ++r) {
-      const int jj = t + S::R2 * r - A.p;
-      dst[r] = (live && jj >= 0 && jj < A.ncols) ? zrow[jj] : make_float2(0.0f, 0.0f);
-    }
+    for (int r = 0; r < S::R1; ++r) dst[r] = zrow[S::R2 * r];
   };
   float2 nxt[S::R1];
   load_item(blockIdx.x, nxt);
@@ -249,6 +267,16 @@ __global__ void __launch_bounds__(S::THREADS) k_fast_rows_fwd(const float2* __re
       }
     }
     __syncthreads();  // stage-2 results visible; buf free for the next item
+    if (g == 0) {
+      // rows of every column outside the support [p, p + nrows) are zero, so the
+      // column pass loads whole columns without range checks
+      float2* Sz = spec + (size_t)field * A.Nh * A.ldM;
+      const int nz = A.M - A.nrows;
+      for (int idx = tid; idx < A.Nh * nz; idx += blockDim.x) {
+        const int k = idx / nz, q = idx - k * nz;
+        Sz[(size_t)k * A.ldM + (q < kP ? q : q + A.nrows)] = make_float2(0.0f, 0.0f);
+      }
+    }
     // X_a[k] = (Z[k] + conj Z[N-k]) / 2, X_b[k] = -i (Z[k] - conj Z[N-k]) / 2, stored at spec[k][p + row]
     const int ra = g * 2 * S::F + 2 * uf;
     if (uact && ra < A.nrows) {
@@ -292,13 +320,10 @@ __global__ void __launch_bounds__(S::THREADS, S::MINB) k_fast_cols(const float2*
   const float2* col = spec + (size_t)field * A.Nh * A.ldM + (size_t)(act ? l : 0) * A.ldM;
   const float* gcol = GT + (size_t)(act ? l : 0) * A.ldM;
   float2* mybuf = buf + (c < S::C ? c : 0) * S::MP;
-  const int r_lo = A.p, r_hi = A.p + A.nrows;  // input support rows [r_lo, r_hi)
+  // rows outside the support were zeroed by the row pass
   float2 v[S::R1];
 #pragma unroll
-  for (int r = 0; r < S::R1; ++r) {
-    const int row = t + S::R2 * r;
-    v[r] = (act && row >= r_lo && row < r_hi) ? col[row] : make_float2(0.0f, 0.0f);
-  }
+  for (int r = 0; r < S::R1; ++r) v[r] = col[t + S::R2 * r];
   for (int i = tid; i < S::R1 * S::R2; i += blockDim.x) {
     const int j = i / S::R2, r = i - j * S::R2;
     twF[j * S::TWF_STRIDE + r] = twg[r * j];
@@ -404,18 +429,23 @@ __global__ void __launch_bounds__(S::THREADS) k_fast_rows_inv(const float2* __re
     float2 v[S::R1];
 #pragma unroll
     for (int r = 0; r < S::R1; ++r) {
+      // l = t + R2 r with t < R2: whether l lies below or above N/2 is known at
+      // compile time except for the one r whose range contains N/2
       const int l = t + S::R2 * r;
-      const bool lo = l <= half;
+      const bool all_lo = S::R2 * r + S::R2 - 1 < half;
+      const bool all_hi = S::R2 * r > half;
+      const bool lo = all_lo || (!all_hi && l < half);
       const int src = lo ? l : S::N - l;
       float2 ya = va ? ya_row[src] : make_float2(0.0f, 0.0f);
       float2 yb = vb ? yb_row[src] : make_float2(0.0f, 0.0f);
-      if (src == 0 || src == half) {
+      // bins 0 and N/2 are real in a real transform: drop their imaginary parts
+      const bool may_edge = (r == 0) || (!all_lo && !all_hi);
+      if (may_edge && (src == 0 || src == half)) {
         ya.y = 0.0f;
         yb.y = 0.0f;
       }
       v[r] = lo ? make_float2(ya.x - yb.y, ya.y + yb.x) : make_float2(ya.x + yb.y, yb.x - ya.y);
-    }
-    if (act) dft_reg<S::R1, +1>(v);
+    }    if (act) dft_reg<S::R1, +1>(v);
     __syncthreads();  // previous item's stage 2 done with buf; u00 published
     if (act) {
 #pragma unroll
@@ -435,8 +465,10 @@ __global__ void __launch_bounds__(S::THREADS) k_fast_rows_inv(const float2* __re
         dft_reg<S::R2, +1>(u);
 #pragma unroll
         for (int s2 = 0; s2 < S::R2; ++s2) {
-          const int jc = j + S::R1 * s2 - A.p;
-          if (jc >= 0 && jc < A.W) {
+          const int jc = j + S::R1 * s2 - kP;
+          // columns of this stage inside [0, WMIN) for every t need no crop test
+          const bool sure = (S::R2 * jj + S::R1 * s2 >= kP) && (S::R2 * jj + S::R2 - 1 + S::R1 * s2 - kP < S::WMIN);
+          if (sure || (jc >= 0 && jc < A.W)) {
             if (va) o[(size_t)ia * A.W + jc] = f_from_f<T>(u[s2].x - u00);
             if (vb) o[(size_t)ib * A.W + jc] = f_from_f<T>(u[s2].y - u00);
           }
@@ -458,7 +490,9 @@ bool fast_cols_supported(int M) { return M == 810; }
 // The packed-row buffer also receives pass B's row-major output (H rows of
 // N/2+1 columns, stride rounded up to 4), so it is sized for the larger of the two.
 size_t fast_zbuf_elems(int H, int W, int N) {
-  const size_t packed = (size_t)((H + 2) / 2) * (((W + 1) + 3) & ~3);
+  (void)W;
+  const size_t groups = (size_t)(((H + 2) / 2) + 4) / 5;  // row groups of the 5-transform row pass
+  const size_t packed = groups * 5 * ((N + 3) & ~3);
   const size_t rows = (size_t)H * (((N / 2 + 1) + 3) & ~3);
   return packed > rows ? packed : rows;
 }
@@ -480,14 +514,16 @@ static cudaError_t fast_setup(K kernel, int threads, size_t smem, int* slots) {
 }
 
 template <class RS, class CS, typename T, int MODE>
-static cudaError_t run_fast(gfc_plan* P, const T* in0, const T* in1, T* out, int nf, cudaStream_t st) {
+static cudaError_t run_fast(gfc_plan* P, const Bufs& bf, const T* in0, const T* in1, T* out, int nf,
+                            cudaStream_t st) {
   FastArgs A;
   A.H = P->H; A.W = P->W; A.p = P->pad; A.M = P->M; A.N = P->N; A.Nh = P->Nh; A.ldM = P->ldM;
   A.nrows = (MODE == 0) ? P->H + 1 : P->H;
   A.ncols = (MODE == 0) ? P->W + 1 : P->W;
   A.npairs = (A.nrows + 1) / 2;
-  A.ldz = (A.ncols + 3) & ~3;
+  A.ldz = (RS::N + 3) & ~3;
   A.ngroups = (A.npairs + RS::F - 1) / RS::F;
+  A.zpairs = A.ngroups * RS::F;
   A.nparts = (P->Nh + CS::C - 1) / CS::C;
   A.nf = nf;
   A.ldY = (P->Nh + 3) & ~3;
@@ -503,51 +539,51 @@ static cudaError_t run_fast(gfc_plan* P, const T* in0, const T* in1, T* out, int
     }
   }
   auto grid_for = [](long items, int slots) { return (int)(items < slots ? items : slots); };
-  prof_begin(P, 3);
+  prof_begin(P, 3, st);
   {
     const int nq = A.ldz / 4, bx = nq >= 256 ? 256 : ((nq + 31) / 32) * 32;
-    k_fast_div<T, MODE><<<dim3((nq + bx - 1) / bx, A.npairs, nf), bx, 0, st>>>(in0, in1, P->zbuf, A);
+    k_fast_div<T, MODE><<<dim3((nq + bx - 1) / bx, A.zpairs, nf), bx, 0, st>>>(in0, in1, bf.zbuf, A);
   }
-  prof_end(P);
+  prof_end(P, st);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  prof_begin(P, 0);
+  prof_begin(P, 0, st);
   k_fast_rows_fwd<RS><<<grid_for((long)nf * A.ngroups, slots_a), RS::THREADS, RS::smem_bytes_fwd(), st>>>(
-      P->zbuf, P->spec, P->twN, A);
-  prof_end(P);
+      bf.zbuf, bf.spec, P->twN, A);
+  prof_end(P, st);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  prof_begin(P, 1);
-  k_fast_cols<CS><<<dim3(A.nparts, nf), CS::THREADS, CS::smem_bytes(), st>>>(P->spec, P->zbuf, P->GT, P->twM,
-                                                                               P->partial, A);
-  prof_end(P);
+  prof_begin(P, 1, st);
+  k_fast_cols<CS><<<dim3(A.nparts, nf), CS::THREADS, CS::smem_bytes(), st>>>(bf.spec, bf.zbuf, P->GT, P->twM,
+                                                                               bf.partial, A);
+  prof_end(P, st);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   FastArgs C = A;
   C.ngroups = ((P->H + 1) / 2 + RS::F - 1) / RS::F;
-  prof_begin(P, 2);
+  prof_begin(P, 2, st);
   k_fast_rows_inv<RS, T><<<grid_for((long)nf * C.ngroups, slots_c), RS::THREADS, RS::smem_bytes(), st>>>(
-      P->zbuf, P->partial, out, P->twN, C);
-  prof_end(P);
+      bf.zbuf, bf.partial, out, P->twN, C);
+  prof_end(P, st);
   return cudaGetLastError();
 }
 
 template <typename T>
-static cudaError_t run_fast_mode(gfc_plan* P, int mode, const void* in0, const void* in1, void* out, int nf,
-                                 cudaStream_t st) {
+static cudaError_t run_fast_mode(gfc_plan* P, const Bufs& bf, int mode, const void* in0, const void* in1, void* out,
+                                 int nf, cudaStream_t st) {
   const T* a = static_cast<const T*>(in0);
   const T* b = static_cast<const T*>(in1);
   T* o = static_cast<T*>(out);
   if (P->N == 1250 && P->M == 810) {
-    if (mode == 0) return run_fast<RowS1250, ColS810, T, 0>(P, a, b, o, nf, st);
-    return run_fast<RowS1250, ColS810, T, 1>(P, a, b, o, nf, st);
+    if (mode == 0) return run_fast<RowS1250, ColS810, T, 0>(P, bf, a, b, o, nf, st);
+    return run_fast<RowS1250, ColS810, T, 1>(P, bf, a, b, o, nf, st);
   }
   return cudaErrorNotSupported;
 }
 
-cudaError_t run_chunk_fast(gfc_plan* P, int mode, const void* in0, const void* in1, void* out, int nf,
-                           cudaStream_t st) {
+cudaError_t run_chunk_fast(gfc_plan* P, const Bufs& bf, int mode, const void* in0, const void* in1, void* out,
+                           int nf, cudaStream_t st) {
   switch (P->dtype) {
-    case GFC_F32: return run_fast_mode<float>(P, mode, in0, in1, out, nf, st);
-    case GFC_F16: return run_fast_mode<__half>(P, mode, in0, in1, out, nf, st);
-    default: return run_fast_mode<__nv_bfloat16>(P, mode, in0, in1, out, nf, st);
+    case GFC_F32: return run_fast_mode<float>(P, bf, mode, in0, in1, out, nf, st);
+    case GFC_F16: return run_fast_mode<__half>(P, bf, mode, in0, in1, out, nf, st);
+    default: return run_fast_mode<__nv_bfloat16>(P, bf, mode, in0, in1, out, nf, st);
   }
 }
 
