@@ -75,6 +75,13 @@ typedef struct {
                         forked from and joined back into the plan's stream; 0 = auto */
 } gfc_plan_opts;
 
+/* One item of a ragged batch: C fields of H x W, stored contiguously
+ * ([C, H, W], W fastest) starting `offset` elements into the caller's arrays. */
+typedef struct {
+  int H, W, C;
+  long long offset;
+} gfc_item;
+
 /* Padded-domain size for an H x W image (Algorithm A: size = image + 2 pad,
  * rounded up by the size policy). Host-only, needs no GPU. pad <= 0 selects 4.
  * Writes M, N; returns GFC_ERR_INVALID_ARG for H or W < 2 or null outputs,
@@ -89,6 +96,17 @@ gfc_status gfc_plan_create(gfc_plan** plan, int H, int W, int C, int batch, gfc_
 
 /* As gfc_plan_create, with the options above. */
 gfc_status gfc_plan_create_ex(gfc_plan** plan, const gfc_plan_opts* opts);
+
+/* Create a plan for a ragged batch of n items of different sizes (each field
+ * solved exactly as by a uniform plan of its own size: Eq. 3, Eq. 23,
+ * Algorithm B, pad 4, SMOOTH sizes). Items may share or differ in size; one
+ * Green spectrum and one pair of twiddle tables is built per distinct padded
+ * size. Fields are processed in chunks that keep the spectrum scratch within
+ * 1 GB; every pass of a chunk is one launch over all its fields. The solve,
+ * Laplacian and backward entry points take the packed arrays (each item at
+ * its offset). gfc_plan_padded_size reports the largest M and N.
+ * gfc_solve_from_gradient_host is not supported on ragged plans. Synchronous. */
+gfc_status gfc_plan_create_ragged(gfc_plan** plan, int n, const gfc_item* items, gfc_dtype dtype);
 
 /* Run later calls of this plan on `stream` (a cudaStream_t of the plan's device). */
 gfc_status gfc_plan_set_stream(gfc_plan* plan, void* stream);

@@ -16,6 +16,17 @@ struct Bufs {
   float* partial;  // per-block sums
 };
 constexpr int kMaxSlots = 4;
+
+// One field (item, channel) of a ragged batch, as the generic passes read it.
+struct FieldDesc {
+  long long in_off;    // element offset of the field in the caller's arrays
+  long long spec_off;  // complex offset of its spectrum in the chunk scratch
+  long long G_off;     // float offset of its Green table in the pool
+  int H, W, M, N, Nh, ldS;
+  int twN_off, twM_off;  // float2 offsets of its twiddle tables in the pool
+  int plan;              // index of its (row, column) transform schedules
+  int pad;
+};
 }  // namespace gfc
 
 struct gfc_plan {
@@ -53,6 +64,14 @@ struct gfc_plan {
   cudaStream_t copy_in, copy_out;
   cudaEvent_t ev_in[2], ev_comp[2], ev_out[2];
   bool host_ready;
+  // ragged batch (gfc_plan_create_ragged)
+  bool ragged;
+  int nfields;               // total fields (sum of item channels)
+  int nchunks;               // chunks of fields processed one after another
+  int* chunk_begin;          // [nchunks + 1] host: first field of each chunk
+  gfc::FieldDesc* d_desc;    // [nfields] device
+  gfc::FftPlan* d_plans;     // [2 * sizes] device: row, column schedule per distinct size
+  int maxM, maxN, maxNh, maxH, maxW;
   // tracing
   gfc_profile prof;
   bool profiling;

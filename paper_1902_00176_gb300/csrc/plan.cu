@@ -13,6 +13,10 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
+#include <utility>
+#include <vector>
+
 #include "gfc_internal.h"
 
 namespace gfc {
@@ -245,6 +249,135 @@ gfc_status gfc_plan_create_ex(gfc_plan** out, const gfc_plan_opts* o) {
   return GFC_OK;
 }
 
+gfc_status gfc_plan_create_ragged(gfc_plan** out, int n, const gfc_item* items, gfc_dtype dtype) {
+  clear_error();
+  if (!out || !items || n < 1) return fail(GFC_ERR_INVALID_ARG, "gfc_plan_create_ragged: bad arguments (n=%d)", n);
+  *out = nullptr;
+  if (dtype != GFC_F32 && dtype != GFC_F16 && dtype != GFC_BF16)
+    return fail(GFC_ERR_INVALID_ARG, "gfc_plan_create_ragged: unknown dtype %d", (int)dtype);
+  const int pad = 4;
+  // distinct padded sizes
+  std::vector<std::pair<int, int>> sizes;
+  std::vector<int> item_size(n);
+  long long nfields = 0;
+  for (int i = 0; i < n; ++i) {
+    const gfc_item& it = items[i];
+    if (it.C < 1 || it.offset < 0)
+      return fail(GFC_ERR_INVALID_ARG, "gfc_plan_create_ragged: item %d has C=%d offset=%lld", i, it.C, it.offset);
+    int M, N;
+    gfc_status st = gfc_padded_size(it.H, it.W, pad, GFC_SIZE_SMOOTH, &M, &N);
+    if (st != GFC_OK) return st;
+    int k = 0;
+    while (k < (int)sizes.size() && sizes[k] != std::make_pair(M, N)) ++k;
+    if (k == (int)sizes.size()) sizes.push_back({M, N});
+    item_size[i] = k;
+    nfields += it.C;
+  }
+  if (nfields > (1 << 24)) return fail(GFC_ERR_UNSUPPORTED, "gfc_plan_create_ragged: too many fields");
+  // pooled tables and schedules
+  std::vector<FftPlan> plans(2 * sizes.size());
+  std::vector<int> twN_off(sizes.size()), twM_off(sizes.size());
+  std::vector<long long> G_off(sizes.size());
+  int tw_total = 0;
+  long long g_total = 0;
+  for (size_t k = 0; k < sizes.size(); ++k) {
+    const int M = sizes[k].first, N = sizes[k].second;
+    if (!make_fft_plan(N, &plans[2 * k]) || !make_fft_plan(M, &plans[2 * k + 1]))
+      return fail(GFC_ERR_UNSUPPORTED, "gfc_plan_create_ragged: no FFT schedule for %dx%d", M, N);
+    twN_off[k] = tw_total;
+    tw_total += N;
+    twM_off[k] = tw_total;
+    tw_total += M;
+    G_off[k] = g_total;
+    g_total += (long long)M * (N / 2 + 1);
+  }
+  // field descriptors and chunks (spectrum scratch of a chunk <= 1 GB, <= 65535 fields)
+  const long long budget = (1ll << 30) / (long long)sizeof(float2);
+  std::vector<FieldDesc> desc((size_t)nfields);
+  std::vector<int> chunk_begin(1, 0);
+  long long used = 0, max_chunk = 0;
+  int fidx = 0, maxM = 0, maxN = 0, maxH = 0, maxW = 0;
+  for (int i = 0; i < n; ++i) {
+    const gfc_item& it = items[i];
+    const int k = item_size[i], M = sizes[k].first, N = sizes[k].second;
+    const int Nh = N / 2 + 1, ldS = (Nh + 3) & ~3;
+    const long long need = (long long)M * ldS;
+    for (int c = 0; c < it.C; ++c, ++fidx) {
+      const int in_chunk = fidx - chunk_begin.back();
+      if (in_chunk > 0 && (used + need > budget || in_chunk >= 65535)) {
+        chunk_begin.push_back(fidx);
+        used = 0;
+      }
+      FieldDesc& d = desc[fidx];
+      d.in_off = it.offset + (long long)c * it.H * it.W;
+      d.spec_off = used;
+      d.G_off = G_off[k];
+      d.H = it.H; d.W = it.W; d.M = M; d.N = N; d.Nh = Nh; d.ldS = ldS;
+      d.twN_off = twN_off[k]; d.twM_off = twM_off[k];
+      d.plan = k;
+      d.pad = pad;
+      used += need;
+      if (used > max_chunk) max_chunk = used;
+    }
+    if (M > maxM) maxM = M;
+    if (N > maxN) maxN = N;
+    if (it.H > maxH) maxH = it.H;
+    if (it.W > maxW) maxW = it.W;
+  }
+  chunk_begin.push_back((int)nfields);
+  int max_fields_chunk = 0;
+  for (size_t c = 0; c + 1 < chunk_begin.size(); ++c)
+    max_fields_chunk = std::max(max_fields_chunk, chunk_begin[c + 1] - chunk_begin[c]);
+
+  gfc_plan* p = (gfc_plan*)calloc(1, sizeof(gfc_plan));
+  if (!p) return fail(GFC_ERR_ALLOC, "gfc_plan_create_ragged: host allocation failed");
+  p->ragged = true;
+  p->H = maxH; p->W = maxW; p->C = 1; p->batch = (int)nfields; p->pad = pad; p->dtype = dtype;
+  p->M = maxM; p->N = maxN; p->Nh = maxN / 2 + 1; p->ldS = (p->Nh + 3) & ~3; p->ldM = (maxM + 3) & ~3;
+  p->maxM = maxM; p->maxN = maxN; p->maxNh = maxN / 2 + 1; p->maxH = maxH; p->maxW = maxW;
+  p->nfields = (int)nfields;
+  p->nchunks = (int)chunk_begin.size() - 1;
+  p->chunk = max_fields_chunk;
+  p->nslots = 1;
+  p->spec_field = 0;
+  p->chunk_begin = (int*)malloc(chunk_begin.size() * sizeof(int));
+  if (!p->chunk_begin) {
+    free(p);
+    return fail(GFC_ERR_ALLOC, "gfc_plan_create_ragged: host allocation failed");
+  }
+  memcpy(p->chunk_begin, chunk_begin.data(), chunk_begin.size() * sizeof(int));
+  cudaError_t e = cudaGetDevice(&p->device);
+  if (e == cudaSuccess) e = cudaMalloc(&p->twN, (size_t)tw_total * sizeof(float2));
+  if (e == cudaSuccess) e = cudaMalloc(&p->G, (size_t)g_total * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&p->d_desc, desc.size() * sizeof(FieldDesc));
+  if (e == cudaSuccess) e = cudaMalloc(&p->d_plans, plans.size() * sizeof(FftPlan));
+  if (e == cudaSuccess) e = cudaMalloc(&p->spec, (size_t)max_chunk * sizeof(float2));
+  if (e == cudaSuccess) e = cudaMalloc(&p->partial, (size_t)max_fields_chunk * kMaxRowBlocks * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&p->dev_err, sizeof(int));
+  cudaStream_t bs = nullptr;
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaMemsetAsync(p->dev_err, 0, sizeof(int), bs);
+  for (size_t k = 0; k < sizes.size() && e == cudaSuccess; ++k) {
+    const int M = sizes[k].first, N = sizes[k].second;
+    e = build_twiddles(p->twN + twN_off[k], N, bs);
+    if (e == cudaSuccess) e = build_twiddles(p->twN + twM_off[k], M, bs);
+    if (e == cudaSuccess) e = build_green(p->G + G_off[k], M, N, N / 2 + 1, bs);
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(p->d_desc, desc.data(), desc.size() * sizeof(FieldDesc), cudaMemcpyHostToDevice, bs);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(p->d_plans, plans.data(), plans.size() * sizeof(FftPlan), cudaMemcpyHostToDevice, bs);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(bs);
+  if (bs) cudaStreamDestroy(bs);
+  if (e != cudaSuccess) {
+    gfc_status st = cuda_fail(e, "gfc_plan_create_ragged");
+    destroy_plan(p);
+    return st;
+  }
+  *out = p;
+  return GFC_OK;
+}
+
 gfc_status gfc_plan_create(gfc_plan** plan, int H, int W, int C, int batch, gfc_dtype dtype) {
   gfc_plan_opts o;
   memset(&o, 0, sizeof(o));
@@ -296,6 +429,9 @@ static void destroy_plan(gfc_plan* p) {
   release_host_state(p);
   cudaFree(p->G);
   cudaFree(p->GT);
+  cudaFree(p->d_desc);
+  cudaFree(p->d_plans);
+  free(p->chunk_begin);
   cudaFree(p->zbuf);
   cudaFree(p->twN);
   cudaFree(p->twM);

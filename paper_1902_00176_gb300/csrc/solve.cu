@@ -36,7 +36,35 @@ struct PassArgs {
   int ppb;           // row pairs per block
   int nparts;        // pass A blocks per field (adjoint partial sums)
   FftPlan plan;      // the transform this pass runs
+  // ragged batches: per-field sizes and offsets (nullptr for a uniform batch)
+  const FieldDesc* fd;
+  const FftPlan* plans;
 };
+
+// Load this block's field descriptor into A (ragged batches). pass: 0 row
+// forward, 1 column, 2 row inverse. Returns false if the block has no work in
+// its field (grids are sized for the largest field).
+template <int MODE>
+__device__ __forceinline__ bool ragged_field(PassArgs& A, int pass, FieldDesc& d) {
+  d = A.fd[blockIdx.y];
+  A.H = d.H; A.W = d.W; A.M = d.M; A.N = d.N; A.Nh = d.Nh; A.ldS = d.ldS; A.p = d.pad;
+  A.nrows = (MODE == 0) ? d.H + 1 : d.H;
+  A.ncols = (MODE == 0) ? d.W + 1 : d.W;
+  const int pairs_in = (A.nrows + 1) / 2;
+  A.nparts = (pairs_in + A.ppb - 1) / A.ppb;
+  if (pass == 0) {
+    A.plan = A.plans[2 * d.plan];
+    A.pairs = pairs_in;
+    return (int)blockIdx.x < A.nparts;
+  }
+  if (pass == 1) {
+    A.plan = A.plans[2 * d.plan + 1];
+    return (int)blockIdx.x * A.pairs < A.Nh;  // A.pairs carries the strip width here
+  }
+  A.plan = A.plans[2 * d.plan];
+  A.pairs = (d.H + 1) / 2;
+  return (int)blockIdx.x * A.ppb < A.pairs;
+}
 
 __device__ __forceinline__ float to_f(float x) { return x; }
 __device__ __forceinline__ float to_f(__half x) { return __half2float(x); }
@@ -87,14 +115,21 @@ __global__ void __launch_bounds__(256) k_pass_a(const T* __restrict__ in0, const
                                                 const float2* __restrict__ twg, PassArgs A) {
   extern __shared__ float2 sm[];
   __shared__ float red[32];
+  long long in_off = (long long)blockIdx.y * A.H * A.W, spec_off = (long long)blockIdx.y * A.M * A.ldS;
+  if (A.fd) {
+    FieldDesc d;
+    if (!ragged_field<MODE>(A, 0, d)) return;
+    in_off = d.in_off;
+    spec_off = d.spec_off;
+    twg += d.twN_off;
+  }
   float2* tw = sm;
   float2* b0 = sm + A.N;
   float2* b1 = b0 + A.N;
   const int tid = threadIdx.x, nthr = blockDim.x;
-  const size_t fe = (size_t)A.H * A.W;
-  const T* a = in0 + blockIdx.y * fe;
-  const T* b = (MODE == kGrad) ? in1 + blockIdx.y * fe : nullptr;
-  float2* S = spec + (size_t)blockIdx.y * A.M * A.ldS;
+  const T* a = in0 + in_off;
+  const T* b = (MODE == kGrad) ? in1 + in_off : nullptr;
+  float2* S = spec + spec_off;
   for (int m = tid; m < A.N; m += nthr) tw[m] = twg[m];
   float acc = 0.0f;
   const int q0 = blockIdx.x * A.ppb;
@@ -142,12 +177,21 @@ __global__ void __launch_bounds__(256) k_pass_b(float2* __restrict__ spec, const
                                                 const float2* __restrict__ twg, const float* __restrict__ partial,
                                                 PassArgs A) {
   extern __shared__ float2 sm[];
+  long long spec_off = (long long)blockIdx.y * A.M * A.ldS;
+  if (A.fd) {
+    FieldDesc d;
+    A.pairs = S;
+    if (!ragged_field<MODE>(A, 1, d)) return;
+    spec_off = d.spec_off;
+    twg += d.twM_off;
+    G += d.G_off;
+  }
   float2* tw = sm;
   float2* b0 = sm + A.M;
   float2* b1 = b0 + (size_t)A.M * S;
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int l0 = blockIdx.x * S;
-  float2* Sp = spec + (size_t)blockIdx.y * A.M * A.ldS;
+  float2* Sp = spec + spec_off;
   for (int m = tid; m < A.M; m += nthr) tw[m] = twg[m];
   float tot = 0.0f;
   if (MODE == kAdj) {
@@ -205,12 +249,20 @@ __global__ void __launch_bounds__(256) k_pass_c(const float2* __restrict__ spec,
                                                 const float2* __restrict__ twg, PassArgs A) {
   extern __shared__ float2 sm[];
   __shared__ double redd[32];
+  long long out_off = (long long)blockIdx.y * A.H * A.W, spec_off = (long long)blockIdx.y * A.M * A.ldS;
+  if (A.fd) {
+    FieldDesc d;
+    if (!ragged_field<kGrad>(A, 2, d)) return;
+    out_off = d.in_off;
+    spec_off = d.spec_off;
+    twg += d.twN_off;
+  }
   float2* tw = sm;
   float2* b0 = sm + A.N;
   float2* b1 = b0 + A.N;
   const int tid = threadIdx.x, nthr = blockDim.x;
-  const float2* Sp = spec + (size_t)blockIdx.y * A.M * A.ldS;
-  T* o = out + (size_t)blockIdx.y * A.H * A.W;
+  const float2* Sp = spec + spec_off;
+  T* o = out + out_off;
   for (int m = tid; m < A.N; m += nthr) tw[m] = twg[m];
   // u[0,0] = sum over the full row-0 spectrum = Re Y[0] + Re Y[N/2] + 2 sum_{0<l<N/2} Re Y[l],
   // accumulated in FP64 (an error in u[0,0] shifts every output pixel)
@@ -250,11 +302,22 @@ __global__ void __launch_bounds__(256) k_pass_c_adj(const float2* __restrict__ s
   float2* tw = sm;
   float2* b0 = sm + A.N;
   float2* b1 = b0 + A.N;
-  float* prev = reinterpret_cast<float*>(b1 + A.N);  // [W] row 2q-1 of w from the previous pair
   const int tid = threadIdx.x, nthr = blockDim.x;
-  const float2* Sp = spec + (size_t)blockIdx.y * A.M * A.ldS;
-  T* gx = ggx + (size_t)blockIdx.y * A.H * A.W;
-  T* gy = ggy + (size_t)blockIdx.y * A.H * A.W;
+  long long out_off = (long long)blockIdx.y * A.H * A.W, spec_off = (long long)blockIdx.y * A.M * A.ldS;
+  if (A.fd) {
+    FieldDesc d;
+    if (!ragged_field<kAdj>(A, 2, d)) return;
+    out_off = d.in_off;
+    spec_off = d.spec_off;
+    twg += d.twN_off;
+    tw = sm;
+    b0 = sm + A.N;
+    b1 = b0 + A.N;
+  }
+  float* prev = reinterpret_cast<float*>(b1 + A.N);  // [W] row 2q-1 of w from the previous pair
+  const float2* Sp = spec + spec_off;
+  T* gx = ggx + out_off;
+  T* gy = ggy + out_off;
   for (int m = tid; m < A.N; m += nthr) tw[m] = twg[m];
   const int q0 = blockIdx.x * A.ppb;
   const int q1 = min(q0 + A.ppb, A.pairs);
@@ -367,6 +430,8 @@ static PassArgs base_args(const gfc_plan* P) {
   a.H = P->H; a.W = P->W; a.p = P->pad; a.M = P->M; a.N = P->N; a.Nh = P->Nh; a.ldS = P->ldS;
   a.nrows = a.ncols = a.pairs = a.ppb = a.nparts = 0;
   a.plan = P->rowplan;
+  a.fd = nullptr;
+  a.plans = nullptr;
   return a;
 }
 
@@ -475,8 +540,90 @@ static gfc_status run_all(gfc_plan* P, const void* a, const void* b, void* o0, v
   return GFC_OK;
 }
 
+// Ragged batches: per chunk of fields, each pass is one launch over all its
+// fields; every block reads its field's descriptor (sizes, table offsets,
+// schedules) and grids are sized for the largest field.
+template <typename T, int MODE>
+static gfc_status run_ragged(gfc_plan* P, const void* a, const void* b, void* o0, void* o1) {
+  cudaStream_t st = P->stream;
+  P->prof.calls += 1;
+  const int nrows_max = (MODE == kGrad) ? P->maxH + 1 : P->maxH;
+  const int pairs_max = (nrows_max + 1) / 2;
+  int ppb = 4;
+  if (ceil_div(pairs_max, ppb) > kMaxRowBlocks) ppb = ceil_div(pairs_max, kMaxRowBlocks);
+  const int S = pick_strip(P->maxM);
+  for (int c = 0; c < P->nchunks; ++c) {
+    const int f0 = P->chunk_begin[c], nf = P->chunk_begin[c + 1] - f0;
+    PassArgs A = base_args(P);
+    A.M = P->maxM;
+    A.N = P->maxN;
+    A.ppb = ppb;
+    A.fd = P->d_desc + f0;
+    A.plans = P->d_plans;
+    cudaError_t e;
+    {
+      const size_t smem = 3 * (size_t)P->maxN * sizeof(float2);
+      auto k = k_pass_a<T, MODE>;
+      if ((e = ensure_smem(k, smem)) != cudaSuccess) return cuda_fail(e, "gfc ragged pass A");
+      prof_begin(P, 0, st);
+      k<<<dim3(ceil_div(pairs_max, ppb), nf), 256, smem, st>>>(static_cast<const T*>(a), static_cast<const T*>(b),
+                                                                 P->spec, P->partial, P->twN, A);
+      prof_end(P, st);
+      if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "gfc ragged pass A");
+    }
+    {
+      const size_t smem = (size_t)(P->maxM + 2 * (size_t)P->maxM * S) * sizeof(float2);
+      const dim3 grid(ceil_div(P->maxNh, S), nf);
+      prof_begin(P, 1, st);
+      switch (S) {
+        case 8:
+          if ((e = ensure_smem(k_pass_b<8, MODE>, smem)) != cudaSuccess) break;
+          k_pass_b<8, MODE><<<grid, 256, smem, st>>>(P->spec, P->G, P->twN, P->partial, A);
+          break;
+        case 4:
+          if ((e = ensure_smem(k_pass_b<4, MODE>, smem)) != cudaSuccess) break;
+          k_pass_b<4, MODE><<<grid, 256, smem, st>>>(P->spec, P->G, P->twN, P->partial, A);
+          break;
+        case 2:
+          if ((e = ensure_smem(k_pass_b<2, MODE>, smem)) != cudaSuccess) break;
+          k_pass_b<2, MODE><<<grid, 256, smem, st>>>(P->spec, P->G, P->twN, P->partial, A);
+          break;
+        default:
+          if ((e = ensure_smem(k_pass_b<1, MODE>, smem)) != cudaSuccess) break;
+          k_pass_b<1, MODE><<<grid, 256, smem, st>>>(P->spec, P->G, P->twN, P->partial, A);
+      }
+      prof_end(P, st);
+      if (e != cudaSuccess || (e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "gfc ragged pass B");
+    }
+    {
+      const int pairs_out = (P->maxH + 1) / 2;
+      const dim3 grid(ceil_div(pairs_out, ppb), nf);
+      prof_begin(P, 2, st);
+      if (MODE == kAdj) {
+        const size_t smem = 3 * (size_t)P->maxN * sizeof(float2) + (size_t)P->maxW * sizeof(float);
+        if ((e = ensure_smem(k_pass_c_adj<T>, smem)) == cudaSuccess)
+          k_pass_c_adj<T><<<grid, 256, smem, st>>>(P->spec, static_cast<T*>(o0), static_cast<T*>(o1), P->twN, A);
+      } else {
+        const size_t smem = 3 * (size_t)P->maxN * sizeof(float2);
+        if ((e = ensure_smem(k_pass_c<T>, smem)) == cudaSuccess)
+          k_pass_c<T><<<grid, 256, smem, st>>>(P->spec, static_cast<T*>(o0), P->twN, A);
+      }
+      prof_end(P, st);
+      if (e != cudaSuccess || (e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "gfc ragged pass C");
+    }
+  }
+  return GFC_OK;
+}
+
 template <int MODE>
 static gfc_status dispatch(gfc_plan* P, const void* a, const void* b, void* o0, void* o1) {
+  if (P->ragged) {
+    switch (P->dtype) {
+      case GFC_F32: return run_ragged<float, MODE>(P, a, b, o0, o1);
+      case GFC_F16: return run_ragged<__half, MODE>(P, a, b, o0, o1);
+      default: return run_ragged<__nv_bfloat16, MODE>(P, a, b, o0, o1);
+    }
+  }
   switch (P->dtype) {
     case GFC_F32: return run_all<float, MODE>(P, a, b, o0, o1);
     case GFC_F16: return run_all<__half, MODE>(P, a, b, o0, o1);
@@ -614,6 +761,7 @@ gfc_status gfc_solve_from_gradient_host(gfc_plan* plan, const void* gx, const vo
   clear_error();
   if (!plan || !gx || !gy || !out) return fail(GFC_ERR_INVALID_ARG, "gfc_solve_from_gradient_host: null argument");
   if (out == gx || out == gy) return fail(GFC_ERR_INVALID_ARG, "gfc_solve_from_gradient_host: out aliases an input");
+  if (plan->ragged) return fail(GFC_ERR_UNSUPPORTED, "gfc_solve_from_gradient_host: not available for ragged plans");
   switch (plan->dtype) {
     case GFC_F32: return run_host<float>(plan, gx, gy, out);
     case GFC_F16: return run_host<__half>(plan, gx, gy, out);

@@ -40,6 +40,11 @@ class _Opts(ctypes.Structure):
                 ("chunk", ctypes.c_int), ("stream", ctypes.c_void_p), ("streams", ctypes.c_int)]
 
 
+class Item(ctypes.Structure):
+    """Mirror of gfc_item: C fields of H x W at `offset` elements into the packed arrays."""
+    _fields_ = [("H", ctypes.c_int), ("W", ctypes.c_int), ("C", ctypes.c_int), ("offset", ctypes.c_longlong)]
+
+
 class Profile(ctypes.Structure):
     """Mirror of gfc_profile: per-pass device time (ms) and launch counts."""
     _fields_ = [("pass_ms", ctypes.c_double * 4), ("launches", ctypes.c_long * 4), ("calls", ctypes.c_long),
@@ -60,6 +65,7 @@ _SIGNATURES = {
     "gfc_plan_create": [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                         ctypes.c_int],
     "gfc_plan_create_ex": [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(_Opts)],
+    "gfc_plan_create_ragged": [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_void_p, ctypes.c_int],
     "gfc_plan_set_stream": [ctypes.c_void_p, ctypes.c_void_p],
     "gfc_plan_padded_size": [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                              ctypes.POINTER(ctypes.c_int)],
@@ -305,3 +311,86 @@ class GFCFunction(torch.autograd.Function):
 def gfc_layer(gx: torch.Tensor, gy: torch.Tensor) -> torch.Tensor:
     """Differentiable GFC solve (see GFCFunction)."""
     return GFCFunction.apply(gx, gy)
+
+
+class RaggedPlan:
+    """A plan for a ragged batch: items of different sizes packed into one flat array.
+
+    ``items`` is a list of ``(C, H, W)``; item i occupies ``C*H*W`` contiguous
+    elements ([C, H, W]) starting at ``offsets[i]`` of the packed arrays.
+    """
+
+    def __init__(self, items, dtype=torch.float32, device=None):
+        if dtype not in _DTYPES:
+            raise ValueError(f"unsupported dtype {dtype}")
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else
+                                   torch.device(device).index or 0)
+        self.items = [tuple(int(v) for v in it) for it in items]
+        self.dtype = dtype
+        self.offsets, off = [], 0
+        for (C, H, W) in self.items:
+            self.offsets.append(off)
+            off += C * H * W
+            off = (off + 7) // 8 * 8  # keep every item 16-byte aligned in any dtype
+        self.total = off
+        arr = (Item * len(self.items))(*[Item(H, W, C, o) for (C, H, W), o in zip(self.items, self.offsets)])
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            _check(lib().gfc_plan_create_ragged(ctypes.byref(h), len(self.items), ctypes.cast(arr, ctypes.c_void_p),
+                                                _DTYPES[dtype]))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().gfc_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def empty(self):
+        return torch.zeros(self.total, dtype=self.dtype, device=self.device)
+
+    def pack(self, tensors):
+        """Pack a list of [C, H, W] tensors (one per item) into a flat array."""
+        flat = self.empty()
+        for t, (C, H, W), o in zip(tensors, self.items, self.offsets):
+            flat[o:o + C * H * W] = t.reshape(-1).to(self.device, self.dtype)
+        return flat
+
+    def unpack(self, flat):
+        return [flat[o:o + C * H * W].view(C, H, W) for (C, H, W), o in zip(self.items, self.offsets)]
+
+    def _check_flat(self, t, name):
+        if not t.is_cuda or t.device != self.device or t.dtype != self.dtype or t.numel() != self.total \
+                or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous {self.dtype} CUDA tensor of {self.total} elements")
+        return t
+
+    def _bind_stream(self):
+        _check(lib().gfc_plan_set_stream(self._h, ctypes.c_void_p(_stream_ptr(self.device))))
+
+    def solve_from_gradient(self, gx, gy, out=None):
+        gx, gy = self._check_flat(gx, "gx"), self._check_flat(gy, "gy")
+        out = self.empty() if out is None else self._check_flat(out, "out")
+        self._bind_stream()
+        _check(lib().gfc_solve_from_gradient(self._h, gx.data_ptr(), gy.data_ptr(), out.data_ptr()))
+        return out
+
+    def solve_from_laplacian(self, lap, out=None):
+        lap = self._check_flat(lap, "lap")
+        out = self.empty() if out is None else self._check_flat(out, "out")
+        self._bind_stream()
+        _check(lib().gfc_solve_from_laplacian(self._h, lap.data_ptr(), out.data_ptr()))
+        return out
+
+    def backward(self, grad_out, grad_gx=None, grad_gy=None):
+        grad_out = self._check_flat(grad_out, "grad_out")
+        grad_gx = self.empty() if grad_gx is None else self._check_flat(grad_gx, "grad_gx")
+        grad_gy = self.empty() if grad_gy is None else self._check_flat(grad_gy, "grad_gy")
+        self._bind_stream()
+        _check(lib().gfc_backward(self._h, grad_out.data_ptr(), grad_gx.data_ptr(), grad_gy.data_ptr()))
+        return grad_gx, grad_gy

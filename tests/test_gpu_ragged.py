@@ -1,0 +1,106 @@
+"""Ragged batches (items of different sizes in one plan) against the oracle and
+against uniform plans of each item's size."""
+import numpy as np
+import pytest
+import torch
+
+import oracle.gfc_oracle as O
+from paper_1902_00176_gb300 import gfc, synth
+
+pytestmark = pytest.mark.gpu
+DEV = torch.device("cuda:0")
+REL_F32 = 1e-5
+
+
+@pytest.fixture(autouse=True)
+def _lib(gfc_lib):
+    yield
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def _items_small():
+    return [(1, 37, 50), (3, 64, 96), (1, 20, 20), (2, 101, 33), (1, 64, 96), (3, 9, 140)]
+
+
+def _inputs(items, seed=0):
+    gxs, gys = [], []
+    for i, (C, H, W) in enumerate(items):
+        gx, gy = synth.ragged_item_gradients((C, H, W), item=i, seed=seed)
+        gxs.append(torch.from_numpy(gx))
+        gys.append(torch.from_numpy(gy))
+    return gxs, gys
+
+
+def test_ragged_matches_oracle_per_item():
+    items = _items_small()
+    gxs, gys = _inputs(items)
+    rp = gfc.RaggedPlan(items, device=DEV)
+    out = rp.unpack(rp.solve_from_gradient(rp.pack(gxs), rp.pack(gys)))
+    torch.cuda.synchronize()
+    for (C, H, W), gx, gy, o in zip(items, gxs, gys, out):
+        M, N = gfc.padded_size(H, W)
+        ref = O.solve_from_gradient_batch(gx.double().numpy(), gy.double().numpy(), M, N, 4)
+        assert _rel(o.double().cpu().numpy(), ref) <= REL_F32, (C, H, W)
+    rp.close()
+
+
+def test_ragged_is_bitwise_equal_to_uniform_generic_plans(monkeypatch):
+    items = _items_small()
+    gxs, gys = _inputs(items, seed=1)
+    rp = gfc.RaggedPlan(items, device=DEV)
+    out = rp.unpack(rp.solve_from_gradient(rp.pack(gxs), rp.pack(gys)))
+    monkeypatch.setenv("GFC_FORCE_GENERIC", "1")
+    for (C, H, W), gx, gy, o in zip(items, gxs, gys, out):
+        p = gfc.Plan(H, W, C, 1, device=DEV)
+        ref = p.solve_from_gradient(gx.view(1, C, H, W).to(DEV), gy.view(1, C, H, W).to(DEV))[0]
+        assert torch.equal(o, ref), (C, H, W)
+        p.close()
+    rp.close()
+
+
+def test_ragged_laplacian_and_adjoint_modes():
+    items = [(1, 30, 45), (2, 17, 64), (1, 64, 20)]
+    rng = np.random.default_rng(3)
+    laps = [torch.from_numpy(rng.standard_normal((C, H, W)).astype(np.float32) * 0.01) for (C, H, W) in items]
+    rp = gfc.RaggedPlan(items, device=DEV)
+    out = rp.unpack(rp.solve_from_laplacian(rp.pack(laps)))
+    bx, by = rp.backward(rp.pack(laps))
+    bx, by = rp.unpack(bx), rp.unpack(by)
+    torch.cuda.synchronize()
+    for (C, H, W), lap, o, gx_, gy_ in zip(items, laps, out, bx, by):
+        M, N = gfc.padded_size(H, W)
+        ref = O.solve_from_laplacian_batch(lap.double().numpy(), M, N, 4)
+        assert _rel(o.double().cpu().numpy(), ref) <= REL_F32
+        rx, ry = O.backward_batch(lap.double().numpy(), M, N, 4)
+        assert _rel(gx_.double().cpu().numpy(), rx) <= REL_F32
+        assert _rel(gy_.double().cpu().numpy(), ry) <= REL_F32
+    rp.close()
+
+
+def test_ragged_workload_shapes_sampled():
+    """The 64-item ragged workload (C in {1,3}, H, W in [128, 2048]); a few items checked in full."""
+    items = synth.ragged_items()
+    rp = gfc.RaggedPlan(items, device=DEV)
+    gx = rp.empty()
+    gy = rp.empty()
+    check = [0, 17, 63]
+    for i in check:
+        C, H, W = items[i]
+        a, b = synth.ragged_item_gradients((C, H, W), item=i)
+        o = rp.offsets[i]
+        gx[o:o + C * H * W] = torch.from_numpy(a).reshape(-1).to(DEV)
+        gy[o:o + C * H * W] = torch.from_numpy(b).reshape(-1).to(DEV)
+    out = rp.solve_from_gradient(gx, gy)
+    torch.cuda.synchronize()
+    for i in check:
+        C, H, W = items[i]
+        o = rp.offsets[i]
+        M, N = gfc.padded_size(H, W)
+        ref = O.solve_from_gradient(gx[o:o + H * W].view(H, W).double().cpu().numpy(),
+                                    gy[o:o + H * W].view(H, W).double().cpu().numpy(), M, N, 4)
+        got = out[o:o + H * W].view(H, W).double().cpu().numpy()
+        assert _rel(got, ref) <= REL_F32, items[i]
+    rp.close()
