@@ -41,6 +41,29 @@ UNIT = "solves/s"
 WORKLOAD = "GFC solve from gradient, 100 x 1 x 801x1200 fp32 per GPU (perturbed smooth images)"
 
 
+def rank_seed(rank: int, batch: int) -> int:
+    """First generator seed of a rank's shard: ranks solve disjoint sets of fields
+    (weak scaling: every rank holds `batch` fields, no data-path collective)."""
+    return 1000 + batch * rank
+
+
+def max_over_ranks(ms: float, world: int, device=None) -> float:
+    """Slowest rank's elapsed time (the job is as fast as its slowest rank)."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(fields_per_rank: int, world: int, steps: int, ms_total: float) -> float:
+    """Whole-job throughput: fields solved by all ranks per second of the slowest rank."""
+    return fields_per_rank * world * steps / (ms_total / 1000.0)
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -182,7 +205,7 @@ def run_gfc(args, rank, world, local_rank):
 
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
-    gx, gy = synth.perturbed_gradient_batch(batch=B, H=H, W=W, seed=1000 + B * rank)
+    gx, gy = synth.perturbed_gradient_batch(batch=B, H=H, W=W, seed=rank_seed(rank, B))
     tx = torch.from_numpy(gx).to(dev)
     ty = torch.from_numpy(gy).to(dev)
     out = torch.empty_like(tx)
@@ -221,12 +244,9 @@ def run_gfc(args, rank, world, local_rank):
     ms_total = e0.elapsed_time(e1)
     prof = plan.profile(reset=True)
     plan.set_profiling(False)
-    if world > 1:
-        t = torch.tensor([ms_total], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total = max_over_ranks(ms_total, world, dev)
     ms_step = ms_total / args.steps
-    value = B * world * args.steps / (ms_total / 1000.0)
+    value = job_rate(B, world, args.steps, ms_total)
 
     e2e = None
     if not args.no_e2e:
@@ -270,6 +290,8 @@ def run_gfc(args, rank, world, local_rank):
         "gpu_launches": int(sum(prof["launches"])),
         "clocks": clocks,
     }
+    if not args.no_extra:
+        line["extra_workloads"] = extra_workloads(torch.device("cuda", local_rank))
     if not args.no_cpu_baseline:
         rate, n, el = cpu_oracle_rate(args.cpu_budget)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
@@ -299,15 +321,102 @@ def _e2e(args, plan, gx, gy, out, dev, stream, world, barrier):
         plan.solve_from_gradient_host(hx, hy, ho)
     e1.record(stream)
     torch.cuda.synchronize(dev)
-    ms = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
     ok = bool(np.array_equal(ho.numpy()[B // 2], out.cpu().numpy()[B // 2]))
     fe = H * W
-    return {"value": B * world * steps / (ms / 1000.0), "unit": UNIT, "h2d_bytes_per_step": 2 * 4 * fe * B,
+    return {"value": job_rate(B, world, steps, ms), "unit": UNIT, "h2d_bytes_per_step": 2 * 4 * fe * B,
             "d2h_bytes_per_step": 4 * fe * B, "steps": steps, "matches_device_result": ok}
+
+
+def _time_ms(fn, dev, reps):
+    import torch
+
+    for _ in range(2):
+        fn()
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize(dev)
+    return e0.elapsed_time(e1) / reps
+
+
+def extra_workloads(dev):
+    """The other workload shapes of the method, each timed on this GPU (inputs resident)."""
+    import torch
+
+    from paper_1902_00176_gb300 import gfc, synth
+
+    res = {}
+    # single 64x96 field with gradient removal: plain call vs captured graph replay
+    img, gx, gy = synth.gradient_removal_image(seed=0)
+    p = gfc.Plan(64, 96, device=dev)
+    tx = torch.from_numpy(gx).to(dev).view(1, 1, 64, 96)
+    ty = torch.from_numpy(gy).to(dev).view(1, 1, 64, 96)
+    out = torch.empty_like(tx)
+    ms = _time_ms(lambda: p.solve_from_gradient(tx, ty, out), dev, 200)
+    g = gfc.Graph(p, "gradient", tx, ty, out)
+    msg = _time_ms(g.launch, dev, 200)
+    res["single_64x96_fp32"] = {"ms_per_solve": ms, "ms_per_solve_graph": msg, "solves_per_s": 1000.0 / ms,
+                                "solves_per_s_graph": 1000.0 / msg}
+    g.close()
+    p.close()
+    # Poisson blending batch 16 x 3 x 1024x1536, fp32 and fp16 storage
+    bx, by, _ = synth.poisson_blend_batch()
+    for dt, name in ((torch.float32, "fp32"), (torch.float16, "fp16")):
+        tx = torch.from_numpy(bx).to(dev).to(dt)
+        ty = torch.from_numpy(by).to(dev).to(dt)
+        p = gfc.Plan(1024, 1536, 3, 16, dt, device=dev)
+        out = torch.empty_like(tx)
+        ms = _time_ms(lambda: p.solve_from_gradient(tx, ty, out), dev, 10)
+        res[f"blend_16x3x1024x1536_{name}"] = {"ms_per_batch": ms, "solves_per_s": 48 * 1000.0 / ms}
+        p.close()
+    del bx, by
+    # ragged batch of 64 items vs 64 sequential plain solves
+    items = synth.ragged_items()
+    rp = gfc.RaggedPlan(items, device=dev)
+    gxr = torch.randn(rp.total, device=dev) * 0.01
+    gyr = torch.randn(rp.total, device=dev) * 0.01
+    outr = rp.empty()
+    ms = _time_ms(lambda: rp.solve_from_gradient(gxr, gyr, outr), dev, 5)
+    gr = gfc.Graph(rp, "gradient", gxr, gyr, outr)
+    msg = _time_ms(gr.launch, dev, 5)
+    plans = [gfc.Plan(h, w, c, 1, device=dev) for c, h, w in items]
+    views = [(gxr[o:o + c * h * w].view(1, c, h, w), gyr[o:o + c * h * w].view(1, c, h, w),
+              outr[o:o + c * h * w].view(1, c, h, w)) for (c, h, w), o in zip(items, rp.offsets)]
+
+    def seq():
+        for pl, (a, b, o) in zip(plans, views):
+            pl.solve_from_gradient(a, b, o)
+
+    ms_seq = _time_ms(seq, dev, 3)
+    nf = sum(c for c, h, w in items)
+    res["ragged_64_items"] = {"fields": nf, "ms": ms, "ms_graph": msg, "solves_per_s": nf * 1000.0 / ms,
+                              "ms_sequential_plans": ms_seq, "speedup_vs_sequential": ms_seq / ms}
+    gr.close()
+    rp.close()
+    for pl in plans:
+        pl.close()
+    # differentiable layer: 32 x 64 x 256x256 bf16 storage, forward + hand-written adjoint
+    fx, fy = synth.feature_gradients()
+    tx = torch.from_numpy(fx).to(dev).to(torch.bfloat16)
+    ty = torch.from_numpy(fy).to(dev).to(torch.bfloat16)
+    del fx, fy
+    go = torch.randn(tx.shape, device=dev).to(torch.bfloat16)
+    p = gfc.Plan(256, 256, 64, 32, torch.bfloat16, device=dev)
+    out = torch.empty_like(tx)
+    gx_, gy_ = torch.empty_like(tx), torch.empty_like(tx)
+    ms_f = _time_ms(lambda: p.solve_from_gradient(tx, ty, out), dev, 5)
+    ms_b = _time_ms(lambda: p.backward(go, gx_, gy_), dev, 5)
+    nfld = 32 * 64
+    res["layer_32x64x256x256_bf16"] = {"ms_forward": ms_f, "ms_backward": ms_b,
+                                       "fwd_solves_per_s": nfld * 1000.0 / ms_f,
+                                       "fwd_bwd_solves_per_s": nfld * 1000.0 / (ms_f + ms_b)}
+    p.close()
+    return res
 
 
 def _kernel_build_id() -> str:
@@ -332,6 +441,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--batch", type=int, default=100, help="fields per GPU (lower only for ncu captures)")
+    ap.add_argument("--no-extra", action="store_true", help="skip the other workload shapes")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -200,6 +200,23 @@ gfc_status gfc_plan_get_profile(gfc_plan* plan, gfc_profile* out, int reset);
 gfc_status gfc_solve_from_gradient_noalloc(int H, int W, int fields, const void* gx, const void* gy, void* out,
                                            void* stream);
 
+/* A solve call captured once as a CUDA graph and replayed with one launch.
+ * The graph is bound to the plan, the operation and the pointers given at
+ * capture; replaying it recomputes the same operation on whatever those
+ * buffers hold at replay time. op: 0 = solve from gradient (in0 = gx,
+ * in1 = gy, out0 = out), 1 = solve from Laplacian (in0 = lap, out0 = out),
+ * 2 = backward (in0 = grad_out, out0 = grad_gx, out1 = grad_gy). Capture runs
+ * one ordinary call first (to finish lazy set-up), then records a second one on
+ * an internal stream; both run synchronously inside gfc_graph_create. The
+ * plan must outlive the graph. */
+typedef struct gfc_graph gfc_graph;
+gfc_status gfc_graph_create(gfc_plan* plan, int op, const void* in0, const void* in1, void* out0, void* out1,
+                            gfc_graph** graph);
+/* Launch the captured graph on `stream` (cudaStream_t). Asynchronous. */
+gfc_status gfc_graph_launch(gfc_graph* graph, void* stream);
+/* Free the graph. NULL is accepted. */
+gfc_status gfc_graph_destroy(gfc_graph* graph);
+
 /* Wait for the plan's stream and report any device-side error since the last
  * sync (GFC_ERR_TIMEOUT for a bounded wait that ran out, GFC_ERR_CUDA otherwise). */
 gfc_status gfc_plan_sync(gfc_plan* plan);

@@ -933,3 +933,83 @@ extern "C" gfc_status gfc_solve_from_gradient_noalloc(int H, int W, int fields, 
   }
   return GFC_OK;
 }
+
+// ---------------------------------------------------------------------------
+// captured solve graphs
+// ---------------------------------------------------------------------------
+struct gfc_graph {
+  cudaGraphExec_t exec;
+  cudaGraph_t graph;
+};
+
+static gfc_status run_op(gfc_plan* plan, int op, const void* in0, const void* in1, void* out0, void* out1) {
+  switch (op) {
+    case 0: return gfc_solve_from_gradient(plan, in0, in1, out0);
+    case 1: return gfc_solve_from_laplacian(plan, in0, out0);
+    case 2: return gfc_backward(plan, in0, out0, out1);
+  }
+  return fail(GFC_ERR_INVALID_ARG, "gfc_graph_create: unknown op %d", op);
+}
+
+extern "C" gfc_status gfc_graph_create(gfc_plan* plan, int op, const void* in0, const void* in1, void* out0,
+                                       void* out1, gfc_graph** graph) {
+  clear_error();
+  if (!plan || !graph) return fail(GFC_ERR_INVALID_ARG, "gfc_graph_create: null argument");
+  *graph = nullptr;
+  if (plan->profiling) return fail(GFC_ERR_UNSUPPORTED, "gfc_graph_create: turn profiling off before capturing");
+  cudaStream_t saved = plan->stream, cs = nullptr;
+  gfc_status st = run_op(plan, op, in0, in1, out0, out1);  // lazy set-up outside the capture
+  if (st != GFC_OK) return st;
+  GFC_CUDA_TRY(cudaStreamSynchronize(saved));
+  GFC_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  plan->stream = cs;
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    st = run_op(plan, op, in0, in1, out0, out1);
+    cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+    if (st == GFC_OK && e2 != cudaSuccess) e = e2;
+  }
+  plan->stream = saved;
+  cudaStreamDestroy(cs);
+  if (st != GFC_OK) {
+    if (g) cudaGraphDestroy(g);
+    return st;
+  }
+  if (e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return cuda_fail(e, "gfc_graph_create: capture");
+  }
+  cudaGraphExec_t x = nullptr;
+  e = cudaGraphInstantiate(&x, g, 0);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return cuda_fail(e, "gfc_graph_create: instantiate");
+  }
+  gfc_graph* out = (gfc_graph*)calloc(1, sizeof(gfc_graph));
+  if (!out) {
+    cudaGraphExecDestroy(x);
+    cudaGraphDestroy(g);
+    return fail(GFC_ERR_ALLOC, "gfc_graph_create: host allocation failed");
+  }
+  out->exec = x;
+  out->graph = g;
+  *graph = out;
+  return GFC_OK;
+}
+
+extern "C" gfc_status gfc_graph_launch(gfc_graph* graph, void* stream) {
+  clear_error();
+  if (!graph) return fail(GFC_ERR_INVALID_ARG, "gfc_graph_launch: null graph");
+  GFC_CUDA_TRY(cudaGraphLaunch(graph->exec, (cudaStream_t)stream));
+  return GFC_OK;
+}
+
+extern "C" gfc_status gfc_graph_destroy(gfc_graph* graph) {
+  clear_error();
+  if (!graph) return GFC_OK;
+  cudaGraphExecDestroy(graph->exec);
+  cudaGraphDestroy(graph->graph);
+  free(graph);
+  return GFC_OK;
+}

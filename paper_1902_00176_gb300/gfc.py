@@ -79,6 +79,10 @@ _SIGNATURES = {
     "gfc_plan_get_profile": [ctypes.c_void_p, ctypes.POINTER(Profile), ctypes.c_int],
     "gfc_solve_from_gradient_noalloc": [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                         ctypes.c_void_p, ctypes.c_void_p],
+    "gfc_graph_create": [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                         ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)],
+    "gfc_graph_launch": [ctypes.c_void_p, ctypes.c_void_p],
+    "gfc_graph_destroy": [ctypes.c_void_p],
     "gfc_plan_sync": [ctypes.c_void_p],
     "gfc_destroy": [ctypes.c_void_p],
     "gfc_last_error": [],
@@ -394,3 +398,35 @@ class RaggedPlan:
         self._bind_stream()
         _check(lib().gfc_backward(self._h, grad_out.data_ptr(), grad_gx.data_ptr(), grad_gy.data_ptr()))
         return grad_gx, grad_gy
+
+
+class Graph:
+    """A captured solve call (see gfc_graph_create): ``launch()`` replays it with one launch
+    on the current stream, reading and writing the buffers given at capture."""
+
+    OPS = {"gradient": 0, "laplacian": 1, "backward": 2}
+
+    def __init__(self, plan, op, in0, in1=None, out0=None, out1=None):
+        self.plan = plan
+        self._keep = (in0, in1, out0, out1)
+        ptr = lambda t: None if t is None else t.data_ptr()
+        plan._bind_stream()
+        h = ctypes.c_void_p()
+        _check(lib().gfc_graph_create(plan.handle if hasattr(plan, "handle") else plan._h, self.OPS[op], ptr(in0),
+                                      ptr(in1), ptr(out0), ptr(out1), ctypes.byref(h)))
+        self._h = h
+        self.device = plan.device
+
+    def launch(self):
+        _check(lib().gfc_graph_launch(self._h, ctypes.c_void_p(_stream_ptr(self.device))))
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().gfc_graph_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -104,3 +104,34 @@ def test_ragged_workload_shapes_sampled():
         got = out[o:o + H * W].view(H, W).double().cpu().numpy()
         assert _rel(got, ref) <= REL_F32, items[i]
     rp.close()
+
+
+def test_captured_graphs_replay_the_same_solve():
+    items = _items_small()
+    gxs, gys = _inputs(items, seed=5)
+    rp = gfc.RaggedPlan(items, device=DEV)
+    gx, gy = rp.pack(gxs), rp.pack(gys)
+    ref = rp.solve_from_gradient(gx, gy).clone()
+    out = rp.empty()
+    g = gfc.Graph(rp, "gradient", gx, gy, out)
+    g.launch()
+    torch.cuda.synchronize()
+    assert torch.equal(out, ref)
+    gx2 = gx * 2.0
+    gx.copy_(gx2)  # new contents, same buffers
+    g.launch()
+    torch.cuda.synchronize()
+    assert torch.equal(out, rp.solve_from_gradient(gx, gy))
+    g.close()
+    # uniform plan, fast path, backward op
+    p = gfc.Plan(801, 1200, 1, 2, device=DEV)
+    go = torch.randn((2, 1, 801, 1200), device=DEV)
+    bx, by = torch.empty_like(go), torch.empty_like(go)
+    g2 = gfc.Graph(p, "backward", go, None, bx, by)
+    g2.launch()
+    rx, ry = p.backward(go)
+    torch.cuda.synchronize()
+    assert torch.equal(bx, rx) and torch.equal(by, ry)
+    g2.close()
+    p.close()
+    rp.close()
