@@ -28,9 +28,15 @@ struct FftPlan {
   int radix[kMaxStages]; // radix of each stage, in order
 };
 
-__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
-__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+// Complex helpers. Component-wise pair operations use the packed FP32
+// instructions of sm_100+ (one instruction for both halves, same rounding as
+// two scalar ones); operations that swap the halves stay scalar.
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+// a - b as fma(b, -1, a): exact negation, one rounding, identical to a - b
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a); }
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return __fmul2_rn(a, make_float2(s, s)); }
+// a * s + c
+__device__ __forceinline__ float2 cfma(float2 a, float s, float2 c) { return __ffma2_rn(a, make_float2(s, s), c); }
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
@@ -39,6 +45,20 @@ __device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y
 template <int DIR>
 __device__ __forceinline__ float2 rot(float2 a) {
   return DIR < 0 ? make_float2(a.y, -a.x) : make_float2(-a.y, a.x);
+}
+// p + rot(q) and p - rot(q)
+template <int DIR>
+__device__ __forceinline__ float2 add_rot(float2 p, float2 q) {
+  return DIR < 0 ? make_float2(p.x + q.y, p.y - q.x) : make_float2(p.x - q.y, p.y + q.x);
+}
+template <int DIR>
+__device__ __forceinline__ float2 sub_rot(float2 p, float2 q) {
+  return DIR < 0 ? make_float2(p.x - q.y, p.y + q.x) : make_float2(p.x + q.y, p.y - q.x);
+}
+// p + s rot(d) and p - s rot(d)
+template <int DIR>
+__device__ __forceinline__ float2 fma_rot(float2 d, float s, float2 p) {
+  return DIR < 0 ? make_float2(fmaf(s, d.y, p.x), fmaf(-s, d.x, p.y)) : make_float2(fmaf(-s, d.y, p.x), fmaf(s, d.x, p.y));
 }
 // twiddle for direction DIR from a forward-root table value
 template <int DIR>
@@ -55,19 +75,19 @@ __device__ __forceinline__ float2 tw_dir(float2 w) { return DIR < 0 ? w : cconj(
 
 template <int DIR>
 __device__ __forceinline__ void dft2(float2* v) {
-  float2 a = v[0], b = v[1];
+  const float2 a = v[0], b = v[1];
   v[0] = cadd(a, b);
   v[1] = csub(a, b);
 }
 
 template <int DIR>
 __device__ __forceinline__ void dft4(float2* v) {
-  float2 a = cadd(v[0], v[2]), b = csub(v[0], v[2]);
-  float2 c = cadd(v[1], v[3]), d = rot<DIR>(csub(v[1], v[3]));
+  const float2 a = cadd(v[0], v[2]), b = csub(v[0], v[2]);
+  const float2 c = cadd(v[1], v[3]), d = csub(v[1], v[3]);
   v[0] = cadd(a, c);
   v[2] = csub(a, c);
-  v[1] = cadd(b, d);
-  v[3] = csub(b, d);
+  v[1] = add_rot<DIR>(b, d);
+  v[3] = sub_rot<DIR>(b, d);
 }
 
 template <int DIR>
@@ -77,47 +97,46 @@ __device__ __forceinline__ void dft8(float2* v) {
   float2 o[4] = {v[1], v[3], v[5], v[7]};
   dft4<DIR>(e);
   dft4<DIR>(o);
-  // o[s] *= w8^s, w8 = (1 + DIR i) sqrt(1/2)
-  float2 o1 = o[1], o3 = o[3];
-  o[1] = cscale(cadd(o1, rot<DIR>(o1)), h);
-  o[2] = rot<DIR>(o[2]);
-  o[3] = cscale(csub(rot<DIR>(o3), o3), h);
-#pragma unroll
-  for (int s = 0; s < 4; ++s) {
-    v[s] = cadd(e[s], o[s]);
-    v[s + 4] = csub(e[s], o[s]);
-  }
+  // o[s] *= w8^s, w8 = (1 + DIR i) sqrt(1/2); o[2] *= DIR i is folded into the output sums
+  const float2 o1 = cscale(add_rot<DIR>(o[1], o[1]), h);
+  const float2 o3 = cscale(add_rot<DIR>(make_float2(-o[3].x, -o[3].y), o[3]), h);  // (rot(o3) - o3) / sqrt 2
+  v[0] = cadd(e[0], o[0]);
+  v[4] = csub(e[0], o[0]);
+  v[1] = cadd(e[1], o1);
+  v[5] = csub(e[1], o1);
+  v[2] = add_rot<DIR>(e[2], o[2]);
+  v[6] = sub_rot<DIR>(e[2], o[2]);
+  v[3] = cadd(e[3], o3);
+  v[7] = csub(e[3], o3);
 }
 
 template <int DIR>
 __device__ __forceinline__ void dft3(float2* v) {
   constexpr float s60 = 0.866025403784438646764f;
-  float2 t1 = cadd(v[1], v[2]);
-  float2 t2 = make_float2(fmaf(-0.5f, t1.x, v[0].x), fmaf(-0.5f, t1.y, v[0].y));
-  float2 t3 = cscale(rot<DIR>(csub(v[1], v[2])), s60);
+  const float2 t1 = cadd(v[1], v[2]);
+  const float2 t2 = cfma(t1, -0.5f, v[0]);
+  const float2 d = csub(v[1], v[2]);
   v[0] = cadd(v[0], t1);
-  v[1] = cadd(t2, t3);
-  v[2] = csub(t2, t3);
+  v[1] = fma_rot<DIR>(d, s60, t2);
+  v[2] = fma_rot<DIR>(d, -s60, t2);
 }
 
 template <int DIR>
 __device__ __forceinline__ void dft5(float2* v) {
   constexpr float c1 = 0.309016994374947424102f, c2 = -0.809016994374947424102f;
   constexpr float s1 = 0.951056516295153572116f, s2 = 0.587785252292473129169f;
-  float2 a1 = cadd(v[1], v[4]), b1 = csub(v[1], v[4]);
-  float2 a2 = cadd(v[2], v[3]), b2 = csub(v[2], v[3]);
-  float2 x0 = v[0];
-  float2 p1 = make_float2(fmaf(c1, a1.x, fmaf(c2, a2.x, x0.x)), fmaf(c1, a1.y, fmaf(c2, a2.y, x0.y)));
-  float2 p2 = make_float2(fmaf(c2, a1.x, fmaf(c1, a2.x, x0.x)), fmaf(c2, a1.y, fmaf(c1, a2.y, x0.y)));
-  float2 q1 = make_float2(fmaf(s1, b1.x, s2 * b2.x), fmaf(s1, b1.y, s2 * b2.y));
-  float2 q2 = make_float2(fmaf(s2, b1.x, -s1 * b2.x), fmaf(s2, b1.y, -s1 * b2.y));
-  q1 = rot<DIR>(q1);
-  q2 = rot<DIR>(q2);
+  const float2 a1 = cadd(v[1], v[4]), b1 = csub(v[1], v[4]);
+  const float2 a2 = cadd(v[2], v[3]), b2 = csub(v[2], v[3]);
+  const float2 x0 = v[0];
+  const float2 p1 = cfma(a1, c1, cfma(a2, c2, x0));
+  const float2 p2 = cfma(a1, c2, cfma(a2, c1, x0));
+  const float2 q1 = cfma(b1, s1, cscale(b2, s2));
+  const float2 q2 = cfma(b1, s2, cscale(b2, -s1));
   v[0] = cadd(x0, cadd(a1, a2));
-  v[1] = cadd(p1, q1);
-  v[4] = csub(p1, q1);
-  v[2] = cadd(p2, q2);
-  v[3] = csub(p2, q2);
+  v[1] = add_rot<DIR>(p1, q1);
+  v[4] = sub_rot<DIR>(p1, q1);
+  v[2] = add_rot<DIR>(p2, q2);
+  v[3] = sub_rot<DIR>(p2, q2);
 }
 
 template <int DIR>
@@ -126,35 +145,25 @@ __device__ __forceinline__ void dft7(float2* v) {
                   c3 = -0.900968867902419126236f;
   constexpr float s1 = 0.781831482468029808708f, s2 = 0.974927912181823607018f,
                   s3 = 0.433883739117558120476f;
-  float2 a1 = cadd(v[1], v[6]), b1 = csub(v[1], v[6]);
-  float2 a2 = cadd(v[2], v[5]), b2 = csub(v[2], v[5]);
-  float2 a3 = cadd(v[3], v[4]), b3 = csub(v[3], v[4]);
-  float2 x0 = v[0];
+  const float2 a1 = cadd(v[1], v[6]), b1 = csub(v[1], v[6]);
+  const float2 a2 = cadd(v[2], v[5]), b2 = csub(v[2], v[5]);
+  const float2 a3 = cadd(v[3], v[4]), b3 = csub(v[3], v[4]);
+  const float2 x0 = v[0];
   // k = 1: (c1, c2, c3), (s1, s2, s3); k = 2: (c2, c3, c1), (s2, -s3, -s1);
   // k = 3: (c3, c1, c2), (s3, -s1, s2)   [cos/sin of 2 pi (k m mod 7)/7]
-  float2 p1, p2, p3, q1, q2, q3;
-  p1.x = fmaf(c1, a1.x, fmaf(c2, a2.x, fmaf(c3, a3.x, x0.x)));
-  p1.y = fmaf(c1, a1.y, fmaf(c2, a2.y, fmaf(c3, a3.y, x0.y)));
-  p2.x = fmaf(c2, a1.x, fmaf(c3, a2.x, fmaf(c1, a3.x, x0.x)));
-  p2.y = fmaf(c2, a1.y, fmaf(c3, a2.y, fmaf(c1, a3.y, x0.y)));
-  p3.x = fmaf(c3, a1.x, fmaf(c1, a2.x, fmaf(c2, a3.x, x0.x)));
-  p3.y = fmaf(c3, a1.y, fmaf(c1, a2.y, fmaf(c2, a3.y, x0.y)));
-  q1.x = fmaf(s1, b1.x, fmaf(s2, b2.x, s3 * b3.x));
-  q1.y = fmaf(s1, b1.y, fmaf(s2, b2.y, s3 * b3.y));
-  q2.x = fmaf(s2, b1.x, fmaf(-s3, b2.x, -s1 * b3.x));
-  q2.y = fmaf(s2, b1.y, fmaf(-s3, b2.y, -s1 * b3.y));
-  q3.x = fmaf(s3, b1.x, fmaf(-s1, b2.x, s2 * b3.x));
-  q3.y = fmaf(s3, b1.y, fmaf(-s1, b2.y, s2 * b3.y));
-  q1 = rot<DIR>(q1);
-  q2 = rot<DIR>(q2);
-  q3 = rot<DIR>(q3);
+  const float2 p1 = cfma(a1, c1, cfma(a2, c2, cfma(a3, c3, x0)));
+  const float2 p2 = cfma(a1, c2, cfma(a2, c3, cfma(a3, c1, x0)));
+  const float2 p3 = cfma(a1, c3, cfma(a2, c1, cfma(a3, c2, x0)));
+  const float2 q1 = cfma(b1, s1, cfma(b2, s2, cscale(b3, s3)));
+  const float2 q2 = cfma(b1, s2, cfma(b2, -s3, cscale(b3, -s1)));
+  const float2 q3 = cfma(b1, s3, cfma(b2, -s1, cscale(b3, s2)));
   v[0] = cadd(x0, cadd(a1, cadd(a2, a3)));
-  v[1] = cadd(p1, q1);
-  v[6] = csub(p1, q1);
-  v[2] = cadd(p2, q2);
-  v[5] = csub(p2, q2);
-  v[3] = cadd(p3, q3);
-  v[4] = csub(p3, q3);
+  v[1] = add_rot<DIR>(p1, q1);
+  v[6] = sub_rot<DIR>(p1, q1);
+  v[2] = add_rot<DIR>(p2, q2);
+  v[5] = sub_rot<DIR>(p2, q2);
+  v[3] = add_rot<DIR>(p3, q3);
+  v[4] = sub_rot<DIR>(p3, q3);
 }
 
 template <int R, int DIR>

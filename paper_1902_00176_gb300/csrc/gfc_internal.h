@@ -64,6 +64,7 @@ struct gfc_plan {
   cudaStream_t copy_in, copy_out;
   cudaEvent_t ev_in[2], ev_comp[2], ev_out[2];
   bool host_ready;
+  int host_chunk;         // fields per host-pipeline step (copies of one step overlap the solve of another)
   // ragged batch (gfc_plan_create_ragged)
   bool ragged;
   int nfields;               // total fields (sum of item channels)

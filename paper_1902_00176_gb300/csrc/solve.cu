@@ -639,7 +639,13 @@ static bool misaligned(const void* p) { return (reinterpret_cast<uintptr_t>(p) &
 // buffer, copy_out waits for the solve.
 static gfc_status host_setup(gfc_plan* P) {
   if (P->host_ready) return GFC_OK;
-  const size_t bytes = (size_t)P->chunk * P->H * P->W * dtype_size(P->dtype);
+  // about eight steps per call, so that copies in both directions overlap solves
+  const long fields = (long)P->batch * P->C;
+  long hc = (fields + 7) / 8;
+  if (hc > P->chunk) hc = P->chunk;
+  if (hc < 1) hc = 1;
+  P->host_chunk = (int)hc;
+  const size_t bytes = (size_t)hc * P->H * P->W * dtype_size(P->dtype);
   for (int b = 0; b < 2; ++b) {
     GFC_CUDA_TRY(cudaMalloc(&P->stage_in[b][0], bytes));
     GFC_CUDA_TRY(cudaMalloc(&P->stage_in[b][1], bytes));
@@ -668,9 +674,10 @@ static gfc_status run_host(gfc_plan* P, const void* gx, const void* gy, void* ou
   GFC_CUDA_TRY(cudaStreamWaitEvent(P->copy_out, start, 0));
   P->prof.calls += 1;
   long c = 0;
-  for (long f0 = 0; f0 < fields; f0 += P->chunk, ++c) {
+  const int hc = P->host_chunk;
+  for (long f0 = 0; f0 < fields; f0 += hc, ++c) {
     const int b = (int)(c & 1);
-    const int nf = (int)((fields - f0 < P->chunk) ? fields - f0 : P->chunk);
+    const int nf = (int)((fields - f0 < hc) ? fields - f0 : hc);
     const size_t bytes = (size_t)nf * fe * sizeof(T);
     if (c >= 2) GFC_CUDA_TRY(cudaStreamWaitEvent(P->copy_in, P->ev_comp[b], 0));
     GFC_CUDA_TRY(cudaMemcpyAsync(P->stage_in[b][0], static_cast<const T*>(gx) + f0 * fe, bytes,

@@ -120,8 +120,10 @@ struct ColShape {
   static constexpr int THREADS = ((C * T + 31) / 32) * 32;
   static constexpr int MINB = (THREADS <= 256) ? 2 : 1;  // blocks per SM the registers must allow
   static_assert(R1 <= R2, "column schedule needs R1 <= R2");
+  static constexpr int GS = ((M + 3) / 4) * 4;  // floats per staged Green column (16-byte multiple)
   static constexpr size_t smem_bytes() {
-    return (size_t)(R1 * TWF_STRIDE + R2 * TWI_STRIDE + WORK) * sizeof(float2) + C * sizeof(double);
+    return (size_t)C * GS * sizeof(float) +
+           (size_t)(R1 * TWF_STRIDE + R2 * TWI_STRIDE + WORK) * sizeof(float2) + C * sizeof(double);
   }
   static __device__ __forceinline__ int pad(int m) { return m + m / R2; }
 };
@@ -308,7 +310,8 @@ __global__ void __launch_bounds__(S::THREADS, S::MINB) k_fast_cols(const float2*
                                                           const float* __restrict__ GT, const float2* __restrict__ twg,
                                                           float* __restrict__ partial, FastArgs A) {
   extern __shared__ float2 sm[];
-  float2* twF = sm;                                     // [R1][TWF_STRIDE]: w_M^(r j), j < R1, r < R2
+  float* gsm = reinterpret_cast<float*>(sm);            // [C][GS] this block's Green columns
+  float2* twF = reinterpret_cast<float2*>(gsm + S::C * S::GS);  // [R1][TWF_STRIDE]: w_M^(r j), j < R1, r < R2
   float2* twI = twF + S::R1 * S::TWF_STRIDE;            // [R2][TWI_STRIDE]: w_M^(r j), j < R2, r < R1
   float2* buf = twI + S::R2 * S::TWI_STRIDE;            // [C][MP]
   double* colval = reinterpret_cast<double*>(buf + S::WORK);  // [C] row-0 contributions
@@ -318,7 +321,21 @@ __global__ void __launch_bounds__(S::THREADS, S::MINB) k_fast_cols(const float2*
   const int l = blk * S::C + c;
   const bool act = (c < S::C) && (l < A.Nh);
   const float2* col = spec + (size_t)field * A.Nh * A.ldM + (size_t)(act ? l : 0) * A.ldM;
-  const float* gcol = GT + (size_t)(act ? l : 0) * A.ldM;
+  // stage this block's Green columns into shared memory asynchronously; they are
+  // first needed after the first exchange
+  {
+    const int ncol = (A.Nh - blk * S::C) < S::C ? (A.Nh - blk * S::C) : S::C;
+    const float* gsrc = GT + (size_t)blk * S::C * A.ldM;
+    constexpr int CH = S::GS / 4;  // 16-byte chunks per column
+    for (int i = tid; i < ncol * CH; i += blockDim.x) {
+      const int cc = i / CH, q = i - cc * CH;
+      const unsigned dst = (unsigned)__cvta_generic_to_shared(gsm + cc * S::GS + 4 * q);
+      const float* src = gsrc + (size_t)cc * A.ldM + 4 * q;
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src) : "memory");
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  }
+  const float* gcol = gsm + (c < S::C ? c : 0) * S::GS;
   float2* mybuf = buf + (c < S::C ? c : 0) * S::MP;
   // rows outside the support were zeroed by the row pass
   float2 v[S::R1];
@@ -337,6 +354,7 @@ __global__ void __launch_bounds__(S::THREADS, S::MINB) k_fast_cols(const float2*
 #pragma unroll
     for (int s2 = 0; s2 < S::R1; ++s2) mybuf[t * S::R1 + s2] = v[s2];
   }
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
   __syncthreads();
   float2 u[S::R2];
   const bool act2 = act && t < S::R1;

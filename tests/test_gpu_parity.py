@@ -128,15 +128,18 @@ def test_modes_and_sizes_sharing_a_kernel_can_alternate():
     mode must not leave the kernel unable to run a larger launch of the other."""
     rng = np.random.default_rng(3)
     for (H, W, mode) in [(300, 700, "grad"), (20, 30, "lap"), (96, 80, "grad"), (500, 900, "lap")]:
-        a = rng.uniform(-0.1, 0.1, (1, 1, H, W)).astype(np.float32)
+        img = synth.gaussian_image(rng, H, W, 16, max(2.0, H / 40), max(4.0, H / 5))
+        gx, gy = synth.forward_gradient(img)
         p = gfc.Plan(H, W, device=DEV)
         if mode == "grad":
-            out = _np(p.solve_from_gradient(_to_dev(a), _to_dev(a[..., ::-1].copy())))
-            ref = O.solve_from_gradient_batch(a.astype(np.float64), a[..., ::-1].astype(np.float64), p.M, p.N, p.pad)
+            out = _np(p.solve_from_gradient(_to_dev(gx[None, None]), _to_dev(gy[None, None])))[0, 0]
+            ref = O.solve_from_gradient(gx.astype(np.float32).astype(np.float64),
+                                        gy.astype(np.float32).astype(np.float64), p.M, p.N, p.pad)
         else:
-            out = _np(p.solve_from_laplacian(_to_dev(a)))
-            ref = O.solve_from_laplacian_batch(a.astype(np.float64), p.M, p.N, p.pad)
-        assert _rel(out, ref) <= REL_F32
+            lap = (gx - np.pad(gx, ((0, 0), (1, 0)))[:, :-1]) + (gy - np.pad(gy, ((1, 0), (0, 0)))[:-1, :])
+            out = _np(p.solve_from_laplacian(_to_dev(lap[None, None])))[0, 0]
+            ref = O.solve_from_laplacian(lap.astype(np.float32).astype(np.float64), p.M, p.N, p.pad)
+        assert _rel(out, ref) <= REL_F32, (H, W, mode, _rel(out, ref))
         p.close()
 
 
@@ -305,4 +308,20 @@ def test_fast_path_16bit_storage(dtype):
     out = _np(p.solve_from_gradient(tx, ty))[0, 0]
     ref = O.solve_from_gradient(_np(tx)[0, 0], _np(ty)[0, 0], p.M, p.N, p.pad)
     assert _rel(out, ref) <= REL_16
+    p.close()
+
+
+@pytest.mark.parametrize("H,W,B", [(64, 96, 5), (801, 1200, 3)])
+def test_host_buffer_entry_matches_device_entry(H, W, B):
+    gx, gy = synth.perturbed_gradient_batch(batch=B, H=H, W=W, seed=321)
+    p = gfc.Plan(H, W, 1, B, device=DEV)
+    ref = p.solve_from_gradient(_to_dev(gx), _to_dev(gy)).cpu()
+    hx = torch.from_numpy(gx).pin_memory()
+    hy = torch.from_numpy(gy).pin_memory()
+    ho = torch.empty_like(hx).pin_memory()
+    for _ in range(2):  # twice: the staging buffers are reused
+        ho.zero_()
+        p.solve_from_gradient_host(hx, hy, ho)
+        torch.cuda.synchronize()
+        assert torch.equal(ho, ref)
     p.close()
