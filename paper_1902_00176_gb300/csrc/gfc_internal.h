@@ -84,7 +84,7 @@ struct gfc_plan {
 
 namespace gfc {
 
-constexpr int kMaxRowBlocks = 1024;
+constexpr int kMaxRowBlocks = 2048;
 
 // thread-local error text, set by fail()
 gfc_status fail(gfc_status s, const char* fmt, ...);
@@ -101,11 +101,11 @@ cudaError_t build_green(float* G, int M, int N, int Nh, cudaStream_t s);
 cudaError_t build_green_t(float* GT, int M, int N, int Nh, int ldM, cudaStream_t s);
 
 // register-resident passes (solve_fast.cu): spectrum laid out [l][r]
-bool fast_rows_supported(int N);
-bool fast_cols_supported(int M);
-size_t fast_zbuf_elems(int H, int W, int N);  // per field
-cudaError_t run_chunk_fast(gfc_plan* P, const Bufs& B, int mode, const void* in0, const void* in1, void* out,
-                           int nf, cudaStream_t st);
+bool fast_supported(int M, int N);
+size_t fast_zbuf_elems(int H, int M, int N);  // per field
+// mode 0 gradient, 1 Laplacian, 2 adjoint (out1 = grad_gy)
+cudaError_t run_chunk_fast(gfc_plan* P, const Bufs& B, int mode, const void* in0, const void* in1, void* out0,
+                           void* out1, int nf, cudaStream_t st);
 inline Bufs slot_bufs(const gfc_plan* P, int s) {
   Bufs b;
   b.spec = P->spec + (size_t)s * P->chunk * P->spec_field;

@@ -183,7 +183,7 @@ gfc_status gfc_plan_create_ex(gfc_plan** out, const gfc_plan_opts* o) {
   if (!p) return fail(GFC_ERR_ALLOC, "gfc_plan_create: host allocation failed");
   p->H = o->H; p->W = o->W; p->C = o->C; p->batch = o->batch; p->pad = pad; p->dtype = o->dtype;
   p->M = M; p->N = N; p->Nh = N / 2 + 1; p->ldS = (p->Nh + 3) & ~3; p->ldM = (M + 3) & ~3;
-  p->fast = fast_rows_supported(N) && fast_cols_supported(M) && pad == 4 && getenv("GFC_FORCE_GENERIC") == nullptr;
+  p->fast = fast_supported(M, N) && pad == 4 && getenv("GFC_FORCE_GENERIC") == nullptr;
   p->stream = (cudaStream_t)o->stream;
   if (!make_fft_plan(N, &p->rowplan) || !make_fft_plan(M, &p->colplan)) {
     free(p);
@@ -196,7 +196,7 @@ gfc_status gfc_plan_create_ex(gfc_plan** out, const gfc_plan_opts* o) {
   const long fields = (long)o->batch * o->C;
   const size_t per_row_major = (size_t)M * p->ldS, per_col_major = (size_t)p->Nh * p->ldM;
   p->spec_field = per_row_major > per_col_major ? per_row_major : per_col_major;
-  p->zbuf_field = p->fast ? fast_zbuf_elems(o->H, o->W, N) : 0;
+  p->zbuf_field = p->fast ? fast_zbuf_elems(o->H, M, N) : 0;
   const size_t per_field = p->spec_field * sizeof(float2);
   const size_t ws = per_field + p->zbuf_field * sizeof(float2);
   long chunk = o->chunk;

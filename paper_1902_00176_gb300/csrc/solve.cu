@@ -462,7 +462,7 @@ static cudaError_t launch_b_any(gfc_plan* P, const Bufs& bf, PassArgs B, int nf,
 template <typename T, int MODE>
 static cudaError_t run_chunk(gfc_plan* P, const Bufs& bf, const T* in0, const T* in1, T* out0, T* out1, int nf,
                              cudaStream_t st) {
-  if (P->fast && MODE != kAdj) return run_chunk_fast(P, bf, MODE, in0, in1, out0, nf, st);
+  if (P->fast) return run_chunk_fast(P, bf, MODE, in0, in1, out0, out1, nf, st);
   // pass A
   PassArgs A = base_args(P);
   A.nrows = (MODE == kGrad) ? P->H + 1 : P->H;

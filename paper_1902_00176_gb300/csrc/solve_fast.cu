@@ -1,608 +1,50 @@
-// solve_fast.cu -- register-resident GFC passes for transform lengths with a
-// two-stage schedule (Eq. 23, Algorithm B; the same three passes as solve.cu).
-//
-// Hand-offs between the passes:
-//   pass L  writes the packed rows z[pair][j] = L[2 pair][j] + i L[2 pair+1][j]
-//   pass A  reads z, writes the row spectrum column-major, spec[l][r] (l < N/2+1
-//           Hermitian columns), one 2F-row column segment at a time: the
-//           transpose is folded into the two-for-one split it does through
-//           shared memory anyway;
-//   pass B  loads whole columns of spec straight into registers and writes its
-//           result row-major, Y[i][l] (image rows i < H), through a padded
-//           shared-memory transpose, into the buffer that held z;
-//   pass C  loads rows of Y straight into registers.
-//
-// Row transforms (length N = R1 R2, T = R2 threads per transform, F transforms
-// per block): stage 1 is one radix-R1 DFT per thread on x[t + R2 r]; one
-// shared-memory exchange; stage 2 is R1/R2 radix-R2 DFTs per thread with the
-// twiddles w_N^(r j). Column transforms (M = R1 R2, R1 <= R2, T = R2 threads
-// per column): forward stage 1 radix-R1, exchange, forward stage 2 radix-R2;
-// each thread then holds the bins t + R1 s, multiplies them by the Green
-// spectrum and runs the inverse's first stage (radix-R2, no twiddles) on the
-// same registers; one more exchange and the inverse's radix-R1 stage.
-#include <cuda_bf16.h>
-#include <cuda_fp16.h>
-#include <cuda_runtime.h>
-
-#include <mutex>
-
-#include "fft_reg.cuh"
+// solve_fast.cu -- registry of the padded sizes with register-resident passes
+// (kernels in fast_kernels.cuh, one translation unit per size pair).
 #include "gfc_internal.h"
 
 namespace gfc {
 
-// The register-resident schedules assume Algorithm A's pad of 4.
-constexpr int kP = 4;
+#define GFC_FAST_SHAPE(M, N)                                                                                  \
+  cudaError_t fast_run_##M##x##N(gfc_plan*, const Bufs&, int, const void*, const void*, void*, void*, int, \
+                                 cudaStream_t);                                                           \
+  size_t fast_zbuf_##M##x##N(int H);
+GFC_FAST_SHAPE(810, 1250)
+GFC_FAST_SHAPE(1050, 1568)
+GFC_FAST_SHAPE(270, 270)
+GFC_FAST_SHAPE(72, 108)
+#undef GFC_FAST_SHAPE
 
-constexpr bool cx_smooth7(int n) {
-  if (n < 1) return false;
-  for (int f : {2, 3, 5, 7})
-    while (n % f == 0) n /= f;
-  return n == 1;
-}
-// smallest image width that pads to N under the SMOOTH policy (pad kP)
-constexpr int cx_min_width(int N) {
-  int prev = N - 2;
-  while (prev > 0 && !cx_smooth7(prev)) prev -= 2;
-  return prev - 2 * kP + 1;
-}
-
-struct FastArgs {
-  int H, W, p, M, N, Nh, ldM;
-  int nrows, ncols;  // support of L (from torus row/col p): H+1, W+1 (gradient) or H, W
-  int npairs, ldz;   // packed row pairs of L, and the stride of a packed row (>= N, zero padded)
-  int zpairs;        // packed rows per field (npairs rounded up to whole groups, extra rows zero)
-  int ngroups;       // row-pair groups per field (pass A) / output row-pair groups (pass C)
-  int nparts;        // pass B column blocks per field (u[0,0] partial sums)
-  int nf;            // fields in this chunk
-  int ldY;           // row stride of the row-major spectrum Y (complex elements)
+namespace {
+struct FastEntry {
+  int M, N;
+  cudaError_t (*run)(gfc_plan*, const Bufs&, int, const void*, const void*, void*, void*, int, cudaStream_t);
+  size_t (*zbuf)(int H);
 };
-
-__device__ __forceinline__ float f_to_f(float x) { return x; }
-__device__ __forceinline__ float f_to_f(__half x) { return __half2float(x); }
-__device__ __forceinline__ float f_to_f(__nv_bfloat16 x) { return __bfloat162float(x); }
-template <typename T> __device__ __forceinline__ T f_from_f(float x);
-template <> __device__ __forceinline__ float f_from_f<float>(float x) { return x; }
-template <> __device__ __forceinline__ __half f_from_f<__half>(float x) { return __float2half_rn(x); }
-template <> __device__ __forceinline__ __nv_bfloat16 f_from_f<__nv_bfloat16>(float x) { return __float2bfloat16_rn(x); }
-
-template <typename T>
-__device__ __forceinline__ float ldz(const T* __restrict__ g, int i, int j, int H, int W) {
-  return (i >= 0 && i < H && j >= 0 && j < W) ? f_to_f(g[(size_t)i * W + j]) : 0.0f;
-}
-
-template <typename T>
-__device__ __forceinline__ float4 ld4(const T* __restrict__ g, int i, int j, int W);
-template <>
-__device__ __forceinline__ float4 ld4<float>(const float* __restrict__ g, int i, int j, int W) {
-  return __ldg(reinterpret_cast<const float4*>(g + (size_t)i * W + j));
-}
-template <>
-__device__ __forceinline__ float4 ld4<__half>(const __half* __restrict__ g, int i, int j, int W) {
-  const uint2 u = __ldg(reinterpret_cast<const uint2*>(g + (size_t)i * W + j));
-  const float2 lo = __half22float2(*reinterpret_cast<const __half2*>(&u.x));
-  const float2 hi = __half22float2(*reinterpret_cast<const __half2*>(&u.y));
-  return make_float4(lo.x, lo.y, hi.x, hi.y);
-}
-template <>
-__device__ __forceinline__ float4 ld4<__nv_bfloat16>(const __nv_bfloat16* __restrict__ g, int i, int j, int W) {
-  const uint2 u = __ldg(reinterpret_cast<const uint2*>(g + (size_t)i * W + j));
-  const float2 lo = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.x));
-  const float2 hi = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.y));
-  return make_float4(lo.x, lo.y, hi.x, hi.y);
-}
-
-template <int N_, int R1_, int R2_, int F_>
-struct RowShape {
-  static constexpr int N = N_, R1 = R1_, R2 = R2_, F = F_;
-  static constexpr int T = R2;             // threads per transform
-  static constexpr int J2 = R1 / R2;       // stage-2 butterflies per thread
-  static constexpr int NP = N + N / R1;    // padded transform buffer
-  static constexpr int THREADS = ((F * T + 31) / 32) * 32;
-  static_assert(R1 % R2 == 0, "row schedule needs R2 | R1");
-  static constexpr int NO = N + 1;        // stage-2 output buffer stride (natural order)
-  static constexpr int WMIN = cx_min_width(N);
-  static constexpr size_t smem_bytes() { return (size_t)(R1 * R2 + F * NP) * sizeof(float2); }
-  static constexpr size_t smem_bytes_fwd() { return (size_t)(R1 * R2 + F * NP + F * NO) * sizeof(float2); }
-  // padded index: one spare slot every R1 elements (conflict-free stage-1 writes)
-  static __device__ __forceinline__ int pad(int m) { return m + m / R1; }
+const FastEntry kFast[] = {
+    {810, 1250, fast_run_810x1250, fast_zbuf_810x1250},
+    {1050, 1568, fast_run_1050x1568, fast_zbuf_1050x1568},
+    {270, 270, fast_run_270x270, fast_zbuf_270x270},
+    {72, 108, fast_run_72x108, fast_zbuf_72x108},
 };
+const FastEntry* find(int M, int N) {
+  for (const FastEntry& e : kFast)
+    if (e.M == M && e.N == N) return &e;
+  return nullptr;
+}
+}  // namespace
 
-template <int M_, int R1_, int R2_, int C_>
-struct ColShape {
-  static constexpr int M = M_, R1 = R1_, R2 = R2_, C = C_;
-  static constexpr int T = R2;             // threads per column
-  static constexpr int MP = M + M / R2;    // padded column buffer
-  static constexpr int OS = C + 1;         // row stride of the output transpose tile [M][OS]
-  static constexpr int WORK = (C * MP > M * OS) ? C * MP : M * OS;
-  static constexpr int TWF_STRIDE = (R2 % 2 == 0) ? R2 + 1 : R2;
-  static constexpr int TWI_STRIDE = (R1 % 2 == 0) ? R1 + 1 : R1;
-  static constexpr int THREADS = ((C * T + 31) / 32) * 32;
-  static constexpr int MINB = (THREADS <= 256) ? 2 : 1;  // blocks per SM the registers must allow
-  static_assert(R1 <= R2, "column schedule needs R1 <= R2");
-  static constexpr int GS = ((M + 3) / 4) * 4;  // floats per staged Green column (16-byte multiple)
-  static constexpr size_t smem_bytes() {
-    return (size_t)C * GS * sizeof(float) +
-           (size_t)(R1 * TWF_STRIDE + R2 * TWI_STRIDE + WORK) * sizeof(float2) + C * sizeof(double);
-  }
-  static __device__ __forceinline__ int pad(int m) { return m + m / R2; }
-};
+bool fast_supported(int M, int N) { return find(M, N) != nullptr; }
 
-// ---------------------------------------------------------------------------
-// pass L: divergence (Eq. 3) or copy of the given Laplacian, packed two rows per
-// complex value: z[pair][j] = L[2 pair][j] + i L[2 pair + 1][j], j < ncols
-// (image columns; the pad is implicit). Streams gx, gy once.
-// ---------------------------------------------------------------------------
-template <typename T, int MODE>
-__global__ void __launch_bounds__(256) k_fast_div(const T* __restrict__ in0, const T* __restrict__ in1,
-                                                  float2* __restrict__ z, FastArgs A) {
-  // grid: x = groups of 4 padded columns, y = packed rows (zpairs), z = fields.
-  // Packed row `pair`, padded column c holds L[2 pair][c - p] + i L[2 pair + 1][c - p],
-  // zero outside the support, so the row pass can load it without range checks.
-  const int q = blockIdx.x * blockDim.x + threadIdx.x;
-  const int pair = blockIdx.y, field = blockIdx.z;
-  if (q >= A.ldz / 4) return;
-  const int c0 = 4 * q, j0 = c0 - kP;
-  float la[4] = {0.0f, 0.0f, 0.0f, 0.0f}, lb[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-  if (pair < A.npairs && j0 + 3 >= 0 && j0 < A.ncols) {
-    const bool vec4 = (A.W % 4) == 0 && j0 >= 0;
-    const size_t fe = (size_t)A.H * A.W;
-    const T* a = in0 + field * fe;
-    const T* b = (MODE == 0) ? in1 + field * fe : nullptr;
-    const int ia = 2 * pair, ib = ia + 1;
-    if (MODE == 0) {
-      float xa[5], xb[5], ya[4], yb[4], ym[4];  // gx rows ia, ib at j0-1..j0+3; gy rows ia, ib, ia-1
-      const bool ina = ia < A.H, inb = ib < A.H, inm = ia >= 1 && ia - 1 < A.H;
-      if (vec4 && j0 + 3 < A.W) {
-        const float4 z4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-        const float4 ga = ina ? ld4(a, ia, j0, A.W) : z4, gb = inb ? ld4(a, ib, j0, A.W) : z4;
-        const float4 ha = ina ? ld4(b, ia, j0, A.W) : z4, hb = inb ? ld4(b, ib, j0, A.W) : z4;
-        const float4 hm = inm ? ld4(b, ia - 1, j0, A.W) : z4;
-        xa[1] = ga.x; xa[2] = ga.y; xa[3] = ga.z; xa[4] = ga.w;
-        xb[1] = gb.x; xb[2] = gb.y; xb[3] = gb.z; xb[4] = gb.w;
-        ya[0] = ha.x; ya[1] = ha.y; ya[2] = ha.z; ya[3] = ha.w;
-        yb[0] = hb.x; yb[1] = hb.y; yb[2] = hb.z; yb[3] = hb.w;
-        ym[0] = hm.x; ym[1] = hm.y; ym[2] = hm.z; ym[3] = hm.w;
-      } else {
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          xa[e + 1] = ldz(a, ia, j0 + e, A.H, A.W);
-          xb[e + 1] = ldz(a, ib, j0 + e, A.H, A.W);
-          ya[e] = ldz(b, ia, j0 + e, A.H, A.W);
-          yb[e] = ldz(b, ib, j0 + e, A.H, A.W);
-          ym[e] = ldz(b, ia - 1, j0 + e, A.H, A.W);
-        }
-      }
-      xa[0] = ldz(a, ia, j0 - 1, A.H, A.W);
-      xb[0] = ldz(a, ib, j0 - 1, A.H, A.W);
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        la[e] = (xa[e + 1] - xa[e]) + (ya[e] - ym[e]);
-        lb[e] = (xb[e + 1] - xb[e]) + (yb[e] - ya[e]);
-      }
-    } else {
-      if (vec4 && j0 + 3 < A.W) {
-        const float4 z4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-        const float4 ga = ia < A.H ? ld4(a, ia, j0, A.W) : z4, gb = ib < A.H ? ld4(a, ib, j0, A.W) : z4;
-        la[0] = ga.x; la[1] = ga.y; la[2] = ga.z; la[3] = ga.w;
-        lb[0] = gb.x; lb[1] = gb.y; lb[2] = gb.z; lb[3] = gb.w;
-      } else {
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          la[e] = ldz(a, ia, j0 + e, A.H, A.W);
-          lb[e] = ldz(a, ib, j0 + e, A.H, A.W);
-        }
-      }
-    }
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      const bool inj = j0 + e >= 0 && j0 + e < A.ncols;
-      la[e] = (inj && ia < A.nrows) ? la[e] : 0.0f;
-      lb[e] = (inj && ib < A.nrows) ? lb[e] : 0.0f;
-    }
-  }
-  float4* dst = reinterpret_cast<float4*>(z + ((size_t)field * A.zpairs + pair) * A.ldz + c0);
-  dst[0] = make_float4(la[0], lb[0], la[1], lb[1]);
-  dst[1] = make_float4(la[2], lb[2], la[3], lb[3]);
+size_t fast_zbuf_elems(int H, int M, int N) {
+  const FastEntry* e = find(M, N);
+  return e ? e->zbuf(H) : 0;
 }
 
-// ---------------------------------------------------------------------------
-// pass A: forward row transforms of the packed rows + two-for-one split +
-// transposed store. Persistent over (field, group of F row pairs).
-// ---------------------------------------------------------------------------
-template <class S>
-__global__ void __launch_bounds__(S::THREADS) k_fast_rows_fwd(const float2* __restrict__ z, float2* __restrict__ spec,
-                                                              const float2* __restrict__ twg, FastArgs A) {
-  extern __shared__ float2 sm[];
-  float2* tw2 = sm;                   // [R1][R2]: w_N^(r j)
-  float2* buf = sm + S::R1 * S::R2;   // [F][NP] exchange, index m -> m + m / R1
-  float2* buf2 = buf + S::F * S::NP;  // [F][NO] stage-2 output, natural order
-  const int tid = threadIdx.x;
-  const int f = tid / S::T, t = tid - f * S::T;
-  const bool act = f < S::F;
-  for (int i = tid; i < S::R1 * S::R2; i += blockDim.x) {
-    const int j = i / S::R2, r = i - j * S::R2;
-    tw2[i] = twg[r * j];
-  }
-  float2* mybuf = buf + (act ? f : 0) * S::NP;
-  float2* mybuf2 = buf2 + (act ? f : 0) * S::NO;
-  // unpack mapping: thread (uf, uk0) takes the bins k = uk0 + T s of transform uf
-  const int uf = tid % S::F, uk0 = tid / S::F;
-  const bool uact = tid < S::F * S::T;
-  const int items = A.nf * A.ngroups;
-  // the packed-row inputs of the next item are loaded while this one is transformed
-  auto load_item = [&](int w, float2 (&dst)[S::R1]) {
-    // packed rows are zero padded to the full transform length: no range checks
-    const int field = w / A.ngroups, g = w - field * A.ngroups;
-    const bool live = act && w < items;
-    const float2* zrow = z + ((size_t)(live ? field : 0) * A.zpairs + (live ? g * S::F + f : 0)) * A.ldz + t;
-#pragma unroll
-    for (int r = 0; r < S::R1; ++r) dst[r] = zrow[S::R2 * r];
-  };
-  float2 nxt[S::R1];
-  load_item(blockIdx.x, nxt);
-#pragma unroll 1
-  for (int w = blockIdx.x; w < items; w += gridDim.x) {
-    const int field = w / A.ngroups, g = w - field * A.ngroups;
-    float2 v[S::R1];
-#pragma unroll
-    for (int r = 0; r < S::R1; ++r) v[r] = nxt[r];
-    load_item(w + gridDim.x, nxt);
-    if (act) {
-      dft_reg<S::R1, -1>(v);
-      // Stockham stage 1 writes t R1 + s; its padded index is t (R1 + 1) + s
-#pragma unroll
-      for (int s2 = 0; s2 < S::R1; ++s2) mybuf[t * (S::R1 + 1) + s2] = v[s2];
-    }
-    __syncthreads();  // stage-1 results visible; previous unpack done with buf2
-    if (act) {
-#pragma unroll
-      for (int jj = 0; jj < S::J2; ++jj) {
-        const int j = t + S::R2 * jj;  // j < R1, so the padded index of j + R1 r is j + (R1 + 1) r
-        float2 u[S::R2];
-        u[0] = mybuf[j];
-#pragma unroll
-        for (int r = 1; r < S::R2; ++r) u[r] = cmul(mybuf[j + (S::R1 + 1) * r], tw2[j * S::R2 + r]);
-        dft_reg<S::R2, -1>(u);
-#pragma unroll
-        for (int s2 = 0; s2 < S::R2; ++s2) mybuf2[j + S::R1 * s2] = u[s2];
-      }
-    }
-    __syncthreads();  // stage-2 results visible; buf free for the next item
-    if (g == 0) {
-      // rows of every column outside the support [p, p + nrows) are zero, so the
-      // column pass loads whole columns without range checks
-      float2* Sz = spec + (size_t)field * A.Nh * A.ldM;
-      const int nz = A.M - A.nrows;
-      for (int idx = tid; idx < A.Nh * nz; idx += blockDim.x) {
-        const int k = idx / nz, q = idx - k * nz;
-        Sz[(size_t)k * A.ldM + (q < kP ? q : q + A.nrows)] = make_float2(0.0f, 0.0f);
-      }
-    }
-    // X_a[k] = (Z[k] + conj Z[N-k]) / 2, X_b[k] = -i (Z[k] - conj Z[N-k]) / 2, stored at spec[k][p + row]
-    const int ra = g * 2 * S::F + 2 * uf;
-    if (uact && ra < A.nrows) {
-      float2* Sp = spec + (size_t)field * A.Nh * A.ldM + A.p + ra;
-      const float2* zb = buf2 + uf * S::NO;
-      const bool two = ra + 1 < A.nrows, vec = ((A.p + ra) & 1) == 0;
-      for (int k = uk0; k < A.Nh; k += S::T) {
-        const float2 zk = zb[k], zm = zb[k == 0 ? 0 : S::N - k];
-        const float2 xa = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
-        const float2 xb = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
-        float2* dst = Sp + (size_t)k * A.ldM;
-        if (two && vec) {
-          *reinterpret_cast<float4*>(dst) = make_float4(xa.x, xa.y, xb.x, xb.y);
-        } else {
-          dst[0] = xa;
-          if (two) dst[1] = xb;
-        }
-      }
-    }
-  }
-}
-
-// ---------------------------------------------------------------------------
-// pass B: column transform, Green multiply, inverse column transform; one
-// block per (field, block of C columns).
-// ---------------------------------------------------------------------------
-template <class S>
-__global__ void __launch_bounds__(S::THREADS, S::MINB) k_fast_cols(const float2* __restrict__ spec, float2* __restrict__ Y,
-                                                          const float* __restrict__ GT, const float2* __restrict__ twg,
-                                                          float* __restrict__ partial, FastArgs A) {
-  extern __shared__ float2 sm[];
-  float* gsm = reinterpret_cast<float*>(sm);            // [C][GS] this block's Green columns
-  float2* twF = reinterpret_cast<float2*>(gsm + S::C * S::GS);  // [R1][TWF_STRIDE]: w_M^(r j), j < R1, r < R2
-  float2* twI = twF + S::R1 * S::TWF_STRIDE;            // [R2][TWI_STRIDE]: w_M^(r j), j < R2, r < R1
-  float2* buf = twI + S::R2 * S::TWI_STRIDE;            // [C][MP]
-  double* colval = reinterpret_cast<double*>(buf + S::WORK);  // [C] row-0 contributions
-  const int tid = threadIdx.x;
-  const int c = tid / S::T, t = tid - c * S::T;
-  const int field = blockIdx.y, blk = blockIdx.x;
-  const int l = blk * S::C + c;
-  const bool act = (c < S::C) && (l < A.Nh);
-  const float2* col = spec + (size_t)field * A.Nh * A.ldM + (size_t)(act ? l : 0) * A.ldM;
-  // stage this block's Green columns into shared memory asynchronously; they are
-  // first needed after the first exchange
-  {
-    const int ncol = (A.Nh - blk * S::C) < S::C ? (A.Nh - blk * S::C) : S::C;
-    const float* gsrc = GT + (size_t)blk * S::C * A.ldM;
-    constexpr int CH = S::GS / 4;  // 16-byte chunks per column
-    for (int i = tid; i < ncol * CH; i += blockDim.x) {
-      const int cc = i / CH, q = i - cc * CH;
-      const unsigned dst = (unsigned)__cvta_generic_to_shared(gsm + cc * S::GS + 4 * q);
-      const float* src = gsrc + (size_t)cc * A.ldM + 4 * q;
-      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src) : "memory");
-    }
-    asm volatile("cp.async.commit_group;\n" ::: "memory");
-  }
-  const float* gcol = gsm + (c < S::C ? c : 0) * S::GS;
-  float2* mybuf = buf + (c < S::C ? c : 0) * S::MP;
-  // rows outside the support were zeroed by the row pass
-  float2 v[S::R1];
-#pragma unroll
-  for (int r = 0; r < S::R1; ++r) v[r] = col[t + S::R2 * r];
-  for (int i = tid; i < S::R1 * S::R2; i += blockDim.x) {
-    const int j = i / S::R2, r = i - j * S::R2;
-    twF[j * S::TWF_STRIDE + r] = twg[r * j];
-  }
-  for (int i = tid; i < S::R2 * S::R1; i += blockDim.x) {
-    const int j = i / S::R1, r = i - j * S::R1;
-    twI[j * S::TWI_STRIDE + r] = twg[r * j];
-  }
-  if (act) {
-    dft_reg<S::R1, -1>(v);
-#pragma unroll
-    for (int s2 = 0; s2 < S::R1; ++s2) mybuf[t * S::R1 + s2] = v[s2];
-  }
-  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-  __syncthreads();
-  float2 u[S::R2];
-  const bool act2 = act && t < S::R1;
-  if (act2) {
-    u[0] = mybuf[t];
-#pragma unroll
-    for (int r = 1; r < S::R2; ++r) u[r] = cmul(mybuf[t + S::R1 * r], twF[t * S::TWF_STRIDE + r]);
-    dft_reg<S::R2, -1>(u);
-    // bins k = t + R1 s: multiply by the real Green spectrum (Eq. 23)
-#pragma unroll
-    for (int s2 = 0; s2 < S::R2; ++s2) u[s2] = cscale(u[s2], gcol[t + S::R1 * s2]);
-    // inverse stage 1 (span 1): butterfly t takes exactly the bins t + R1 r held here
-    dft_reg<S::R2, +1>(u);
-  }
-  __syncthreads();
-  if (act2) {
-#pragma unroll
-    for (int s2 = 0; s2 < S::R2; ++s2) mybuf[S::pad(t * S::R2 + s2)] = u[s2];
-  }
-  __syncthreads();
-  if (act) {
-    v[0] = mybuf[S::pad(t)];
-#pragma unroll
-    for (int r = 1; r < S::R1; ++r) v[r] = cmul(mybuf[S::pad(t + S::R2 * r)], cconj(twI[t * S::TWI_STRIDE + r]));
-    dft_reg<S::R1, +1>(v);
-    // u[0,0] = sum over the row-0 spectrum, weight 1 at l = 0 and N/2, 2 elsewhere
-    if (t == 0) colval[c] = (l == 0 || 2 * l == A.N) ? (double)v[0].x : 2.0 * (double)v[0].x;
-  }
-  __syncthreads();  // everyone is done reading buf: reuse it as the [M][OS] transpose tile
-  if (act) {
-#pragma unroll
-    for (int s2 = 0; s2 < S::R1; ++s2) buf[(t + S::R2 * s2) * S::OS + c] = v[s2];
-  }
-  __syncthreads();
-  {
-    // rows p .. p+H-1 of this block's columns, C consecutive complex per row segment
-    const int ncol = (A.Nh - blk * S::C) < S::C ? (A.Nh - blk * S::C) : S::C;
-    float2* Yf = Y + (size_t)field * A.H * A.ldY + blk * S::C;
-    for (int idx = tid; idx < A.H * S::C; idx += blockDim.x) {
-      const int i = idx / S::C, cc = idx - i * S::C;
-      if (cc < ncol) Yf[(size_t)i * A.ldY + cc] = buf[(A.p + i) * S::OS + cc];
-    }
-  }
-  if (tid == 0) {
-    // FP64 accumulation: an error in u[0,0] shifts every output pixel
-    double s2 = 0.0;
-    for (int cc = 0; cc < S::C; ++cc)
-      if (blk * S::C + cc < A.Nh) s2 += colval[cc];
-    reinterpret_cast<double*>(partial)[(size_t)field * (kMaxRowBlocks / 2) + blk] = s2;
-  }
-}
-
-// ---------------------------------------------------------------------------
-// pass C: Hermitian extension loaded straight from the column-major spectrum,
-// inverse row transforms, offset, crop and cast. Persistent over (field,
-// group of F output row pairs).
-// ---------------------------------------------------------------------------
-template <class S, typename T>
-__global__ void __launch_bounds__(S::THREADS) k_fast_rows_inv(const float2* __restrict__ Y,
-                                                              const float* __restrict__ partial, T* __restrict__ out,
-                                                              const float2* __restrict__ twg, FastArgs A) {
-  extern __shared__ float2 sm[];
-  float2* tw2 = sm;
-  float2* buf = sm + S::R1 * S::R2;
-  __shared__ float u00s[2];
-  const int tid = threadIdx.x;
-  const int f = tid / S::T, t = tid - f * S::T;
-  const bool act = f < S::F;
-  for (int i = tid; i < S::R1 * S::R2; i += blockDim.x) {
-    const int j = i / S::R2, r = i - j * S::R2;
-    tw2[i] = twg[r * j];
-  }
-  float2* mybuf = buf + (act ? f : 0) * S::NP;
-  const int half = S::N / 2;
-  const int items = A.nf * A.ngroups;
-  int parity = 0;
-#pragma unroll 1
-  for (int w = blockIdx.x; w < items; w += gridDim.x, parity ^= 1) {
-    const int field = w / A.ngroups, g = w - field * A.ngroups;
-    if (tid == 0) {
-      const double* pp = reinterpret_cast<const double*>(partial) + (size_t)field * (kMaxRowBlocks / 2);
-      double s2 = 0.0;
-      for (int i = 0; i < A.nparts; ++i) s2 += pp[i];
-      u00s[parity] = (float)s2;
-    }
-    const int ia = g * 2 * S::F + 2 * f, ib = ia + 1;
-    const bool va = act && ia < A.H, vb = act && ib < A.H;
-    const float2* ya_row = Y + ((size_t)field * A.H + (va ? ia : 0)) * A.ldY;
-    const float2* yb_row = Y + ((size_t)field * A.H + (vb ? ib : 0)) * A.ldY;
-    float2 v[S::R1];
-#pragma unroll
-    for (int r = 0; r < S::R1; ++r) {
-      // l = t + R2 r with t < R2: whether l lies below or above N/2 is known at
-      // compile time except for the one r whose range contains N/2
-      const int l = t + S::R2 * r;
-      const bool all_lo = S::R2 * r + S::R2 - 1 < half;
-      const bool all_hi = S::R2 * r > half;
-      const bool lo = all_lo || (!all_hi && l < half);
-      const int src = lo ? l : S::N - l;
-      float2 ya = va ? ya_row[src] : make_float2(0.0f, 0.0f);
-      float2 yb = vb ? yb_row[src] : make_float2(0.0f, 0.0f);
-      // bins 0 and N/2 are real in a real transform: drop their imaginary parts
-      const bool may_edge = (r == 0) || (!all_lo && !all_hi);
-      if (may_edge && (src == 0 || src == half)) {
-        ya.y = 0.0f;
-        yb.y = 0.0f;
-      }
-      v[r] = lo ? make_float2(ya.x - yb.y, ya.y + yb.x) : make_float2(ya.x + yb.y, yb.x - ya.y);
-    }    if (act) dft_reg<S::R1, +1>(v);
-    __syncthreads();  // previous item's stage 2 done with buf; u00 published
-    if (act) {
-#pragma unroll
-      for (int s2 = 0; s2 < S::R1; ++s2) mybuf[t * (S::R1 + 1) + s2] = v[s2];
-    }
-    __syncthreads();
-    if (act) {
-      const float u00 = u00s[parity];
-      T* o = out + (size_t)field * A.H * A.W;
-#pragma unroll
-      for (int jj = 0; jj < S::J2; ++jj) {
-        const int j = t + S::R2 * jj;
-        float2 u[S::R2];
-        u[0] = mybuf[j];
-#pragma unroll
-        for (int r = 1; r < S::R2; ++r) u[r] = cmul(mybuf[j + (S::R1 + 1) * r], cconj(tw2[j * S::R2 + r]));
-        dft_reg<S::R2, +1>(u);
-#pragma unroll
-        for (int s2 = 0; s2 < S::R2; ++s2) {
-          const int jc = j + S::R1 * s2 - kP;
-          // columns of this stage inside [0, WMIN) for every t need no crop test
-          const bool sure = (S::R2 * jj + S::R1 * s2 >= kP) && (S::R2 * jj + S::R2 - 1 + S::R1 * s2 - kP < S::WMIN);
-          if (sure || (jc >= 0 && jc < A.W)) {
-            if (va) o[(size_t)ia * A.W + jc] = f_from_f<T>(u[s2].x - u00);
-            if (vb) o[(size_t)ib * A.W + jc] = f_from_f<T>(u[s2].y - u00);
-          }
-        }
-      }
-    }
-  }
-}
-
-// ---------------------------------------------------------------------------
-// host side
-// ---------------------------------------------------------------------------
-using RowS1250 = RowShape<1250, 50, 25, 5>;
-using ColS810 = ColShape<810, 27, 30, 8>;
-
-bool fast_rows_supported(int N) { return N == 1250; }
-bool fast_cols_supported(int M) { return M == 810; }
-
-// The packed-row buffer also receives pass B's row-major output (H rows of
-// N/2+1 columns, stride rounded up to 4), so it is sized for the larger of the two.
-size_t fast_zbuf_elems(int H, int W, int N) {
-  (void)W;
-  const size_t groups = (size_t)(((H + 2) / 2) + 4) / 5;  // row groups of the 5-transform row pass
-  const size_t packed = groups * 5 * ((N + 3) & ~3);
-  const size_t rows = (size_t)H * (((N / 2 + 1) + 3) & ~3);
-  return packed > rows ? packed : rows;
-}
-
-static std::mutex g_fast_mu;
-
-// Set the kernel's shared-memory cap (each kernel here has one fixed size) and
-// return how many blocks of it fit on the device at once.
-template <typename K>
-static cudaError_t fast_setup(K kernel, int threads, size_t smem, int* slots) {
-  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  int per_sm = 0, dev = 0, sms = 0;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem)) != cudaSuccess) return e;
-  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-  *slots = (per_sm > 0 ? per_sm : 1) * sms;
-  return cudaSuccess;
-}
-
-template <class RS, class CS, typename T, int MODE>
-static cudaError_t run_fast(gfc_plan* P, const Bufs& bf, const T* in0, const T* in1, T* out, int nf,
-                            cudaStream_t st) {
-  FastArgs A;
-  A.H = P->H; A.W = P->W; A.p = P->pad; A.M = P->M; A.N = P->N; A.Nh = P->Nh; A.ldM = P->ldM;
-  A.nrows = (MODE == 0) ? P->H + 1 : P->H;
-  A.ncols = (MODE == 0) ? P->W + 1 : P->W;
-  A.npairs = (A.nrows + 1) / 2;
-  A.ldz = (RS::N + 3) & ~3;
-  A.ngroups = (A.npairs + RS::F - 1) / RS::F;
-  A.zpairs = A.ngroups * RS::F;
-  A.nparts = (P->Nh + CS::C - 1) / CS::C;
-  A.nf = nf;
-  A.ldY = (P->Nh + 3) & ~3;
-  static int slots_div = 0, slots_a = 0, slots_b = 0, slots_c = 0;
-  cudaError_t e;
-  {
-    std::lock_guard<std::mutex> lock(g_fast_mu);
-    if (!slots_a) {
-      if ((e = fast_setup(k_fast_div<T, MODE>, 256, 0, &slots_div)) != cudaSuccess) return e;
-      if ((e = fast_setup(k_fast_rows_fwd<RS>, RS::THREADS, RS::smem_bytes_fwd(), &slots_a)) != cudaSuccess) return e;
-      if ((e = fast_setup(k_fast_cols<CS>, CS::THREADS, CS::smem_bytes(), &slots_b)) != cudaSuccess) return e;
-      if ((e = fast_setup(k_fast_rows_inv<RS, T>, RS::THREADS, RS::smem_bytes(), &slots_c)) != cudaSuccess) return e;
-    }
-  }
-  auto grid_for = [](long items, int slots) { return (int)(items < slots ? items : slots); };
-  prof_begin(P, 3, st);
-  {
-    const int nq = A.ldz / 4, bx = nq >= 256 ? 256 : ((nq + 31) / 32) * 32;
-    k_fast_div<T, MODE><<<dim3((nq + bx - 1) / bx, A.zpairs, nf), bx, 0, st>>>(in0, in1, bf.zbuf, A);
-  }
-  prof_end(P, st);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  prof_begin(P, 0, st);
-  k_fast_rows_fwd<RS><<<grid_for((long)nf * A.ngroups, slots_a), RS::THREADS, RS::smem_bytes_fwd(), st>>>(
-      bf.zbuf, bf.spec, P->twN, A);
-  prof_end(P, st);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  prof_begin(P, 1, st);
-  k_fast_cols<CS><<<dim3(A.nparts, nf), CS::THREADS, CS::smem_bytes(), st>>>(bf.spec, bf.zbuf, P->GT, P->twM,
-                                                                               bf.partial, A);
-  prof_end(P, st);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  FastArgs C = A;
-  C.ngroups = ((P->H + 1) / 2 + RS::F - 1) / RS::F;
-  prof_begin(P, 2, st);
-  k_fast_rows_inv<RS, T><<<grid_for((long)nf * C.ngroups, slots_c), RS::THREADS, RS::smem_bytes(), st>>>(
-      bf.zbuf, bf.partial, out, P->twN, C);
-  prof_end(P, st);
-  return cudaGetLastError();
-}
-
-template <typename T>
-static cudaError_t run_fast_mode(gfc_plan* P, const Bufs& bf, int mode, const void* in0, const void* in1, void* out,
-                                 int nf, cudaStream_t st) {
-  const T* a = static_cast<const T*>(in0);
-  const T* b = static_cast<const T*>(in1);
-  T* o = static_cast<T*>(out);
-  if (P->N == 1250 && P->M == 810) {
-    if (mode == 0) return run_fast<RowS1250, ColS810, T, 0>(P, bf, a, b, o, nf, st);
-    return run_fast<RowS1250, ColS810, T, 1>(P, bf, a, b, o, nf, st);
-  }
-  return cudaErrorNotSupported;
-}
-
-cudaError_t run_chunk_fast(gfc_plan* P, const Bufs& bf, int mode, const void* in0, const void* in1, void* out,
-                           int nf, cudaStream_t st) {
-  switch (P->dtype) {
-    case GFC_F32: return run_fast_mode<float>(P, bf, mode, in0, in1, out, nf, st);
-    case GFC_F16: return run_fast_mode<__half>(P, bf, mode, in0, in1, out, nf, st);
-    default: return run_fast_mode<__nv_bfloat16>(P, bf, mode, in0, in1, out, nf, st);
-  }
+cudaError_t run_chunk_fast(gfc_plan* P, const Bufs& bf, int mode, const void* in0, const void* in1, void* out0,
+                           void* out1, int nf, cudaStream_t st) {
+  const FastEntry* e = find(P->M, P->N);
+  if (!e) return cudaErrorNotSupported;
+  return e->run(P, bf, mode, in0, in1, out0, out1, nf, st);
 }
 
 }  // namespace gfc

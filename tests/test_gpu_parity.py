@@ -241,6 +241,19 @@ def test_bad_tensor_arguments_raise():
 
 # ---------------------------------------------------------------- register-resident path
 
+def _torch_fp32_adjoint(gout, M, N, p):
+    """The adjoint in plain PyTorch FP32 (rfft2 / irfft2): the FP32 baseline error."""
+    H, W = gout.shape
+    G = torch.from_numpy(O.green_spectrum(M, N)[:, : N // 2 + 1]).float().to(DEV)
+    z = torch.zeros((M, N), device=DEV)
+    g = torch.from_numpy(np.ascontiguousarray(gout)).float().to(DEV)
+    z[p:p + H, p:p + W] = g
+    z[0, 0] -= g.sum()
+    w = torch.fft.irfft2(torch.fft.rfft2(z) * G, s=(M, N))
+    gx = (w - torch.roll(w, -1, -1))[p:p + H, p:p + W]
+    gy = (w - torch.roll(w, -1, -2))[p:p + H, p:p + W]
+    return gx.double().cpu().numpy(), gy.double().cpu().numpy()
+
 def _torch_fp32_solve(gx, gy, M, N, p):
     """The same math in plain PyTorch FP32 (rfft2 / irfft2): the FP32 baseline error."""
     H, W = gx.shape
@@ -324,4 +337,63 @@ def test_host_buffer_entry_matches_device_entry(H, W, B):
         p.solve_from_gradient_host(hx, hy, ho)
         torch.cuda.synchronize()
         assert torch.equal(ho, ref)
+    p.close()
+
+
+# image size -> padded size with a register-resident schedule
+FAST_SIZES = [(64, 96), (256, 256), (1024, 1536), (801, 1200)]
+
+
+@pytest.mark.parametrize("H,W", FAST_SIZES)
+def test_fast_shapes_forward_laplacian_adjoint_match_oracle(H, W):
+    rng = np.random.default_rng(H * 3 + W)
+    img = synth.gaussian_image(rng, H, W, 24, max(2.0, H / 30), max(4.0, H / 4))
+    gx, gy = synth.forward_gradient(img)
+    gx[5:9, 7:20] += 0.05  # a non-conservative edit
+    gx, gy = gx.astype(np.float32), gy.astype(np.float32)
+    p = gfc.Plan(H, W, 1, 1, device=DEV)
+    out = _np(p.solve_from_gradient(_to_dev(gx[None, None]), _to_dev(gy[None, None])))[0, 0]
+    ref = O.solve_from_gradient(gx.astype(np.float64), gy.astype(np.float64), p.M, p.N, p.pad)
+    e = _rel(out, ref)
+    assert e <= REL_F32 and np.abs(out - ref).max() <= MAXABS_F32 * max(1.0, np.abs(ref).max()), e
+    lap = (gx - np.pad(gx, ((0, 0), (1, 0)))[:, :-1]) + (gy - np.pad(gy, ((1, 0), (0, 0)))[:-1, :])
+    out = _np(p.solve_from_laplacian(_to_dev(lap[None, None])))[0, 0]
+    ref = O.solve_from_laplacian(lap.astype(np.float64), p.M, p.N, p.pad)
+    assert _rel(out, ref) <= REL_F32, _rel(out, ref)
+    gout = synth.upstream_gradient((H, W), seed=H)
+    bx, by = p.backward(_to_dev(gout[None, None]))
+    rx, ry = O.backward(gout.astype(np.float64), p.M, p.N, p.pad)
+    # N(0,1) upstream gradients are white noise: the same FP32 conditioning limit as
+    # white-noise gradients in the forward solve (see test_fast_path_matches_oracle)
+    tx_, ty_ = _torch_fp32_adjoint(gout, p.M, p.N, p.pad)
+    ex, ey = _rel(_np(bx)[0, 0], rx), _rel(_np(by)[0, 0], ry)
+    assert ex <= max(REL_F32, 3.0 * _rel(tx_, rx)), (ex, _rel(tx_, rx))
+    assert ey <= max(REL_F32, 3.0 * _rel(ty_, ry)), (ey, _rel(ty_, ry))
+    p.close()
+
+
+def test_fast_adjoint_agrees_with_generic_adjoint(monkeypatch):
+    H, W, C, B = 256, 256, 3, 2
+    gout = _to_dev(synth.upstream_gradient((B, C, H, W), seed=77))
+    fast = gfc.Plan(H, W, C, B, device=DEV)
+    monkeypatch.setenv("GFC_FORCE_GENERIC", "1")
+    gen = gfc.Plan(H, W, C, B, device=DEV)
+    monkeypatch.delenv("GFC_FORCE_GENERIC")
+    fx, fy = fast.backward(gout)
+    gx_, gy_ = gen.backward(gout)
+    # two FP32 evaluations of one linear map (spectral vs spatial differences)
+    assert _rel(_np(fx), _np(gx_)) <= REL_F32 and _rel(_np(fy), _np(gy_)) <= REL_F32
+    fast.close()
+    gen.close()
+
+
+@pytest.mark.parametrize("dtype", [torch.float16, torch.bfloat16])
+def test_blend_workload_16bit_storage(dtype):
+    gx, gy, _ = synth.poisson_blend_batch(batch=1, C=3, seed=2000)
+    tx, ty = _to_dev(gx, dtype), _to_dev(gy, dtype)
+    p = gfc.Plan(1024, 1536, 3, 1, dtype, device=DEV)
+    assert (p.M, p.N) == (1050, 1568)
+    out = _np(p.solve_from_gradient(tx, ty))
+    ref = O.solve_from_gradient(_np(tx)[0, 1], _np(ty)[0, 1], p.M, p.N, p.pad)
+    assert _rel(out[0, 1], ref) <= REL_16
     p.close()
