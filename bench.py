@@ -416,6 +416,60 @@ def extra_workloads(dev):
                                        "fwd_solves_per_s": nfld * 1000.0 / ms_f,
                                        "fwd_bwd_solves_per_s": nfld * 1000.0 / (ms_f + ms_b)}
     p.close()
+    res["edit_100x801x1200_fp32"] = _edit_workload(dev)
+    return res
+
+
+def _edit_workload(dev):
+    """The editing steps of Sec. 2.3.2 / Sec. 3.2 on 100 fields of 801x1200 (4 distinct images tiled)."""
+    import torch
+
+    from paper_1902_00176_gb300 import gfc, synth
+
+    B, H, W = 100, 801, 1200
+    img, gx, gy, edges = synth.edit_batch(4, 1, H, W, seed=5000)
+    rep = lambda a: torch.from_numpy(a).to(dev).repeat(B // 4, 1, 1, 1).contiguous()
+    timg, tx, ty, te = rep(img), rep(gx), rep(gy), rep(edges)
+    p = gfc.Plan(H, W, 1, B, device=dev)
+    out = p.solve_from_gradient(tx, ty)
+    ox, oy = torch.empty_like(tx), torch.empty_like(tx)
+    mean, std = p.field_stats(timg)
+    inner = torch.empty((B, 1, H - 6, W - 6), device=dev)
+    fb = 4.0 * H * W * B  # bytes of one [100, 1, 801, 1200] fp32 array
+    ops = {
+        # name: (callable, bytes each call moves as designed)
+        "field_stats": (lambda: p.field_stats(timg, mean, std), fb),
+        "color_correct": (lambda: p.color_correct(out, mean, std), 3 * fb),
+        "threshold_max": (lambda: p.gradient_threshold(tx, ty, 0.1, 0.0, ox, oy), 6 * fb),
+        "threshold_ref": (lambda: p.gradient_threshold(tx, ty, 0.1, 1.0, ox, oy), 4 * fb),
+        "merge": (lambda: p.gradient_merge(tx, ty, te, 0.5, ox, oy), 5 * fb),
+        "boundary_offset": (lambda: p.boundary_offset(out, 3, inner), 2 * fb * (H - 6) * (W - 6) / (H * W)),
+    }
+    peak = _peaks()[0]
+    res = {}
+    for name, (fn, nbytes) in ops.items():
+        ms = _time_ms(fn, dev, 10)
+        res[name] = {"ms": ms, "gb_per_s": nbytes / ms / 1e6, "frac_of_hbm": nbytes / ms / 1e6 / peak}
+
+    def pipeline():
+        p.gradient_threshold(tx, ty, 0.1, 0.0, ox, oy)
+        p.solve_from_gradient(ox, oy, out)
+        p.color_correct(out, mean, std)
+
+    ms = _time_ms(pipeline, dev, 5)
+    res["threshold_solve_correct"] = {"ms": ms, "solves_per_s": B * 1000.0 / ms}
+
+    def fused():
+        p.solve_edited(tx, ty, "threshold", frac=0.1, out=out)
+        p.color_correct(out, mean, std)
+
+    ms = _time_ms(fused, dev, 5)
+    res["threshold_solve_correct_fused"] = {"ms": ms, "solves_per_s": B * 1000.0 / ms}
+    ms = _time_ms(lambda: p.solve_edited(tx, ty, "threshold", frac=0.1, out=out), dev, 5)
+    res["solve_threshold_fused"] = {"ms": ms, "solves_per_s": B * 1000.0 / ms}
+    ms = _time_ms(lambda: p.solve_edited(tx, ty, "merge", alpha=0.5, edges=te, out=out), dev, 5)
+    res["solve_merge_fused"] = {"ms": ms, "solves_per_s": B * 1000.0 / ms}
+    p.close()
     return res
 
 

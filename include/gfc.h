@@ -200,6 +200,65 @@ gfc_status gfc_plan_get_profile(gfc_plan* plan, gfc_profile* out, int reset);
 gfc_status gfc_solve_from_gradient_noalloc(int H, int W, int fields, const void* gx, const void* gy, void* out,
                                            void* stream);
 
+/* ---- Gradient-domain editing around the solve (Sec. 2.3.2, Sec. 3.2) ----
+ * These act on [batch, C, H, W] arrays of a uniform plan, in the plan's dtype,
+ * on the plan's stream; per-field statistics are FP32 device arrays of
+ * batch * C values. Reductions accumulate in FP64 in a fixed order
+ * (deterministic). Ragged plans return GFC_ERR_UNSUPPORTED. */
+
+/* Mean and population standard deviation of every field of `fields`
+ * (mean, std: device arrays of batch * C floats). */
+gfc_status gfc_field_stats(gfc_plan* plan, const void* fields, float* mean, float* std);
+
+/* Colour correction of Eq. 25 (Sec. 3.2.2), in place on a solved `out`:
+ * out = (out - mean(out)) * ref_std / std(out) + ref_mean per field, where
+ * ref_mean / ref_std are the statistics of the original image (for example
+ * from gfc_field_stats). A field with std(out) = 0 becomes ref_mean. */
+gfc_status gfc_color_correct(gfc_plan* plan, void* out, const float* ref_mean, const float* ref_std);
+
+/* Gradient thresholding (Sec. 3.1.4, Sec. 3.2.3): pixels whose gradient
+ * magnitude |E| = sqrt(gx^2 + gy^2) is below frac * r get gx = gy = 0; other
+ * pixels are copied bit for bit. r is `ref` when ref > 0 (the highest
+ * possible gradient of an image of known range), else the field's largest
+ * magnitude. The decision is taken in FP32 without contraction:
+ * m2 = fl(fl(gx*gx) + fl(gy*gy)), r = fl(sqrt(max m2)), t = fl(frac*r), and
+ * the pixel is dropped when m2 < fl(t*t). frac >= 0. Writes gx_out, gy_out
+ * (which may be gx, gy). */
+gfc_status gfc_gradient_threshold(gfc_plan* plan, const void* gx, const void* gy, float frac, float ref,
+                                  void* gx_out, void* gy_out);
+
+/* Gradient-domain merging of Eq. 26 (Sec. 3.2.4): |E_p| = |E|^(1-alpha) C^alpha
+ * with the orientation of E kept, i.e. E_p = E |E|^(-alpha) C^alpha per pixel
+ * (E_p = 0 where |E| = 0). `edges` holds the edge intensity C >= 0 in the
+ * plan's layout and dtype; 0 <= alpha <= 1. Writes gx_out, gy_out (which may
+ * be gx, gy). */
+gfc_status gfc_gradient_merge(gfc_plan* plan, const void* gx, const void* gy, const void* edges, float alpha,
+                              void* gx_out, void* gy_out);
+
+/* A gradient edit applied inside a solve (gfc_solve_edited). */
+typedef enum { GFC_EDIT_NONE = 0, GFC_EDIT_THRESHOLD = 1, GFC_EDIT_MERGE = 2 } gfc_edit_kind;
+typedef struct {
+  int kind;          /* gfc_edit_kind */
+  float frac, ref;   /* GFC_EDIT_THRESHOLD: as in gfc_gradient_threshold */
+  float alpha;       /* GFC_EDIT_MERGE: as in gfc_gradient_merge */
+  const void* edges; /* GFC_EDIT_MERGE: edge map [batch, C, H, W] in the plan's dtype */
+} gfc_edit;
+
+/* Solve (Eq. 23) from a gradient edited as it is loaded: the same output, bit
+ * for bit, as gfc_gradient_threshold or gfc_gradient_merge into temporaries
+ * followed by gfc_solve_from_gradient, without the edited gradient ever being
+ * written or read back. A threshold with ref <= 0 first reads gx and gy once
+ * for the per-field largest magnitudes. Uniform plans only; `edit` is read
+ * during the call. */
+gfc_status gfc_solve_edited(gfc_plan* plan, const void* gx, const void* gy, const gfc_edit* edit, void* out);
+
+/* Boundary-preserving offset (Sec. 2.3.2): for fields solved from an image
+ * that was padded by `ring` pixels on every side, subtract the mean of the
+ * solution over that ring (the least-squares constant that makes the padded
+ * region zero) and write the inner (H - 2 ring) x (W - 2 ring) block of every
+ * field to `inner`, contiguous [batch, C, H - 2 ring, W - 2 ring]. */
+gfc_status gfc_boundary_offset(gfc_plan* plan, const void* out, int ring, void* inner);
+
 /* A solve call captured once as a CUDA graph and replayed with one launch.
  * The graph is bound to the plan, the operation and the pointers given at
  * capture; replaying it recomputes the same operation on whatever those

@@ -230,6 +230,98 @@ __global__ void __launch_bounds__(512) k_fast_div(const T* __restrict__ in0, con
   }
 }
 
+// Pass L with a gradient edit applied as the gradient is loaded (Sec. 3.2.3
+// thresholding, Eq. 26 merging): the same packed rows as k_fast_div<T, 0> on
+// the edited field, bit for bit, without the edited field ever being stored.
+// Every edited pixel is computed once: a thread owns 4 columns and walks down
+// kEditPairs row pairs, keeping the edited gy of the row above in registers;
+// the edited gx of the column to its left comes from the neighbouring lane
+// (lane 0 edits that one pixel itself).
+constexpr int kEditPairs = 8;
+
+template <typename T, int EDIT>
+__device__ __forceinline__ void edit_row4(const T* __restrict__ a, const T* __restrict__ b,
+                                          const T* __restrict__ e, int i, int j0, const FastArgs& A, float t2,
+                                          float alpha, float* ex, float* ey) {
+  if (i < 0 || i >= A.H || j0 + 3 < 0 || j0 >= A.W) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) ex[k] = ey[k] = 0.0f;
+    return;
+  }
+  if ((A.W % 4) == 0 && j0 >= 0 && j0 + 3 < A.W) {
+    const float4 x = ld4(a, i, j0, A.W), y = ld4(b, i, j0, A.W);
+    float xs[4] = {x.x, x.y, x.z, x.w}, ys[4] = {y.x, y.y, y.z, y.w}, cs[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    if (EDIT == kEditMerge) {
+      const float4 c = ld4(e, i, j0, A.W);
+      cs[0] = c.x; cs[1] = c.y; cs[2] = c.z; cs[3] = c.w;
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      if (EDIT == kEditThreshold) {
+        const bool drop = edit_mag2(xs[k], ys[k]) < t2;
+        ex[k] = drop ? 0.0f : xs[k];
+        ey[k] = drop ? 0.0f : ys[k];
+      } else {
+        const float sc = edit_merge_scale(xs[k], ys[k], cs[k], alpha);
+        ex[k] = edit_round(__fmul_rn(xs[k], sc), a);
+        ey[k] = edit_round(__fmul_rn(ys[k], sc), a);
+      }
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const float2 v = edit_pixel<T, EDIT>(a, b, e, i, j0 + k, A.H, A.W, t2, alpha);
+      ex[k] = v.x;
+      ey[k] = v.y;
+    }
+  }
+}
+
+template <typename T, int EDIT>
+__global__ void __launch_bounds__(512) k_fast_div_edit(const T* __restrict__ gx, const T* __restrict__ gy,
+                                                       const T* __restrict__ edges, const float* __restrict__ t2s,
+                                                       float alpha, float2* __restrict__ z, FastArgs A) {
+  // grid: x = groups of 4 padded columns (whole warps), y = blocks of kEditPairs
+  // packed rows, z = fields. Every lane stays to the end (warp shuffles).
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  const int field = blockIdx.z, lane = threadIdx.x & 31;
+  const bool inq = q < A.ldz / 4;
+  const int c0 = 4 * q, j0 = c0 - kP;
+  const size_t fe = (size_t)A.H * A.W;
+  const T* a = gx + field * fe;
+  const T* b = gy + field * fe;
+  const T* e = (EDIT == kEditMerge) ? edges + field * fe : nullptr;
+  const float t2 = (EDIT == kEditThreshold) ? t2s[field] : 0.0f;
+  const int p0 = blockIdx.y * kEditPairs;
+  const int p1 = min(p0 + kEditPairs, A.zpairs);
+  // edited gy of the row above the first row of the block
+  float ym[4], scratch[4];
+  edit_row4<T, EDIT>(a, b, e, 2 * p0 - 1, j0, A, t2, alpha, scratch, ym);
+  for (int pair = p0; pair < p1; ++pair) {
+    float L[2][4];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int i = 2 * pair + h;
+      float ex[4], ey[4];
+      edit_row4<T, EDIT>(a, b, e, i, j0, A, t2, alpha, ex, ey);
+      float left = __shfl_up_sync(0xffffffffu, ex[3], 1);
+      if (lane == 0) left = edit_pixel<T, EDIT>(a, b, e, i, j0 - 1, A.H, A.W, t2, alpha).x;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const float xl = (k == 0) ? left : ex[k - 1];
+        const bool in = j0 + k >= 0 && j0 + k < A.ncols && i < A.nrows && pair < A.npairs;
+        L[h][k] = in ? (ex[k] - xl) + (ey[k] - ym[k]) : 0.0f;
+        ym[k] = ey[k];
+      }
+    }
+    if (inq) {
+      float4* dst = reinterpret_cast<float4*>(z + ((size_t)field * A.zpairs + pair) * A.ldz + c0);
+      dst[0] = make_float4(L[0][0], L[1][0], L[0][1], L[1][1]);
+      dst[1] = make_float4(L[0][2], L[1][2], L[0][3], L[1][3]);
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // pass A: forward row transforms of the packed rows + two-for-one split +
 // transposed store. Persistent over (field, group of F row pairs).
@@ -660,7 +752,7 @@ static cudaError_t fast_setup(K kernel, int threads, size_t smem, int* slots) {
 // out0 = grad_gx, out1 = grad_gy).
 template <class RS, class CS, typename T, int MODE>
 static cudaError_t run_fast_mode(gfc_plan* P, const Bufs& bf, const T* in0, const T* in1, T* out0, T* out1, int nf,
-                                 cudaStream_t st) {
+                                 cudaStream_t st, const EditArgs* ed = nullptr) {
   static_assert(RS::N <= 2048, "the adjoint packing pass covers a whole row in one block");
   FastArgs A;
   A.H = P->H; A.W = P->W; A.p = P->pad; A.M = P->M; A.N = P->N; A.Nh = P->Nh; A.ldM = P->ldM;
@@ -695,7 +787,17 @@ static cudaError_t run_fast_mode(gfc_plan* P, const Bufs& bf, const T* in0, cons
   {
     const int nq = A.ldz / 4;
     const int bx = (MODE == 2) ? ((nq + 31) / 32) * 32 : (nq >= 256 ? 256 : ((nq + 31) / 32) * 32);
-    k_fast_div<T, MODE><<<dim3((nq + bx - 1) / bx, A.zpairs, nf), bx, 0, st>>>(in0, in1, bf.zbuf, bf.partial, A);
+    const dim3 grid((nq + bx - 1) / bx, A.zpairs, nf);
+    const int kind = (MODE == 0 && ed) ? ed->kind : kEditNone;
+    const int ex = ((nq + 31) / 32) * 32 <= 512 ? ((nq + 31) / 32) * 32 : 256;  // whole warps
+    const dim3 egrid((nq + ex - 1) / ex, (A.zpairs + kEditPairs - 1) / kEditPairs, nf);
+    if (kind == kEditThreshold)
+      k_fast_div_edit<T, kEditThreshold><<<egrid, ex, 0, st>>>(in0, in1, nullptr, ed->t2, 0.0f, bf.zbuf, A);
+    else if (kind == kEditMerge)
+      k_fast_div_edit<T, kEditMerge><<<egrid, ex, 0, st>>>(in0, in1, static_cast<const T*>(ed->edges), nullptr,
+                                                           ed->alpha, bf.zbuf, A);
+    else
+      k_fast_div<T, MODE><<<grid, bx, 0, st>>>(in0, in1, bf.zbuf, bf.partial, A);
   }
   prof_end(P, st);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -726,14 +828,14 @@ static cudaError_t run_fast_mode(gfc_plan* P, const Bufs& bf, const T* in0, cons
 
 template <class RS, class CS>
 cudaError_t run_fast_shape(gfc_plan* P, const Bufs& bf, int mode, const void* in0, const void* in1, void* out0,
-                           void* out1, int nf, cudaStream_t st) {
+                           void* out1, int nf, cudaStream_t st, const EditArgs* ed) {
   auto go = [&](auto tag) -> cudaError_t {
     using T = decltype(tag);
     const T* a = static_cast<const T*>(in0);
     const T* b = static_cast<const T*>(in1);
     T* o0 = static_cast<T*>(out0);
     T* o1 = static_cast<T*>(out1);
-    if (mode == 0) return run_fast_mode<RS, CS, T, 0>(P, bf, a, b, o0, o1, nf, st);
+    if (mode == 0) return run_fast_mode<RS, CS, T, 0>(P, bf, a, b, o0, o1, nf, st, ed);
     if (mode == 1) return run_fast_mode<RS, CS, T, 1>(P, bf, a, b, o0, o1, nf, st);
     return run_fast_mode<RS, CS, T, 2>(P, bf, a, b, o0, o1, nf, st);
   };

@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include "../../include/gfc.h"
+#include "edit_ops.cuh"
 #include "fft_core.cuh"
 
 namespace gfc {
@@ -51,6 +52,7 @@ struct gfc_plan {
   float2* twM;    // [M] exp(-2 pi i m / M)
   float2* spec;   // [slots][chunk] spectrum scratch (per field: max(M ldS, Nh ldM) complex)
   float* partial; // [slots][chunk][kMaxRowBlocks] per-block sums (adjoint, u[0,0])
+  float* edit_t2; // [batch * C] squared gradient threshold per field (Sec. 3.2.3)
   float2* zbuf;   // [slots][chunk] packed rows of L / row-major spectrum (fast passes)
   size_t spec_field, zbuf_field;  // elements per field of spec and zbuf
   int nslots;                     // chunks in flight
@@ -104,8 +106,9 @@ cudaError_t build_green_t(float* GT, int M, int N, int Nh, int ldM, cudaStream_t
 bool fast_supported(int M, int N);
 size_t fast_zbuf_elems(int H, int M, int N);  // per field
 // mode 0 gradient, 1 Laplacian, 2 adjoint (out1 = grad_gy)
+// `ed` (mode 0 only, may be null) applies a gradient edit as the gradient is loaded
 cudaError_t run_chunk_fast(gfc_plan* P, const Bufs& B, int mode, const void* in0, const void* in1, void* out0,
-                           void* out1, int nf, cudaStream_t st);
+                           void* out1, int nf, cudaStream_t st, const EditArgs* ed = nullptr);
 inline Bufs slot_bufs(const gfc_plan* P, int s) {
   Bufs b;
   b.spec = P->spec + (size_t)s * P->chunk * P->spec_field;
@@ -119,6 +122,10 @@ inline size_t dtype_size(gfc_dtype d) { return d == GFC_F32 ? 4 : 2; }
 // tracing around one kernel launch on the plan's stream
 void prof_begin(gfc_plan* P, int pass, cudaStream_t st);
 void prof_end(gfc_plan* P, cudaStream_t st);
+// per-field squared thresholds of Sec. 3.2.3 into P->edit_t2 (edit.cu): from
+// the fields' largest gradient magnitudes when ref <= 0, else from ref
+gfc_status edit_prepare_threshold(gfc_plan* P, const void* gx, const void* gy, float frac, float ref);
+
 // free the host-buffer pipeline and the profiling event pool (plan teardown)
 void release_host_state(gfc_plan* P);
 

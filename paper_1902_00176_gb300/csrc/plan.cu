@@ -225,6 +225,7 @@ gfc_status gfc_plan_create_ex(gfc_plan** out, const gfc_plan_opts* o) {
   if (e == cudaSuccess) e = cudaMalloc(&p->twM, (size_t)M * sizeof(float2));
   if (e == cudaSuccess) e = cudaMalloc(&p->spec, per_field * (size_t)chunk * nslots);
   if (e == cudaSuccess) e = cudaMalloc(&p->partial, (size_t)chunk * nslots * kMaxRowBlocks * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&p->edit_t2, (size_t)fields * sizeof(float));
   for (int sl = 0; sl < nslots && e == cudaSuccess; ++sl) {
     e = cudaStreamCreateWithFlags(&p->slot_stream[sl], cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->slot_done[sl], cudaEventDisableTiming);
@@ -437,6 +438,7 @@ static void destroy_plan(gfc_plan* p) {
   cudaFree(p->twM);
   cudaFree(p->spec);
   cudaFree(p->partial);
+  cudaFree(p->edit_t2);
   for (int sl = 0; sl < kMaxSlots; ++sl) {
     if (p->slot_stream[sl]) cudaStreamDestroy(p->slot_stream[sl]);
     if (p->slot_done[sl]) cudaEventDestroy(p->slot_done[sl]);

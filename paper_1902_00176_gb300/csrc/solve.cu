@@ -109,10 +109,12 @@ __device__ double block_sum_d(double v, double* red) {
 // ---------------------------------------------------------------------------
 // pass A
 // ---------------------------------------------------------------------------
-template <typename T, int MODE>
+// EDIT (gradient mode only): the edit of Sec. 3.2.3 / Eq. 26 applied to every
+// gradient value as it is loaded (edit_pixel), so the edited field is never stored.
+template <typename T, int MODE, int EDIT = kEditNone>
 __global__ void __launch_bounds__(256) k_pass_a(const T* __restrict__ in0, const T* __restrict__ in1,
                                                 float2* __restrict__ spec, float* __restrict__ partial,
-                                                const float2* __restrict__ twg, PassArgs A) {
+                                                const float2* __restrict__ twg, PassArgs A, EditArgs ed) {
   extern __shared__ float2 sm[];
   __shared__ float red[32];
   long long in_off = (long long)blockIdx.y * A.H * A.W, spec_off = (long long)blockIdx.y * A.M * A.ldS;
@@ -142,7 +144,17 @@ __global__ void __launch_bounds__(256) k_pass_a(const T* __restrict__ in0, const
       const int j = c - A.p;
       float va = 0.0f, vb = 0.0f;
       if (j >= 0 && j < A.ncols) {
-        if (MODE == kGrad) {
+        if (MODE == kGrad && EDIT != kEditNone) {
+          const T* e = static_cast<const T*>(ed.edges) + (ed.edges ? in_off : 0);
+          const float t2 = (EDIT == kEditThreshold) ? ed.t2[blockIdx.y] : 0.0f;
+          const float2 c0 = edit_pixel<T, EDIT>(a, b, e, i0, j, A.H, A.W, t2, ed.alpha);
+          va = c0.x - edit_pixel<T, EDIT>(a, b, e, i0, j - 1, A.H, A.W, t2, ed.alpha).x + c0.y -
+               edit_pixel<T, EDIT>(a, b, e, i0 - 1, j, A.H, A.W, t2, ed.alpha).y;
+          if (has1) {
+            const float2 c1 = edit_pixel<T, EDIT>(a, b, e, i1, j, A.H, A.W, t2, ed.alpha);
+            vb = c1.x - edit_pixel<T, EDIT>(a, b, e, i1, j - 1, A.H, A.W, t2, ed.alpha).x + c1.y - c0.y;
+          }
+        } else if (MODE == kGrad) {
           va = ld(a, i0, j, A.H, A.W) - ld(a, i0, j - 1, A.H, A.W) + ld(b, i0, j, A.H, A.W) - ld(b, i0 - 1, j, A.H, A.W);
           if (has1)
             vb = ld(a, i1, j, A.H, A.W) - ld(a, i1, j - 1, A.H, A.W) + ld(b, i1, j, A.H, A.W) - ld(b, i1 - 1, j, A.H, A.W);
@@ -461,8 +473,10 @@ static cudaError_t launch_b_any(gfc_plan* P, const Bufs& bf, PassArgs B, int nf,
 
 template <typename T, int MODE>
 static cudaError_t run_chunk(gfc_plan* P, const Bufs& bf, const T* in0, const T* in1, T* out0, T* out1, int nf,
-                             cudaStream_t st) {
-  if (P->fast) return run_chunk_fast(P, bf, MODE, in0, in1, out0, out1, nf, st);
+                             cudaStream_t st, const EditArgs* ed = nullptr) {
+  if (P->fast) return run_chunk_fast(P, bf, MODE, in0, in1, out0, out1, nf, st, ed);
+  const EditArgs none{kEditNone, 0.0f, nullptr, nullptr};
+  const EditArgs& E = ed ? *ed : none;
   // pass A
   PassArgs A = base_args(P);
   A.nrows = (MODE == kGrad) ? P->H + 1 : P->H;
@@ -475,9 +489,13 @@ static cudaError_t run_chunk(gfc_plan* P, const Bufs& bf, const T* in0, const T*
   {
       const size_t smem = 3 * (size_t)P->N * sizeof(float2);
     auto k = k_pass_a<T, MODE>;
+    if constexpr (MODE == kGrad) {
+      if (E.kind == kEditThreshold) k = k_pass_a<T, MODE, kEditThreshold>;
+      if (E.kind == kEditMerge) k = k_pass_a<T, MODE, kEditMerge>;
+    }
     if ((e = ensure_smem(k, smem)) != cudaSuccess) return e;
     prof_begin(P, 0, st);
-    k<<<dim3(A.nparts, nf), 256, smem, st>>>(in0, in1, bf.spec, bf.partial, P->twN, A);
+    k<<<dim3(A.nparts, nf), 256, smem, st>>>(in0, in1, bf.spec, bf.partial, P->twN, A, E);
     prof_end(P, st);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
@@ -510,7 +528,8 @@ static cudaError_t run_chunk(gfc_plan* P, const Bufs& bf, const T* in0, const T*
 // Chunk c runs on slot c mod nslots: its own scratch and internal stream, forked
 // from the plan's stream and joined back into it at the end of the call.
 template <typename T, int MODE>
-static gfc_status run_all(gfc_plan* P, const void* a, const void* b, void* o0, void* o1) {
+static gfc_status run_all(gfc_plan* P, const void* a, const void* b, void* o0, void* o1,
+                          const EditArgs* ed = nullptr) {
   const long fields = (long)P->batch * P->C;
   const size_t fe = (size_t)P->H * P->W;
   P->prof.calls += 1;
@@ -527,8 +546,14 @@ static gfc_status run_all(gfc_plan* P, const void* a, const void* b, void* o0, v
     T* out0 = static_cast<T*>(o0) + f0 * fe;
     T* out1 = o1 ? static_cast<T*>(o1) + f0 * fe : nullptr;
     const int s = fork ? (int)(c % P->nslots) : 0;
+    EditArgs ec{kEditNone, 0.0f, nullptr, nullptr};
+    if (ed) {  // the edit's per-field data, at this chunk's first field
+      ec = *ed;
+      if (ec.edges) ec.edges = static_cast<const T*>(ec.edges) + f0 * fe;
+      if (ec.t2) ec.t2 += f0;
+    }
     cudaError_t e = run_chunk<T, MODE>(P, slot_bufs(P, s), in0, in1, out0, out1, nf,
-                                       fork ? P->slot_stream[s] : P->stream);
+                                       fork ? P->slot_stream[s] : P->stream, ed ? &ec : nullptr);
     if (e != cudaSuccess) return cuda_fail(e, "gfc solve launch");
   }
   if (fork) {
@@ -567,7 +592,8 @@ static gfc_status run_ragged(gfc_plan* P, const void* a, const void* b, void* o0
       if ((e = ensure_smem(k, smem)) != cudaSuccess) return cuda_fail(e, "gfc ragged pass A");
       prof_begin(P, 0, st);
       k<<<dim3(ceil_div(pairs_max, ppb), nf), 256, smem, st>>>(static_cast<const T*>(a), static_cast<const T*>(b),
-                                                                 P->spec, P->partial, P->twN, A);
+                                                                 P->spec, P->partial, P->twN, A,
+                                                                 EditArgs{kEditNone, 0.0f, nullptr, nullptr});
       prof_end(P, st);
       if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "gfc ragged pass A");
     }
@@ -616,7 +642,8 @@ static gfc_status run_ragged(gfc_plan* P, const void* a, const void* b, void* o0
 }
 
 template <int MODE>
-static gfc_status dispatch(gfc_plan* P, const void* a, const void* b, void* o0, void* o1) {
+static gfc_status dispatch(gfc_plan* P, const void* a, const void* b, void* o0, void* o1,
+                           const EditArgs* ed = nullptr) {
   if (P->ragged) {
     switch (P->dtype) {
       case GFC_F32: return run_ragged<float, MODE>(P, a, b, o0, o1);
@@ -625,9 +652,9 @@ static gfc_status dispatch(gfc_plan* P, const void* a, const void* b, void* o0, 
     }
   }
   switch (P->dtype) {
-    case GFC_F32: return run_all<float, MODE>(P, a, b, o0, o1);
-    case GFC_F16: return run_all<__half, MODE>(P, a, b, o0, o1);
-    default: return run_all<__nv_bfloat16, MODE>(P, a, b, o0, o1);
+    case GFC_F32: return run_all<float, MODE>(P, a, b, o0, o1, ed);
+    case GFC_F16: return run_all<__half, MODE>(P, a, b, o0, o1, ed);
+    default: return run_all<__nv_bfloat16, MODE>(P, a, b, o0, o1, ed);
   }
 }
 
@@ -743,6 +770,35 @@ gfc_status gfc_solve_from_gradient(gfc_plan* plan, const void* gx, const void* g
     return fail(GFC_ERR_INVALID_ARG, "gfc_solve_from_gradient: pointers must be 16-byte aligned");
   if (out == gx || out == gy) return fail(GFC_ERR_INVALID_ARG, "gfc_solve_from_gradient: out aliases an input");
   return dispatch<kGrad>(plan, gx, gy, out, nullptr);
+}
+
+gfc_status gfc_solve_edited(gfc_plan* plan, const void* gx, const void* gy, const gfc_edit* edit, void* out) {
+  clear_error();
+  if (!plan || !gx || !gy || !edit || !out) return fail(GFC_ERR_INVALID_ARG, "gfc_solve_edited: null argument");
+  if (misaligned(gx) || misaligned(gy) || misaligned(out))
+    return fail(GFC_ERR_INVALID_ARG, "gfc_solve_edited: pointers must be 16-byte aligned");
+  if (out == gx || out == gy || out == edit->edges)
+    return fail(GFC_ERR_INVALID_ARG, "gfc_solve_edited: out aliases an input");
+  if (edit->kind == GFC_EDIT_NONE) return dispatch<kGrad>(plan, gx, gy, out, nullptr);
+  if (plan->ragged) return fail(GFC_ERR_UNSUPPORTED, "gfc_solve_edited: ragged plans are not supported");
+  EditArgs ed{kEditNone, 0.0f, nullptr, nullptr};
+  if (edit->kind == GFC_EDIT_THRESHOLD) {
+    if (!(edit->frac >= 0.0f) || !(edit->ref == edit->ref))
+      return fail(GFC_ERR_INVALID_ARG, "gfc_solve_edited: frac must be >= 0 and ref a number");
+    if (gfc_status s = edit_prepare_threshold(plan, gx, gy, edit->frac, edit->ref)) return s;
+    ed.kind = kEditThreshold;
+    ed.t2 = plan->edit_t2;
+  } else if (edit->kind == GFC_EDIT_MERGE) {
+    if (!edit->edges) return fail(GFC_ERR_INVALID_ARG, "gfc_solve_edited: merge needs an edge map");
+    if (!(edit->alpha >= 0.0f && edit->alpha <= 1.0f))
+      return fail(GFC_ERR_INVALID_ARG, "gfc_solve_edited: alpha outside [0, 1]");
+    ed.kind = kEditMerge;
+    ed.alpha = edit->alpha;
+    ed.edges = edit->edges;
+  } else {
+    return fail(GFC_ERR_INVALID_ARG, "gfc_solve_edited: unknown edit kind %d", edit->kind);
+  }
+  return dispatch<kGrad>(plan, gx, gy, out, nullptr, &ed);
 }
 
 gfc_status gfc_solve_from_laplacian(gfc_plan* plan, const void* lap, void* out) {

@@ -6,7 +6,7 @@ namespace gfc {
 
 #define GFC_FAST_SHAPE(M, N)                                                                                  \
   cudaError_t fast_run_##M##x##N(gfc_plan*, const Bufs&, int, const void*, const void*, void*, void*, int, \
-                                 cudaStream_t);                                                           \
+                                 cudaStream_t, const EditArgs*);                                          \
   size_t fast_zbuf_##M##x##N(int H);
 GFC_FAST_SHAPE(810, 1250)
 GFC_FAST_SHAPE(1050, 1568)
@@ -17,7 +17,8 @@ GFC_FAST_SHAPE(72, 108)
 namespace {
 struct FastEntry {
   int M, N;
-  cudaError_t (*run)(gfc_plan*, const Bufs&, int, const void*, const void*, void*, void*, int, cudaStream_t);
+  cudaError_t (*run)(gfc_plan*, const Bufs&, int, const void*, const void*, void*, void*, int, cudaStream_t,
+                     const EditArgs*);
   size_t (*zbuf)(int H);
 };
 const FastEntry kFast[] = {
@@ -41,10 +42,10 @@ size_t fast_zbuf_elems(int H, int M, int N) {
 }
 
 cudaError_t run_chunk_fast(gfc_plan* P, const Bufs& bf, int mode, const void* in0, const void* in1, void* out0,
-                           void* out1, int nf, cudaStream_t st) {
+                           void* out1, int nf, cudaStream_t st, const EditArgs* ed) {
   const FastEntry* e = find(P->M, P->N);
   if (!e) return cudaErrorNotSupported;
-  return e->run(P, bf, mode, in0, in1, out0, out1, nf, st);
+  return e->run(P, bf, mode, in0, in1, out0, out1, nf, st, ed);
 }
 
 }  // namespace gfc

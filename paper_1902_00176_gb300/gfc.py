@@ -45,6 +45,14 @@ class Item(ctypes.Structure):
     _fields_ = [("H", ctypes.c_int), ("W", ctypes.c_int), ("C", ctypes.c_int), ("offset", ctypes.c_longlong)]
 
 
+class _Edit(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("frac", ctypes.c_float), ("ref", ctypes.c_float),
+                ("alpha", ctypes.c_float), ("edges", ctypes.c_void_p)]
+
+
+EDIT_KINDS = {"none": 0, "threshold": 1, "merge": 2}
+
+
 class Profile(ctypes.Structure):
     """Mirror of gfc_profile: per-pass device time (ms) and launch counts."""
     _fields_ = [("pass_ms", ctypes.c_double * 4), ("launches", ctypes.c_long * 4), ("calls", ctypes.c_long),
@@ -71,6 +79,7 @@ _SIGNATURES = {
                              ctypes.POINTER(ctypes.c_int)],
     "gfc_plan_copy_green": [ctypes.c_void_p, ctypes.c_void_p],
     "gfc_solve_from_gradient": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
+    "gfc_solve_edited": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(_Edit), ctypes.c_void_p],
     "gfc_solve_from_laplacian": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
     "gfc_backward": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
     "gfc_fft_c2c": [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
@@ -79,6 +88,13 @@ _SIGNATURES = {
     "gfc_plan_get_profile": [ctypes.c_void_p, ctypes.POINTER(Profile), ctypes.c_int],
     "gfc_solve_from_gradient_noalloc": [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                         ctypes.c_void_p, ctypes.c_void_p],
+    "gfc_field_stats": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
+    "gfc_color_correct": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
+    "gfc_gradient_threshold": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_float, ctypes.c_float,
+                               ctypes.c_void_p, ctypes.c_void_p],
+    "gfc_gradient_merge": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_float,
+                           ctypes.c_void_p, ctypes.c_void_p],
+    "gfc_boundary_offset": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p],
     "gfc_graph_create": [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                          ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)],
     "gfc_graph_launch": [ctypes.c_void_p, ctypes.c_void_p],
@@ -193,6 +209,25 @@ class Plan:
         _check(lib().gfc_solve_from_gradient(self._h, gx.data_ptr(), gy.data_ptr(), out.data_ptr()))
         return out
 
+    def solve_edited(self, gx, gy, edit="threshold", frac=0.1, ref=0.0, alpha=0.5, edges=None, out=None):
+        """Solve from the gradient with an edit applied as it is loaded: ``edit`` is
+        "threshold" (Sec. 3.2.3: |E| < frac * r set to 0) or "merge" (Eq. 26 with
+        the edge map ``edges`` and weight ``alpha``)."""
+        gx, gy = self._check_field(gx, "gx"), self._check_field(gy, "gy")
+        if edit not in EDIT_KINDS:
+            raise ValueError(f"unknown edit {edit!r}")
+        eptr = None
+        if edit == "merge":
+            if edges is None:
+                raise ValueError("merge needs an edge map")
+            edges = self._check_field(edges, "edges")
+            eptr = edges.data_ptr()
+        out = self._empty() if out is None else self._check_field(out, "out")
+        e = _Edit(EDIT_KINDS[edit], float(frac), float(ref), float(alpha), eptr)
+        self._bind_stream()
+        _check(lib().gfc_solve_edited(self._h, gx.data_ptr(), gy.data_ptr(), ctypes.byref(e), out.data_ptr()))
+        return out
+
     def solve_from_laplacian(self, lap, out=None):
         lap = self._check_field(lap, "lap")
         out = self._empty() if out is None else self._check_field(out, "out")
@@ -219,6 +254,65 @@ class Plan:
         self._bind_stream()
         _check(lib().gfc_solve_from_gradient_host(self._h, gx.data_ptr(), gy.data_ptr(), out.data_ptr()))
         return out
+
+    # ---- gradient-domain editing (Sec. 2.3.2, Sec. 3.2) ----
+    def _stats_tensor(self, t, name):
+        if t is None:
+            return torch.empty((self.batch, self.C), dtype=torch.float32, device=self.device)
+        if not t.is_cuda or t.device != self.device or t.dtype != torch.float32 or not t.is_contiguous() or \
+                t.numel() != self.batch * self.C:
+            raise ValueError(f"{name} must be a contiguous float32 CUDA tensor of {self.batch * self.C} values")
+        return t
+
+    def field_stats(self, x, mean=None, std=None):
+        """Per-field mean and population standard deviation, each [batch, C] float32."""
+        x = self._check_field(x, "x")
+        mean, std = self._stats_tensor(mean, "mean"), self._stats_tensor(std, "std")
+        self._bind_stream()
+        _check(lib().gfc_field_stats(self._h, x.data_ptr(), mean.data_ptr(), std.data_ptr()))
+        return mean, std
+
+    def color_correct(self, out, ref_mean, ref_std):
+        """Eq. 25 in place on ``out``: rescale each field to the original's mean and contrast."""
+        out = self._check_field(out, "out")
+        ref_mean, ref_std = self._stats_tensor(ref_mean, "ref_mean"), self._stats_tensor(ref_std, "ref_std")
+        self._bind_stream()
+        _check(lib().gfc_color_correct(self._h, out.data_ptr(), ref_mean.data_ptr(), ref_std.data_ptr()))
+        return out
+
+    def gradient_threshold(self, gx, gy, frac, ref=0.0, gx_out=None, gy_out=None):
+        """Zero the gradient where |E| < frac * r (r = ref if ref > 0, else the field's largest |E|)."""
+        gx, gy = self._check_field(gx, "gx"), self._check_field(gy, "gy")
+        gx_out = self._empty() if gx_out is None else self._check_field(gx_out, "gx_out")
+        gy_out = self._empty() if gy_out is None else self._check_field(gy_out, "gy_out")
+        self._bind_stream()
+        _check(lib().gfc_gradient_threshold(self._h, gx.data_ptr(), gy.data_ptr(), float(frac), float(ref),
+                                            gx_out.data_ptr(), gy_out.data_ptr()))
+        return gx_out, gy_out
+
+    def gradient_merge(self, gx, gy, edges, alpha, gx_out=None, gy_out=None):
+        """Eq. 26: |Ep| = |E|^(1-alpha) C^alpha with the orientation of E kept."""
+        gx, gy = self._check_field(gx, "gx"), self._check_field(gy, "gy")
+        edges = self._check_field(edges, "edges")
+        gx_out = self._empty() if gx_out is None else self._check_field(gx_out, "gx_out")
+        gy_out = self._empty() if gy_out is None else self._check_field(gy_out, "gy_out")
+        self._bind_stream()
+        _check(lib().gfc_gradient_merge(self._h, gx.data_ptr(), gy.data_ptr(), edges.data_ptr(), float(alpha),
+                                        gx_out.data_ptr(), gy_out.data_ptr()))
+        return gx_out, gy_out
+
+    def boundary_offset(self, out, ring=3, inner=None):
+        """Sec. 2.3.2: subtract the ring's mean from a solved field and crop the ring."""
+        out = self._check_field(out, "out")
+        shape = (self.batch, self.C, self.H - 2 * ring, self.W - 2 * ring)
+        if inner is None:
+            inner = torch.empty(shape, dtype=self.dtype, device=self.device)
+        elif tuple(inner.shape) != shape or inner.dtype != self.dtype or not inner.is_contiguous() or \
+                inner.device != self.device:
+            raise ValueError(f"inner must be a contiguous {self.dtype} tensor of shape {shape} on {self.device}")
+        self._bind_stream()
+        _check(lib().gfc_boundary_offset(self._h, out.data_ptr(), int(ring), inner.data_ptr()))
+        return inner
 
     def set_profiling(self, enable: bool = True):
         _check(lib().gfc_plan_set_profiling(self._h, 1 if enable else 0))

@@ -32,6 +32,8 @@ __all__ = [
     "ragged_item_gradients",
     "feature_gradients",
     "upstream_gradient",
+    "edit_batch",
+    "ring_padded_batch",
 ]
 
 
@@ -229,3 +231,58 @@ def feature_gradients(batch=32, C=64, H=256, W=256, seed=4000, items=None):
 def upstream_gradient(shape, seed=4500):
     """Random upstream gradient N(0,1) float32 of the given shape."""
     return np.random.default_rng(seed).standard_normal(shape, dtype=np.float32)
+
+
+def edit_batch(batch=4, C=3, H=801, W=1200, seed=5000, items=None):
+    """Images, gradients and an edge map for the editing steps of Sec. 3.2.
+
+    Each channel: 64 Gaussians (sigma 5-80 px) plus U[0, 0.05] texture noise,
+    rescaled to [0, 1]; its forward-difference gradient; and an edge-intensity
+    map standing in for an edge detector's output (Sec. 3.2.4 uses SE or RCF):
+    the gradient magnitude of a 5x5 box-blurred copy, rescaled to [0, 1].
+    Returns float32 arrays ``(img, gx, gy, edges)`` of shape [n, C, H, W];
+    batch item ``b`` uses seed ``seed + b``.
+    """
+    idx = range(batch) if items is None else list(items)
+    img = np.empty((len(idx), C, H, W), dtype=np.float32)
+    gx, gy, edges = np.empty_like(img), np.empty_like(img), np.empty_like(img)
+    for n, b in enumerate(idx):
+        rng = np.random.default_rng(seed + b)
+        for c in range(C):
+            im = gaussian_image(rng, H, W, 64, 5.0, 80.0, noise=0.05)
+            fx, fy = forward_gradient(im)
+            bx, by = forward_gradient(_box5(im.astype(np.float32)).astype(np.float64))
+            e = np.sqrt(bx * bx + by * by)
+            img[n, c], gx[n, c], gy[n, c] = im, fx, fy
+            edges[n, c] = e / e.max() if e.max() > 0 else e
+    return img, gx, gy, edges
+
+
+def ring_padded_batch(batch=4, C=1, H=807, W=1206, ring=3, seed=6000, items=None):
+    """Images padded by a ring of zeros (Sec. 2.3.2) and their edited gradients.
+
+    The inner (H - 2 ring) x (W - 2 ring) block is a 64-Gaussian image in
+    [0, 1]; the ring is 0. Its forward-difference gradient then gets the
+    additive rectangles of ``perturbed_gradient_batch`` inside the inner block,
+    so the field is not conservative. Returns float32 ``(img, gx, gy)`` of
+    shape [n, C, H, W]; batch item ``b`` uses seed ``seed + b``.
+    """
+    idx = range(batch) if items is None else list(items)
+    img = np.zeros((len(idx), C, H, W), dtype=np.float32)
+    gx, gy = np.empty_like(img), np.empty_like(img)
+    Hi, Wi = H - 2 * ring, W - 2 * ring
+    for n, b in enumerate(idx):
+        rng = np.random.default_rng(seed + b)
+        for c in range(C):
+            im = np.zeros((H, W))
+            im[ring:H - ring, ring:W - ring] = gaussian_image(rng, Hi, Wi, 64, 5.0, 80.0)
+            fx, fy = forward_gradient(im)
+            for g in (fx, fy):
+                for _ in range(5):
+                    rh = int(rng.integers(max(1, Hi // 16), max(2, Hi // 4) + 1))
+                    rw = int(rng.integers(max(1, Wi // 16), max(2, Wi // 4) + 1))
+                    r0 = ring + int(rng.integers(0, Hi - rh + 1))
+                    c0 = ring + int(rng.integers(0, Wi - rw + 1))
+                    g[r0:r0 + rh, c0:c0 + rw] += rng.uniform(-0.2, 0.2)
+            img[n, c], gx[n, c], gy[n, c] = im, fx, fy
+    return img, gx, gy
