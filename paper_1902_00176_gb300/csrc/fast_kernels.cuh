@@ -504,13 +504,14 @@ __global__ void __launch_bounds__(S::THREADS, S::MINB) k_fast_cols(const float2*
   __syncthreads();
   if (act2) {
 #pragma unroll
-    for (int s2 = 0; s2 < S::R2; ++s2) mybuf[S::pad(t * S::R2 + s2)] = u[s2];
+    for (int s2 = 0; s2 < S::R2; ++s2) mybuf[t * (S::R2 + 1) + s2] = u[s2];  // pad(t R2 + s2), s2 < R2
   }
   __syncthreads();
   if (act) {
-    v[0] = mybuf[S::pad(t)];
+    // pad(t + R2 r) = t + (R2 + 1) r for t < R2
+    v[0] = mybuf[t];
 #pragma unroll
-    for (int r = 1; r < S::R1; ++r) v[r] = cmul(mybuf[S::pad(t + S::R2 * r)], cconj(twI[t * S::TWI_STRIDE + r]));
+    for (int r = 1; r < S::R1; ++r) v[r] = cmul(mybuf[t + (S::R2 + 1) * r], cconj(twI[t * S::TWI_STRIDE + r]));
     dft_reg<S::R1, +1>(v);
     // u[0,0] = sum over the row-0 spectrum, weight 1 at l = 0 and N/2, 2 elsewhere
     if (MODE != 2 && t == 0) colval[c] = (l == 0 || 2 * l == A.N) ? (double)v[0].x : 2.0 * (double)v[0].x;
@@ -527,9 +528,20 @@ __global__ void __launch_bounds__(S::THREADS, S::MINB) k_fast_cols(const float2*
     const int ncol = (A.Nh - blk * S::C) < S::C ? (A.Nh - blk * S::C) : S::C;
     const int yrows = (MODE == 2) ? A.H + 1 : A.H;
     float2* Yf = Y + (size_t)field * yrows * A.ldY + blk * S::C;
-    for (int idx = tid; idx < yrows * S::C; idx += blockDim.x) {
-      const int i = idx / S::C, cc = idx - i * S::C;
-      if (cc < ncol) Yf[(size_t)i * A.ldY + cc] = buf[(A.p + i) * S::OS + cc];
+    if constexpr (S::THREADS % S::C == 0) {
+      // every thread keeps one column and steps over rows
+      constexpr int RSTEP = S::THREADS / S::C;
+      const int cc = tid % S::C;
+      if (cc < ncol) {
+        const float2* src = buf + (A.p + tid / S::C) * S::OS + cc;
+        float2* dst = Yf + (size_t)(tid / S::C) * A.ldY + cc;
+        for (int i = tid / S::C; i < yrows; i += RSTEP, src += RSTEP * S::OS, dst += (size_t)RSTEP * A.ldY) *dst = *src;
+      }
+    } else {
+      for (int idx = tid; idx < yrows * S::C; idx += blockDim.x) {
+        const int i = idx / S::C, cc = idx - i * S::C;
+        if (cc < ncol) Yf[(size_t)i * A.ldY + cc] = buf[(A.p + i) * S::OS + cc];
+      }
     }
   }
   if (MODE != 2 && tid == 0) {
@@ -568,11 +580,15 @@ __global__ void __launch_bounds__(S::THREADS) k_fast_rows_inv(const float2* __re
 #pragma unroll 1
   for (int w = blockIdx.x; w < items; w += gridDim.x, parity ^= 1) {
     const int field = w / A.ngroups, g = w - field * A.ngroups;
-    if (tid == 0) {
+    if (tid < 32) {
+      // u[0,0] from the column blocks' FP64 partial sums: lane-strided, then a
+      // fixed shuffle tree (the same order on every call)
       const double* pp = reinterpret_cast<const double*>(partial) + (size_t)field * (kMaxRowBlocks / 2);
       double s2 = 0.0;
-      for (int i = 0; i < A.nparts; ++i) s2 += pp[i];
-      u00s[parity] = (float)s2;
+      for (int i = tid; i < A.nparts; i += 32) s2 += pp[i];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s2 += __shfl_down_sync(0xffffffffu, s2, o);
+      if (tid == 0) u00s[parity] = (float)s2;
     }
     const int ia = g * 2 * S::F + 2 * f, ib = ia + 1;
     const bool va = act && ia < A.H, vb = act && ib < A.H;
