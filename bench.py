@@ -417,7 +417,25 @@ def extra_workloads(dev):
                                        "fwd_bwd_solves_per_s": nfld * 1000.0 / (ms_f + ms_b)}
     p.close()
     res["edit_100x801x1200_fp32"] = _edit_workload(dev)
+    res["exact_809x1208_100x801x1200_fp32"] = _exact_workload(dev)
     return res
+
+
+def _exact_workload(dev):
+    """Algorithm A's exact padded size (809 x 1208, Bluestein transforms) on the
+    benchmark batch, against the SMOOTH size (810 x 1250)."""
+    import torch
+
+    from paper_1902_00176_gb300 import gfc
+
+    B, H, W = 100, 801, 1200
+    gx = torch.rand(B, 1, H, W, device=dev) - 0.5
+    gy = torch.rand(B, 1, H, W, device=dev) - 0.5
+    p = gfc.Plan(H, W, 1, B, device=dev, exact=True)
+    out = torch.empty_like(gx)
+    ms = _time_ms(lambda: p.solve_from_gradient(gx, gy, out), dev, 5)
+    p.close()
+    return {"padded": [H + 8, W + 8], "ms_per_batch": ms, "solves_per_s": B * 1000.0 / ms}
 
 
 def _edit_workload(dev):

@@ -61,7 +61,12 @@ typedef enum {
   GFC_ERR_TIMEOUT = 5      /* a bounded device-side wait ran out */
 } gfc_status;
 
-typedef enum { GFC_SIZE_SMOOTH = 0 } gfc_size_policy;
+/* GFC_SIZE_SMOOTH: M, N = smallest even 7-smooth sizes >= H + 2p, W + 2p (the
+ * register-resident transforms). GFC_SIZE_EXACT: Algorithm A's own size,
+ * M = H + 2p, N = W + 2p, whatever their prime factors (Bluestein's chirp-z
+ * for lengths that are not 7-smooth); H + 2p and W + 2p <= 2048, uniform plans,
+ * forward solves only (gfc_backward returns GFC_ERR_UNSUPPORTED). */
+typedef enum { GFC_SIZE_SMOOTH = 0, GFC_SIZE_EXACT = 1 } gfc_size_policy;
 
 typedef struct {
   int H, W;          /* image height and width, each >= 2 */

@@ -1,0 +1,368 @@
+// exact.cu -- solves on Algorithm A's exact padded size (size policy EXACT):
+// M = H + 2p, N = W + 2p, whatever their prime factors (801x1200 -> 809x1208,
+// where 809 is prime and 1208 = 8 x 151).
+//
+// The field is carried as a full complex M x N array (the real Laplacian in
+// the real part): row DFTs of length N, a tiled transpose, column DFTs of
+// length M with the Green multiply (Eq. 23) between the forward and the
+// inverse transform, a transpose back, inverse row DFTs, then Algorithm B's
+// offset and crop. A length that is 7-smooth runs the shared-memory Stockham
+// engine directly; any other length n runs Bluestein's chirp-z identity
+//     X[k] = w[k] sum_m (x[m] w[m]) conj(w[k - m]),   w[j] = exp(-i pi j^2 / n),
+// which follows from m k = (m^2 + k^2 - (k - m)^2) / 2: the sum is a linear
+// convolution, done as a circular one of a 7-smooth length L >= 2n - 1 with
+// the Stockham engine (forward, multiply by the precomputed transform of the
+// conjugate chirp with 1/L folded in, inverse). The inverse DFT is the
+// conjugate of the forward DFT of the conjugate. The chirp reduces j^2 modulo
+// 2n in integers; both Bluestein tables are computed in FP64 on the host at
+// plan creation and rounded once to FP32.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <math.h>
+
+#include <vector>
+
+#include "gfc_internal.h"
+
+namespace gfc {
+namespace {
+
+constexpr int kExactThreads = 256;
+
+template <typename T> __device__ __forceinline__ float ex_ld(const T* p);
+template <> __device__ __forceinline__ float ex_ld<float>(const float* p) { return __ldg(p); }
+template <> __device__ __forceinline__ float ex_ld<__half>(const __half* p) { return __half2float(__ldg(p)); }
+template <> __device__ __forceinline__ float ex_ld<__nv_bfloat16>(const __nv_bfloat16* p) {
+  return __bfloat162float(__ldg(p));
+}
+template <typename T> __device__ __forceinline__ T ex_st(float x);
+template <> __device__ __forceinline__ float ex_st<float>(float x) { return x; }
+template <> __device__ __forceinline__ __half ex_st<__half>(float x) { return __float2half_rn(x); }
+template <> __device__ __forceinline__ __nv_bfloat16 ex_st<__nv_bfloat16>(float x) { return __float2bfloat16_rn(x); }
+
+// ---- one DFT of length d.n on a shared-memory row ------------------------------------
+struct DimArgs {
+  int n, L;           // L = 0: n is 7-smooth (direct)
+  FftPlan plan;       // schedule of n (direct) or L (Bluestein)
+  const float2* tw;   // roots of unity of the scheduled length
+  const float2* chirp;
+  const float2* cf;
+};
+
+// DFT of the n values in b0 (DIR -1 forward, +1 unnormalised inverse); b0, b1
+// are shared buffers of max(n, L) complex. Callers synchronise before; the
+// result is visible to the whole block on return.
+template <int DIR>
+__device__ float2* dft_row(float2* b0, float2* b1, const DimArgs& d, int tid, int nthr) {
+  // input is in b0[0..n); returns the buffer holding the n outputs
+  if (d.L == 0) return fft_smem<DIR>(b0, b1, d.plan, 1, 1, d.tw, tid, nthr);
+  // Bluestein: a[m] = x[m] w[m] (conj of the input for the inverse), zero to L
+  for (int m = tid; m < d.L; m += nthr) {
+    float2 v = make_float2(0.0f, 0.0f);
+    if (m < d.n) {
+      float2 x = b0[m];
+      if (DIR > 0) x = cconj(x);
+      v = cmul(x, __ldg(d.chirp + m));
+    }
+    b1[m] = v;
+  }
+  __syncthreads();
+  float2* A = fft_smem<-1>(b1, b0, d.plan, 1, 1, d.tw, tid, nthr);
+  float2* B = (A == b0) ? b1 : b0;
+  for (int k = tid; k < d.L; k += nthr) A[k] = cmul(A[k], __ldg(d.cf + k));
+  __syncthreads();
+  float2* C = fft_smem<+1>(A, B, d.plan, 1, 1, d.tw, tid, nthr);
+  for (int k = tid; k < d.n; k += nthr) {
+    float2 y = cmul(C[k], __ldg(d.chirp + k));
+    if (DIR > 0) y = cconj(y);
+    C[k] = y;
+  }
+  __syncthreads();
+  return C;
+}
+
+// rows of X (count rows of d.n complex, row stride ld) transformed in place
+template <int DIR>
+__global__ void __launch_bounds__(kExactThreads) k_exact_rows(float2* X, long long rows, int ld, DimArgs d) {
+  extern __shared__ float2 sm[];
+  const int len = d.L > d.n ? d.L : d.n;
+  float2* b0 = sm;
+  float2* b1 = sm + len;
+  for (long long r = blockIdx.x; r < rows; r += gridDim.x) {
+    float2* x = X + r * ld;
+    for (int m = threadIdx.x; m < d.n; m += blockDim.x) b0[m] = x[m];
+    __syncthreads();
+    float2* y = dft_row<DIR>(b0, b1, d, threadIdx.x, blockDim.x);
+    for (int k = threadIdx.x; k < d.n; k += blockDim.x) x[k] = y[k];
+    __syncthreads();
+  }
+}
+
+// column l of a field (row l of the transposed array): forward DFT of length M,
+// times G[k][min(l, N - l)] (G real and even, 1/(MN) folded in), inverse DFT
+__global__ void __launch_bounds__(kExactThreads) k_exact_cols(float2* XT, int nf, int M, int N, int Nh,
+                                                              const float* __restrict__ G, DimArgs d) {
+  extern __shared__ float2 sm[];
+  const int len = d.L > d.n ? d.L : d.n;
+  float2* b0 = sm;
+  float2* b1 = sm + len;
+  const long long rows = (long long)nf * N;
+  for (long long r = blockIdx.x; r < rows; r += gridDim.x) {
+    const int l = (int)(r % N);
+    const int lg = l <= N - l ? l : N - l;
+    float2* x = XT + r * M;
+    for (int m = threadIdx.x; m < M; m += blockDim.x) b0[m] = x[m];
+    __syncthreads();
+    float2* y = dft_row<-1>(b0, b1, d, threadIdx.x, blockDim.x);
+    float2* z = (y == b0) ? b1 : b0;
+    for (int k = threadIdx.x; k < M; k += blockDim.x) z[k] = cscale(y[k], __ldg(G + (size_t)k * Nh + lg));
+    __syncthreads();
+    float2* u = dft_row<+1>(z, y, d, threadIdx.x, blockDim.x);
+    for (int k = threadIdx.x; k < M; k += blockDim.x) x[k] = u[k];
+    __syncthreads();
+  }
+}
+
+// [R][Cn] -> [Cn][R] per field, 32 x 32 tiles through shared memory
+__global__ void k_exact_transpose(const float2* __restrict__ src, float2* __restrict__ dst, int R, int Cn) {
+  __shared__ float2 tile[32][33];
+  const size_t fo = (size_t)blockIdx.z * R * Cn;
+  const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int r = r0 + i, c = c0 + threadIdx.x;
+    if (r < R && c < Cn) tile[i][threadIdx.x] = src[fo + (size_t)r * Cn + c];
+  }
+  __syncthreads();
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int c = c0 + i, r = r0 + threadIdx.x;
+    if (r < R && c < Cn) dst[fo + (size_t)c * R + r] = tile[threadIdx.x][i];
+  }
+}
+
+// X[f][r][c] = L on the M x N torus (real part), image block at (p, p);
+// MODE 0: L = div E (Eq. 3) of the (optionally edited) gradient, MODE 1: L given
+template <typename T, int MODE, int EDIT>
+__global__ void k_exact_load(const T* __restrict__ in0, const T* __restrict__ in1, float2* __restrict__ X, int H,
+                             int W, int M, int N, int p, EditArgs ed) {
+  const size_t fe = (size_t)H * W;
+  const int f = blockIdx.y;
+  const T* a = in0 + f * fe;
+  const T* b = (MODE == 0) ? in1 + f * fe : nullptr;
+  const T* e = (MODE == 0 && EDIT == kEditMerge) ? static_cast<const T*>(ed.edges) + f * fe : nullptr;
+  const float t2 = (MODE == 0 && EDIT == kEditThreshold) ? ed.t2[f] : 0.0f;
+  float2* x = X + (size_t)f * M * N;
+  const int nrows = (MODE == 0) ? H + 1 : H, ncols = (MODE == 0) ? W + 1 : W;
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < (long long)M * N;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(idx / N), c = (int)(idx - (long long)r * N);
+    const int i = r - p, j = c - p;
+    float v = 0.0f;
+    if (i >= 0 && i < nrows && j >= 0 && j < ncols) {
+      if (MODE == 0) {
+        const float2 c0 = edit_pixel<T, EDIT>(a, b, e, i, j, H, W, t2, ed.alpha);
+        v = (c0.x - edit_pixel<T, EDIT>(a, b, e, i, j - 1, H, W, t2, ed.alpha).x) +
+            (c0.y - edit_pixel<T, EDIT>(a, b, e, i - 1, j, H, W, t2, ed.alpha).y);
+      } else {
+        v = ex_ld(a + (size_t)i * W + j);
+      }
+    }
+    x[idx] = make_float2(v, 0.0f);
+  }
+}
+
+// out[i][j] = Re u[p + i][p + j] - Re u[0][0] (Algorithm B)
+template <typename T>
+__global__ void k_exact_out(const float2* __restrict__ X, T* __restrict__ out, int H, int W, int M, int N, int p) {
+  const int f = blockIdx.y;
+  const float2* x = X + (size_t)f * M * N;
+  const float u00 = x[0].x;
+  T* o = out + (size_t)f * H * W;
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < (long long)H * W;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(idx / W), j = (int)(idx - (long long)i * W);
+    o[idx] = ex_st<T>(x[(size_t)(p + i) * N + (p + j)].x - u00);
+  }
+}
+
+int smooth_at_least(int x) {
+  int n = x;
+  while (!is_7smooth(n)) ++n;
+  return n;
+}
+
+DimArgs dim_args(const ExactDim& d) {
+  DimArgs a;
+  a.n = d.n;
+  a.L = d.L;
+  a.plan = d.plan;
+  a.tw = d.tw;
+  a.chirp = d.chirp;
+  a.cf = d.cf;
+  return a;
+}
+
+size_t dim_smem(const ExactDim& d) { return 2 * (size_t)(d.L > d.n ? d.L : d.n) * sizeof(float2); }
+
+template <typename K>
+cudaError_t raise_smem(K kernel, size_t smem) {
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+// Bluestein tables in FP64 on the host, rounded once to FP32:
+//   chirp[j] = exp(-i pi (j^2 mod 2n) / n),                       j < n
+//   cf[k]    = (1/L) sum_j c[j] exp(-2 pi i (j k mod L) / L),     k < L
+// with c[j] = conj(chirp[|j|]) for |j| < n placed circularly (c[L - j] = c[j]).
+// The O(L n) sum uses a table of the L-th roots indexed by exact integer
+// reduction; plan creation only.
+static std::vector<float2> host_chirp(int n) {
+  std::vector<float2> w(n);
+  for (int j = 0; j < n; ++j) {
+    const long long q = ((long long)j * j) % (2LL * n);
+    const double a = M_PI * (double)q / (double)n;
+    w[j] = make_float2((float)cos(a), (float)-sin(a));
+  }
+  return w;
+}
+
+static std::vector<float2> host_bluestein(int n, int L) {
+  std::vector<double> rc(L), rs(L);
+  for (int r = 0; r < L; ++r) {
+    const double a = 2.0 * M_PI * (double)r / (double)L;
+    rc[r] = cos(a);
+    rs[r] = -sin(a);  // exp(-2 pi i r / L)
+  }
+  std::vector<double> re(L, 0.0), im(L, 0.0);
+  for (int j = -(n - 1); j <= n - 1; ++j) {
+    const long long aj = j < 0 ? -j : j;
+    const long long q = (aj * aj) % (2LL * n);
+    const double a = M_PI * (double)q / (double)n;
+    const double cr = cos(a), ci = sin(a);  // conj(chirp[|j|]) = exp(+i pi q / n)
+    const int jj = j < 0 ? j + L : j;
+    int idx = 0;
+    for (int k = 0; k < L; ++k) {
+      re[k] += cr * rc[idx] - ci * rs[idx];
+      im[k] += cr * rs[idx] + ci * rc[idx];
+      idx += jj;
+      if (idx >= L) idx -= L;
+    }
+  }
+  std::vector<float2> cf(L);
+  for (int k = 0; k < L; ++k) cf[k] = make_float2((float)(re[k] / L), (float)(im[k] / L));
+  return cf;
+}
+
+cudaError_t setup_dim(ExactDim* d, int n, cudaStream_t s) {
+  d->n = n;
+  d->L = is_7smooth(n) ? 0 : smooth_at_least(2 * n - 1);
+  const int len = d->L ? d->L : n;
+  if (!make_fft_plan(len, &d->plan)) return cudaErrorInvalidValue;
+  cudaError_t e = cudaMalloc(&d->tw, (size_t)len * sizeof(float2));
+  if (e == cudaSuccess) e = build_twiddles(d->tw, len, s);
+  if (e == cudaSuccess && d->L) {
+    const std::vector<float2> w = host_chirp(n), cf = host_bluestein(n, d->L);
+    e = cudaMalloc(&d->chirp, (size_t)n * sizeof(float2));
+    if (e == cudaSuccess) e = cudaMalloc(&d->cf, (size_t)d->L * sizeof(float2));
+    if (e == cudaSuccess) e = cudaMemcpy(d->chirp, w.data(), w.size() * sizeof(float2), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d->cf, cf.data(), cf.size() * sizeof(float2), cudaMemcpyHostToDevice);
+  }
+  return e;
+}
+
+template <typename T, int MODE>
+cudaError_t run_exact(gfc_plan* P, const Bufs& bf, const T* in0, const T* in1, T* out0, int nf, cudaStream_t st,
+                      const EditArgs* ed) {
+  const int M = P->M, N = P->N;
+  float2* X = bf.spec;
+  float2* XT = bf.spec + (size_t)nf * M * N;
+  const EditArgs none{kEditNone, 0.0f, nullptr, nullptr};
+  const EditArgs& E = ed ? *ed : none;
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const DimArgs dr = dim_args(P->ex_row), dc = dim_args(P->ex_col);
+  const size_t sr = dim_smem(P->ex_row), sc = dim_smem(P->ex_col);
+  cudaError_t e;
+  // divergence / Laplacian into the complex torus
+  {
+    const long long cells = (long long)M * N;
+    int gx = (int)((cells + kExactThreads - 1) / kExactThreads);
+    if (gx > 4 * sms) gx = 4 * sms;
+    const dim3 g(gx, nf);
+    if (MODE == 1)
+      k_exact_load<T, 1, kEditNone><<<g, kExactThreads, 0, st>>>(in0, in1, X, P->H, P->W, M, N, P->pad, E);
+    else if (E.kind == kEditThreshold)
+      k_exact_load<T, 0, kEditThreshold><<<g, kExactThreads, 0, st>>>(in0, in1, X, P->H, P->W, M, N, P->pad, E);
+    else if (E.kind == kEditMerge)
+      k_exact_load<T, 0, kEditMerge><<<g, kExactThreads, 0, st>>>(in0, in1, X, P->H, P->W, M, N, P->pad, E);
+    else
+      k_exact_load<T, 0, kEditNone><<<g, kExactThreads, 0, st>>>(in0, in1, X, P->H, P->W, M, N, P->pad, E);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  const long long rows = (long long)nf * M;
+  const int grow = (int)(rows < 8LL * sms ? rows : 8LL * sms);
+  if ((e = raise_smem(k_exact_rows<-1>, sr)) != cudaSuccess) return e;
+  if ((e = raise_smem(k_exact_rows<+1>, sr)) != cudaSuccess) return e;
+  if ((e = raise_smem(k_exact_cols, sc)) != cudaSuccess) return e;
+  prof_begin(P, 0, st);
+  k_exact_rows<-1><<<grow, kExactThreads, sr, st>>>(X, rows, N, dr);
+  prof_end(P, st);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  const dim3 tb(32, 8);
+  k_exact_transpose<<<dim3((N + 31) / 32, (M + 31) / 32, nf), tb, 0, st>>>(X, XT, M, N);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  const long long cols = (long long)nf * N;
+  prof_begin(P, 1, st);
+  k_exact_cols<<<(int)(cols < 8LL * sms ? cols : 8LL * sms), kExactThreads, sc, st>>>(XT, nf, M, N, P->Nh, P->G, dc);
+  prof_end(P, st);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  k_exact_transpose<<<dim3((M + 31) / 32, (N + 31) / 32, nf), tb, 0, st>>>(XT, X, N, M);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  prof_begin(P, 2, st);
+  k_exact_rows<+1><<<grow, kExactThreads, sr, st>>>(X, rows, N, dr);
+  prof_end(P, st);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  {
+    const long long cells = (long long)P->H * P->W;
+    int gx = (int)((cells + kExactThreads - 1) / kExactThreads);
+    if (gx > 4 * sms) gx = 4 * sms;
+    k_exact_out<T><<<dim3(gx, nf), kExactThreads, 0, st>>>(X, out0, P->H, P->W, M, N, P->pad);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t exact_setup(gfc_plan* P, cudaStream_t s) {
+  cudaError_t e = setup_dim(&P->ex_row, P->N, s);
+  if (e == cudaSuccess) e = setup_dim(&P->ex_col, P->M, s);
+  return e;
+}
+
+void exact_release(gfc_plan* P) {
+  for (ExactDim* d : {&P->ex_row, &P->ex_col}) {
+    cudaFree(d->tw);
+    cudaFree(d->chirp);
+    cudaFree(d->cf);
+    d->tw = d->chirp = d->cf = nullptr;
+  }
+}
+
+cudaError_t run_chunk_exact(gfc_plan* P, const Bufs& bf, int mode, const void* in0, const void* in1, void* out0,
+                            int nf, cudaStream_t st, const EditArgs* ed) {
+  if (mode != 0 && mode != 1) return cudaErrorNotSupported;
+  auto go = [&](auto tag) -> cudaError_t {
+    using T = decltype(tag);
+    const T* a = static_cast<const T*>(in0);
+    const T* b = static_cast<const T*>(in1);
+    T* o = static_cast<T*>(out0);
+    return mode == 0 ? run_exact<T, 0>(P, bf, a, b, o, nf, st, ed) : run_exact<T, 1>(P, bf, a, b, o, nf, st, ed);
+  };
+  switch (P->dtype) {
+    case GFC_F32: return go(float{});
+    case GFC_F16: return go(__half{});
+    default: return go(__nv_bfloat16{});
+  }
+}
+
+}  // namespace gfc

@@ -18,6 +18,16 @@ struct Bufs {
 };
 constexpr int kMaxSlots = 4;
 
+// One transform length of an EXACT-size plan (exact.cu).
+struct ExactDim {
+  int n;          // transform length
+  int L;          // Bluestein convolution length (7-smooth, >= 2n - 1); 0 when n itself is 7-smooth
+  FftPlan plan;   // schedule of n (direct) or of L (Bluestein)
+  float2* tw;     // roots of unity of the scheduled length
+  float2* chirp;  // [n] exp(-i pi j^2 / n)            (Bluestein only)
+  float2* cf;     // [L] DFT of the conjugate chirp / L (Bluestein only)
+};
+
 // One field (item, channel) of a ragged batch, as the generic passes read it.
 struct FieldDesc {
   long long in_off;    // element offset of the field in the caller's arrays
@@ -39,6 +49,8 @@ struct gfc_plan {
   int ldS;    // row stride of the row-major spectrum scratch (generic passes), complex elements
   int ldM;    // column stride of the column-major spectrum scratch (fast passes)
   bool fast;  // both transform lengths have register-resident schedules
+  bool exact; // size policy EXACT: M = H + 2p, N = W + 2p (exact.cu)
+  gfc::ExactDim ex_row, ex_col;  // EXACT: the length-N and length-M transforms
   int chunk;  // fields per pipeline chunk
   int device;
   cudaStream_t stream;
@@ -122,6 +134,14 @@ inline size_t dtype_size(gfc_dtype d) { return d == GFC_F32 ? 4 : 2; }
 // tracing around one kernel launch on the plan's stream
 void prof_begin(gfc_plan* P, int pass, cudaStream_t st);
 void prof_end(gfc_plan* P, cudaStream_t st);
+// EXACT-size plans (exact.cu): tables, teardown, one chunk (mode 0 gradient,
+// 1 Laplacian; `ed` as for run_chunk_fast). The chunk scratch holds 2 M N
+// complex per field.
+cudaError_t exact_setup(gfc_plan* P, cudaStream_t s);
+void exact_release(gfc_plan* P);
+cudaError_t run_chunk_exact(gfc_plan* P, const Bufs& B, int mode, const void* in0, const void* in1, void* out0,
+                            int nf, cudaStream_t st, const EditArgs* ed);
+
 // per-field squared thresholds of Sec. 3.2.3 into P->edit_t2 (edit.cu): from
 // the fields' largest gradient magnitudes when ref <= 0, else from ref
 gfc_status edit_prepare_threshold(gfc_plan* P, const void* gx, const void* gy, float frac, float ref);

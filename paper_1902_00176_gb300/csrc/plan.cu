@@ -152,6 +152,15 @@ gfc_status gfc_padded_size(int H, int W, int pad, int size_policy, int* M, int* 
   if (!M || !N) return fail(GFC_ERR_INVALID_ARG, "gfc_padded_size: null output pointer");
   if (H < 2 || W < 2) return fail(GFC_ERR_INVALID_ARG, "gfc_padded_size: H=%d W=%d (need >= 2)", H, W);
   if (pad <= 0) pad = 4;
+  if (size_policy == GFC_SIZE_EXACT) {
+    // Algorithm A's size; Bluestein's convolution length stays <= kMaxFftLen
+    if ((long)H + 2L * pad > kMaxFftLen / 2 || (long)W + 2L * pad > kMaxFftLen / 2)
+      return fail(GFC_ERR_UNSUPPORTED, "gfc_padded_size: exact size %ldx%ld exceeds %d", (long)H + 2L * pad,
+                  (long)W + 2L * pad, kMaxFftLen / 2);
+    *M = H + 2 * pad;
+    *N = W + 2 * pad;
+    return GFC_OK;
+  }
   if (size_policy != GFC_SIZE_SMOOTH)
     return fail(GFC_ERR_INVALID_ARG, "gfc_padded_size: unknown size policy %d", size_policy);
   if ((long)H + 2L * pad > kMaxFftLen || (long)W + 2L * pad > kMaxFftLen)
@@ -183,9 +192,10 @@ gfc_status gfc_plan_create_ex(gfc_plan** out, const gfc_plan_opts* o) {
   if (!p) return fail(GFC_ERR_ALLOC, "gfc_plan_create: host allocation failed");
   p->H = o->H; p->W = o->W; p->C = o->C; p->batch = o->batch; p->pad = pad; p->dtype = o->dtype;
   p->M = M; p->N = N; p->Nh = N / 2 + 1; p->ldS = (p->Nh + 3) & ~3; p->ldM = (M + 3) & ~3;
-  p->fast = fast_supported(M, N) && pad == 4 && getenv("GFC_FORCE_GENERIC") == nullptr;
+  p->exact = o->size_policy == GFC_SIZE_EXACT;
+  p->fast = !p->exact && fast_supported(M, N) && pad == 4 && getenv("GFC_FORCE_GENERIC") == nullptr;
   p->stream = (cudaStream_t)o->stream;
-  if (!make_fft_plan(N, &p->rowplan) || !make_fft_plan(M, &p->colplan)) {
+  if (!p->exact && (!make_fft_plan(N, &p->rowplan) || !make_fft_plan(M, &p->colplan))) {
     free(p);
     return fail(GFC_ERR_UNSUPPORTED, "gfc_plan_create: no FFT schedule for %dx%d", M, N);
   }
@@ -196,6 +206,7 @@ gfc_status gfc_plan_create_ex(gfc_plan** out, const gfc_plan_opts* o) {
   const long fields = (long)o->batch * o->C;
   const size_t per_row_major = (size_t)M * p->ldS, per_col_major = (size_t)p->Nh * p->ldM;
   p->spec_field = per_row_major > per_col_major ? per_row_major : per_col_major;
+  if (p->exact) p->spec_field = 2 * (size_t)M * N;  // the complex torus and its transpose
   p->zbuf_field = p->fast ? fast_zbuf_elems(o->H, M, N) : 0;
   const size_t per_field = p->spec_field * sizeof(float2);
   const size_t ws = per_field + p->zbuf_field * sizeof(float2);
@@ -212,6 +223,7 @@ gfc_status gfc_plan_create_ex(gfc_plan** out, const gfc_plan_opts* o) {
     if (chunk < 1) chunk = 1;
   }
   if (chunk > fields) chunk = fields;
+  if (p->exact && chunk > 65535) chunk = 65535;  // fields are a grid dimension there
   const long nchunks = (fields + chunk - 1) / chunk;
   if (nslots > nchunks) nslots = (int)nchunks;
   p->chunk = (int)chunk;
@@ -239,6 +251,7 @@ gfc_status gfc_plan_create_ex(gfc_plan** out, const gfc_plan_opts* o) {
   if (e == cudaSuccess) e = build_twiddles(p->twM, M, bs);
   if (e == cudaSuccess) e = build_green(p->G, M, N, p->Nh, bs);
   if (e == cudaSuccess && p->fast) e = build_green_t(p->GT, M, N, p->Nh, p->ldM, bs);
+  if (e == cudaSuccess && p->exact) e = exact_setup(p, bs);
   if (e == cudaSuccess) e = cudaStreamSynchronize(bs);
   if (bs) cudaStreamDestroy(bs);
   if (e != cudaSuccess) {
@@ -439,6 +452,7 @@ static void destroy_plan(gfc_plan* p) {
   cudaFree(p->spec);
   cudaFree(p->partial);
   cudaFree(p->edit_t2);
+  exact_release(p);
   for (int sl = 0; sl < kMaxSlots; ++sl) {
     if (p->slot_stream[sl]) cudaStreamDestroy(p->slot_stream[sl]);
     if (p->slot_done[sl]) cudaEventDestroy(p->slot_done[sl]);

@@ -128,10 +128,10 @@ def _check(status: int):
         raise GFCError(status, lib().gfc_last_error().decode(errors="replace"))
 
 
-def padded_size(H: int, W: int, pad: int = 4):
+def padded_size(H: int, W: int, pad: int = 4, exact: bool = False):
     """(M, N) of the padded torus for an H x W image (host-only, no GPU needed)."""
     M, N = ctypes.c_int(), ctypes.c_int()
-    _check(lib().gfc_padded_size(H, W, pad, 0, ctypes.byref(M), ctypes.byref(N)))
+    _check(lib().gfc_padded_size(H, W, pad, 1 if exact else 0, ctypes.byref(M), ctypes.byref(N)))
     return M.value, N.value
 
 
@@ -153,13 +153,15 @@ class Plan:
     """A GFC plan: Green spectrum, transform tables and scratch for one problem shape."""
 
     def __init__(self, H: int, W: int, C: int = 1, batch: int = 1, dtype=torch.float32, pad: int = 4,
-                 chunk: int = 0, device=None, streams: int = 0):
+                 chunk: int = 0, device=None, streams: int = 0, exact: bool = False):
+        """``exact=True`` solves on Algorithm A's own padded size (H + 2p) x (W + 2p)
+        instead of the next even 7-smooth size."""
         if dtype not in _DTYPES:
             raise ValueError(f"unsupported dtype {dtype}")
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else
                                    torch.device(device).index or 0)
         self.H, self.W, self.C, self.batch, self.dtype = H, W, C, batch, dtype
-        o = _Opts(H, W, C, batch, _DTYPES[dtype], pad, 0, chunk, None, streams)
+        o = _Opts(H, W, C, batch, _DTYPES[dtype], pad, 1 if exact else 0, chunk, None, streams)
         h = ctypes.c_void_p()
         with torch.cuda.device(self.device):
             _check(lib().gfc_plan_create_ex(ctypes.byref(h), ctypes.byref(o)))

@@ -92,3 +92,12 @@ def test_plan_create_without_gpu_reports_cuda_error(gfc_lib):
     st = gfc_lib.gfc_plan_create(ctypes.byref(h), 64, 96, 1, 1, 0)
     assert st in (3, 4)
     assert gfc_lib.gfc_last_error() != b""
+
+
+def test_exact_size_policy(gfc_lib):
+    # Algorithm A's own size: image plus the pad on both sides, any factors
+    assert gfc.padded_size(801, 1200, exact=True) == (809, 1208)
+    assert gfc.padded_size(23, 29, exact=True) == (31, 37)
+    assert gfc.padded_size(10, 17, pad=2, exact=True) == (14, 21)
+    with pytest.raises(gfc.GFCError):
+        gfc.padded_size(2041, 10, exact=True)  # Bluestein length would exceed the engine's 4096

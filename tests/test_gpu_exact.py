@@ -1,0 +1,112 @@
+"""EXACT size policy (Algorithm A's own padded size, M = H + 2p, N = W + 2p):
+parity of the Bluestein/Stockham path with the oracle run on the same torus.
+
+The tolerance is the solver's: relative L2 <= 1e-5 in FP32 on image-like
+inputs, 2e-3 for 16-bit storage against the oracle on the dequantised inputs.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle.gfc_oracle as O
+from paper_1902_00176_gb300 import gfc, synth
+
+pytestmark = pytest.mark.gpu
+
+DEV = torch.device("cuda:0")
+REL_F32, REL_16 = 1e-5, 2e-3
+
+
+@pytest.fixture(autouse=True)
+def _lib(gfc_lib):
+    yield
+
+
+def _rel(got, ref):
+    return float(np.linalg.norm(got - ref) / max(np.linalg.norm(ref), 1e-300))
+
+
+def _dev(a, dtype=torch.float32):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(DEV).to(dtype)
+
+
+def _np(t):
+    return t.double().cpu().numpy()
+
+
+# (H, W): 72x104 (N = 8 x 13 runs Bluestein), 31x37 (both prime), 18x25 (odd,
+# 7-smooth: direct), 809x1208 (the paper's 801x1200 image: 809 prime, 1208 = 8 x 151)
+@pytest.mark.parametrize("H,W,B", [(64, 96, 2), (23, 29, 3), (10, 17, 2), (801, 1200, 1)])
+def test_exact_solve_matches_oracle(H, W, B):
+    gx, gy = synth.perturbed_gradient_batch(B, H, W, seed=7000)
+    p = gfc.Plan(H, W, 1, B, device=DEV, exact=True)
+    assert (p.M, p.N) == (H + 8, W + 8)
+    out = _np(p.solve_from_gradient(_dev(gx), _dev(gy)))
+    for b in range(B):
+        ref = O.solve_from_gradient(gx[b, 0].astype(np.float64), gy[b, 0].astype(np.float64), p.M, p.N, p.pad)
+        err = _rel(out[b, 0], ref)
+        assert err <= REL_F32, (b, err)
+    p.close()
+
+
+def test_exact_recovers_conservative_image():
+    rng = np.random.default_rng(7100)
+    img, c = synth.constant_border_image(rng, 41, 53)
+    gx, gy = synth.forward_gradient(img)
+    p = gfc.Plan(41, 53, device=DEV, exact=True)  # 49 x 61: 7^2 direct, 61 prime
+    out = _np(p.solve_from_gradient(_dev(gx[None, None]), _dev(gy[None, None])))[0, 0]
+    np.testing.assert_allclose(out, img - c, atol=1e-5)
+    p.close()
+
+
+def test_exact_laplacian_and_bf16():
+    gx, gy = synth.perturbed_gradient_batch(2, 30, 44, seed=7200)
+    lap = gx + gy  # any field serves as a Laplacian
+    p = gfc.Plan(30, 44, 1, 2, device=DEV, exact=True)
+    out = _np(p.solve_from_laplacian(_dev(lap)))
+    for b in range(2):
+        ref = O.solve_from_laplacian(lap[b, 0].astype(np.float64), p.M, p.N, p.pad)
+        assert _rel(out[b, 0], ref) <= REL_F32
+    p.close()
+    q = gfc.Plan(30, 44, 1, 2, dtype=torch.bfloat16, device=DEV, exact=True)
+    dx, dy = _dev(gx, torch.bfloat16), _dev(gy, torch.bfloat16)
+    out = _np(q.solve_from_gradient(dx, dy))
+    xq, yq = _np(dx), _np(dy)
+    for b in range(2):
+        ref = O.solve_from_gradient(xq[b, 0], yq[b, 0], q.M, q.N, q.pad)
+        assert _rel(out[b, 0], ref) <= REL_16
+    q.close()
+
+
+def test_exact_edited_solve_matches_two_step():
+    img, gx, gy, edges = synth.edit_batch(2, 1, 45, 70, seed=7300)
+    p = gfc.Plan(45, 70, 1, 2, device=DEV, exact=True)
+    dx, dy, de = _dev(gx), _dev(gy), _dev(edges)
+    tx, ty = p.gradient_threshold(dx, dy, 0.2)
+    assert torch.equal(p.solve_edited(dx, dy, "threshold", frac=0.2), p.solve_from_gradient(tx, ty))
+    mx, my = p.gradient_merge(dx, dy, de, 0.5)
+    assert torch.equal(p.solve_edited(dx, dy, "merge", alpha=0.5, edges=de), p.solve_from_gradient(mx, my))
+    p.close()
+
+
+def test_exact_against_smooth_sizes():
+    """EXACT and SMOOTH solve the same least-squares problem on tori a few pixels
+    apart; the gap is reported, not gated (both are checked against the oracle)."""
+    gx, gy = synth.perturbed_gradient_batch(1, 801, 1200, seed=7400)
+    pe = gfc.Plan(801, 1200, device=DEV, exact=True)
+    ps = gfc.Plan(801, 1200, device=DEV)
+    oe = _np(pe.solve_from_gradient(_dev(gx), _dev(gy)))
+    os_ = _np(ps.solve_from_gradient(_dev(gx), _dev(gy)))
+    gap = _rel(oe - oe.mean(), os_ - os_.mean())
+    print(f"EXACT {pe.M}x{pe.N} vs SMOOTH {ps.M}x{ps.N}: relative L2 gap {gap:.3e}")
+    assert np.isfinite(gap)
+    pe.close()
+    ps.close()
+
+
+def test_exact_rejects_backward():
+    p = gfc.Plan(20, 30, device=DEV, exact=True)
+    g = torch.zeros((1, 1, 20, 30), device=DEV)
+    with pytest.raises(gfc.GFCError):
+        p.backward(g)
+    p.close()
