@@ -33,6 +33,7 @@
 
 #include "fft_reg.cuh"
 #include "gfc_internal.h"
+#include "tma.cuh"
 
 namespace gfc {
 
@@ -61,6 +62,7 @@ struct FastArgs {
   int nparts;        // pass B column blocks per field (u[0,0] partial sums)
   int nf;            // fields in this chunk
   int ldY;           // row stride of the row-major spectrum Y (complex elements)
+  int* err;          // the plan's device error word (bounded waits that run out)
 };
 
 __device__ __forceinline__ float f_to_f(float x) { return x; }
@@ -324,15 +326,21 @@ __global__ void __launch_bounds__(512) k_fast_div_edit(const T* __restrict__ gx,
 
 // ---------------------------------------------------------------------------
 // pass A: forward row transforms of the packed rows + two-for-one split +
-// transposed store. Persistent over (field, group of F row pairs).
+// transposed store. Persistent over (field, group of F row pairs). The F packed
+// rows of an item are one contiguous bulk copy into the exchange buffer,
+// completed on an mbarrier; the copy for the next item is issued as soon as
+// this item's stage-2 inputs are read, so it overlaps the stage-2 transforms
+// and the transposed store of the spectrum.
 // ---------------------------------------------------------------------------
 template <class S>
-__global__ void __launch_bounds__(S::THREADS) k_fast_rows_fwd(const float2* __restrict__ z, float2* __restrict__ spec,
-                                                              const float2* __restrict__ twg, FastArgs A) {
-  extern __shared__ float2 sm[];
+__global__ void __launch_bounds__(S::THREADS, 2) k_fast_rows_fwd(const float2* __restrict__ z,
+                                                                 float2* __restrict__ spec,
+                                                                 const float2* __restrict__ twg, FastArgs A) {
+  extern __shared__ __align__(16) float2 sm[];
   float2* tw2 = sm;                   // [R1][R2]: w_N^(r j)
-  float2* buf = sm + S::R1 * S::R2;   // [F][NP] exchange, index m -> m + m / R1
+  float2* buf = sm + S::R1 * S::R2;   // staged packed rows [F][ldz], then the exchange (m -> m + m / R1)
   float2* buf2 = buf + S::F * S::NP;  // [F][NO] stage-2 output, natural order
+  __shared__ __align__(8) uint64_t bar;
   const int tid = threadIdx.x;
   const int f = tid / S::T, t = tid - f * S::T;
   const bool act = f < S::F;
@@ -346,24 +354,31 @@ __global__ void __launch_bounds__(S::THREADS) k_fast_rows_fwd(const float2* __re
   const int uf = tid % S::F, uk0 = tid / S::F;
   const bool uact = tid < S::F * S::T;
   const int items = A.nf * A.ngroups;
-  // the packed-row inputs of the next item are loaded while this one is transformed
-  auto load_item = [&](int w, float2 (&dst)[S::R1]) {
-    // packed rows are zero padded to the full transform length: no range checks
+  auto issue = [&](int w) {  // one thread: stage the packed rows of item w (zero padded, whole rows)
     const int field = w / A.ngroups, g = w - field * A.ngroups;
-    const bool live = act && w < items;
-    const float2* zrow = z + ((size_t)(live ? field : 0) * A.zpairs + (live ? g * S::F + f : 0)) * A.ldz + t;
-#pragma unroll
-    for (int r = 0; r < S::R1; ++r) dst[r] = zrow[S::R2 * r];
+    bulk_load(buf, z + ((size_t)field * A.zpairs + (size_t)g * S::F) * A.ldz,
+              (unsigned)(S::F * A.ldz * sizeof(float2)), &bar);
   };
-  float2 nxt[S::R1];
-  load_item(blockIdx.x, nxt);
+  if (tid == 0) mbar_init(&bar, 1);
+  __syncthreads();
+  if (tid == 0 && (int)blockIdx.x < items) issue(blockIdx.x);
+  unsigned phase = 0;
 #pragma unroll 1
-  for (int w = blockIdx.x; w < items; w += gridDim.x) {
+  for (int w = blockIdx.x; w < items; w += gridDim.x, phase ^= 1u) {
     const int field = w / A.ngroups, g = w - field * A.ngroups;
+    const bool landed = mbar_wait(&bar, phase);
+    if (__syncthreads_or(!landed)) {  // the copy never completed: report, let it drain, stop
+      if (tid == 0) atomicExch(A.err, kErrBulkWait);
+      mbar_wait(&bar, phase);
+      return;
+    }
     float2 v[S::R1];
+    if (act) {
+      const float2* zr = buf + (size_t)f * A.ldz + t;
 #pragma unroll
-    for (int r = 0; r < S::R1; ++r) v[r] = nxt[r];
-    load_item(w + gridDim.x, nxt);
+      for (int r = 0; r < S::R1; ++r) v[r] = zr[S::R2 * r];
+    }
+    __syncthreads();  // every staged row read: buf becomes the exchange buffer
     if (act) {
       dft_reg<S::R1, -1>(v);
       // Stockham stage 1 writes t R1 + s; its padded index is t (R1 + 1) + s
@@ -371,20 +386,28 @@ __global__ void __launch_bounds__(S::THREADS) k_fast_rows_fwd(const float2* __re
       for (int s2 = 0; s2 < S::R1; ++s2) mybuf[t * (S::R1 + 1) + s2] = v[s2];
     }
     __syncthreads();  // stage-1 results visible; previous unpack done with buf2
-    if (act && t < S::JSPAN) {
+    const bool act2 = act && t < S::JSPAN;
 #pragma unroll
-      for (int jj = 0; jj < S::J2; ++jj) {
-        const int j = t + S::R2 * jj;  // j < R1, so the padded index of j + R1 r is j + (R1 + 1) r
-        float2 u[S::R2];
+    for (int jj = 0; jj < S::J2; ++jj) {
+      const int j = t + S::R2 * jj;  // j < R1, so the padded index of j + R1 r is j + (R1 + 1) r
+      float2 u[S::R2];
+      if (act2) {
         u[0] = mybuf[j];
 #pragma unroll
         for (int r = 1; r < S::R2; ++r) u[r] = cmul(mybuf[j + (S::R1 + 1) * r], tw2[j * S::R2 + r]);
+      }
+      if (jj == S::J2 - 1) {
+        fence_proxy_async_smem();  // this thread's accesses of buf precede the next bulk copy into it
+        __syncthreads();           // buf free
+        if (tid == 0 && w + (int)gridDim.x < items) issue(w + gridDim.x);
+      }
+      if (act2) {
         dft_reg<S::R2, -1>(u);
 #pragma unroll
         for (int s2 = 0; s2 < S::R2; ++s2) mybuf2[j + S::R1 * s2] = u[s2];
       }
     }
-    __syncthreads();  // stage-2 results visible; buf free for the next item
+    __syncthreads();  // stage-2 results visible
     if (g == 0) {
       // rows of every column outside the support [p, p + nrows) are zero, so the
       // column pass loads whole columns without range checks
@@ -554,18 +577,23 @@ __global__ void __launch_bounds__(S::THREADS, S::MINB) k_fast_cols(const float2*
 }
 
 // ---------------------------------------------------------------------------
-// pass C: Hermitian extension loaded straight from the column-major spectrum,
-// inverse row transforms, offset, crop and cast. Persistent over (field,
-// group of F output row pairs).
+// pass C: inverse row transforms of the row-major spectrum Y with the
+// Hermitian extension formed on load, offset, crop and cast. Persistent over
+// (field, group of F output row pairs). The 2F rows of Y an item needs are one
+// contiguous bulk copy into the exchange buffer, completed on an mbarrier; the
+// copy for the next item is issued as soon as this item's stage-2 inputs are
+// in registers, so it overlaps the stage-2 transforms and the output stores.
 // ---------------------------------------------------------------------------
 template <class S, typename T>
-__global__ void __launch_bounds__(S::THREADS) k_fast_rows_inv(const float2* __restrict__ Y,
+__global__ void __launch_bounds__(S::THREADS, 3) k_fast_rows_inv(const float2* __restrict__ Y,
                                                               const float* __restrict__ partial, T* __restrict__ out,
                                                               const float2* __restrict__ twg, FastArgs A) {
-  extern __shared__ float2 sm[];
+  extern __shared__ __align__(16) float2 sm[];
   float2* tw2 = sm;
-  float2* buf = sm + S::R1 * S::R2;
+  float2* buf = sm + S::R1 * S::R2;  // staged rows of Y [2F][ldY], then the stage-1 exchange
   __shared__ float u00s[2];
+  __shared__ __align__(8) uint64_t bar;
+  constexpr int RW = 2 * S::F;       // rows of Y per item
   const int tid = threadIdx.x;
   const int f = tid / S::T, t = tid - f * S::T;
   const bool act = f < S::F;
@@ -576,9 +604,18 @@ __global__ void __launch_bounds__(S::THREADS) k_fast_rows_inv(const float2* __re
   float2* mybuf = buf + (act ? f : 0) * S::NP;
   const int half = S::N / 2;
   const int items = A.nf * A.ngroups;
+  auto issue = [&](int w) {  // one thread: stage the rows of item w
+    const int field = w / A.ngroups, g = w - field * A.ngroups;
+    const int r0 = g * RW, nr = (A.H - r0) < RW ? (A.H - r0) : RW;
+    bulk_load(buf, Y + ((size_t)field * A.H + r0) * A.ldY, (unsigned)(nr * A.ldY * sizeof(float2)), &bar);
+  };
+  if (tid == 0) mbar_init(&bar, 1);
+  __syncthreads();
+  if (tid == 0 && (int)blockIdx.x < items) issue(blockIdx.x);
   int parity = 0;
+  unsigned phase = 0;
 #pragma unroll 1
-  for (int w = blockIdx.x; w < items; w += gridDim.x, parity ^= 1) {
+  for (int w = blockIdx.x; w < items; w += gridDim.x, parity ^= 1, phase ^= 1u) {
     const int field = w / A.ngroups, g = w - field * A.ngroups;
     if (tid < 32) {
       // u[0,0] from the column blocks' FP64 partial sums: lane-strided, then a
@@ -590,10 +627,16 @@ __global__ void __launch_bounds__(S::THREADS) k_fast_rows_inv(const float2* __re
       for (int o = 16; o > 0; o >>= 1) s2 += __shfl_down_sync(0xffffffffu, s2, o);
       if (tid == 0) u00s[parity] = (float)s2;
     }
+    const bool landed = mbar_wait(&bar, phase);
+    if (__syncthreads_or(!landed)) {  // the copy never completed: report, let it drain, stop
+      if (tid == 0) atomicExch(A.err, kErrBulkWait);
+      mbar_wait(&bar, phase);
+      return;
+    }
     const int ia = g * 2 * S::F + 2 * f, ib = ia + 1;
     const bool va = act && ia < A.H, vb = act && ib < A.H;
-    const float2* ya_row = Y + ((size_t)field * A.H + (va ? ia : 0)) * A.ldY;
-    const float2* yb_row = Y + ((size_t)field * A.H + (vb ? ib : 0)) * A.ldY;
+    const float2* ya_row = buf + (size_t)(va ? 2 * f : 0) * A.ldY;
+    const float2* yb_row = buf + (size_t)(vb ? 2 * f + 1 : 0) * A.ldY;
     float2 v[S::R1];
 #pragma unroll
     for (int r = 0; r < S::R1; ++r) {
@@ -613,23 +656,32 @@ __global__ void __launch_bounds__(S::THREADS) k_fast_rows_inv(const float2* __re
         yb.y = 0.0f;
       }
       v[r] = lo ? make_float2(ya.x - yb.y, ya.y + yb.x) : make_float2(ya.x + yb.y, yb.x - ya.y);
-    }    if (act) dft_reg<S::R1, +1>(v);
-    __syncthreads();  // previous item's stage 2 done with buf; u00 published
+    }
+    if (act) dft_reg<S::R1, +1>(v);
+    __syncthreads();  // every staged row read: buf becomes the exchange buffer
     if (act) {
 #pragma unroll
       for (int s2 = 0; s2 < S::R1; ++s2) mybuf[t * (S::R1 + 1) + s2] = v[s2];
     }
     __syncthreads();
-    if (act && t < S::JSPAN) {
-      const float u00 = u00s[parity];
-      T* o = out + (size_t)field * A.H * A.W;
+    const bool act2 = act && t < S::JSPAN;
+    const float u00 = u00s[parity];
+    T* o = out + (size_t)field * A.H * A.W;
 #pragma unroll
-      for (int jj = 0; jj < S::J2; ++jj) {
-        const int j = t + S::R2 * jj;
-        float2 u[S::R2];
+    for (int jj = 0; jj < S::J2; ++jj) {
+      const int j = t + S::R2 * jj;
+      float2 u[S::R2];
+      if (act2) {
         u[0] = mybuf[j];
 #pragma unroll
         for (int r = 1; r < S::R2; ++r) u[r] = cmul(mybuf[j + (S::R1 + 1) * r], cconj(tw2[j * S::R2 + r]));
+      }
+      if (jj == S::J2 - 1) {
+        fence_proxy_async_smem();  // this thread's accesses of buf precede the next bulk copy into it
+        __syncthreads();           // buf free
+        if (tid == 0 && w + (int)gridDim.x < items) issue(w + gridDim.x);
+      }
+      if (act2) {
         dft_reg<S::R2, +1>(u);
 #pragma unroll
         for (int s2 = 0; s2 < S::R2; ++s2) {
@@ -781,6 +833,9 @@ static cudaError_t run_fast_mode(gfc_plan* P, const Bufs& bf, const T* in0, cons
   A.nparts = (P->Nh + CS::C - 1) / CS::C;
   A.nf = nf;
   A.ldY = (P->Nh + 3) & ~3;
+  A.err = P->dev_err;
+  // the row passes stage their F packed rows / 2F rows of Y in the exchange buffer
+  if ((size_t)2 * RS::F * A.ldY > (size_t)RS::F * RS::NP || A.ldz > RS::NP) return cudaErrorInvalidConfiguration;
   static std::mutex mu;
   static int slots_a = 0, slots_c = 0;
   cudaError_t e;

@@ -1,0 +1,65 @@
+// tma.cuh -- bulk asynchronous copies (the TMA's non-tensor form) with mbarrier
+// completion, for kernels that stage whole rows of global memory in shared
+// memory. Every wait is bounded: a wait that runs out reports failure and the
+// caller records an error code in the plan's device error word and returns.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace gfc {
+
+// error codes written to the device error word
+constexpr int kErrBulkWait = 0x7401;  // an mbarrier wait for a bulk copy ran out
+
+// upper bound on try_wait polls before a wait is declared failed (each poll
+// returns after at most a short hardware-defined suspension)
+constexpr unsigned kMbarPolls = 1u << 24;
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+
+// order this thread's earlier generic-proxy accesses of shared memory before
+// later async-proxy (bulk copy) writes to it
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+
+// one thread: expect `bytes` on the barrier's current phase and start the copy
+// of `bytes` (a multiple of 16; both addresses 16-byte aligned) from global to shared
+__device__ __forceinline__ void bulk_load(void* dst_smem, const void* src_gmem, unsigned bytes, uint64_t* bar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+          smem_addr(dst_smem)),
+      "l"(src_gmem), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+
+// wait until the barrier's phase `parity` has completed; false if the bound ran out
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
+  const unsigned a = smem_addr(bar);
+  for (unsigned i = 0; i < kMbarPolls; ++i) {
+    unsigned done;
+    asm volatile(
+        "{\n"
+        ".reg .pred p;\n"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "selp.u32 %0, 1, 0, p;\n"
+        "}\n"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+}  // namespace gfc
