@@ -441,6 +441,155 @@ __global__ void __launch_bounds__(S::THREADS, 2) k_fast_rows_fwd(const float2* _
 }
 
 // ---------------------------------------------------------------------------
+// pass L folded into pass A (gradient input): the 2F gx rows and 2F + 1 gy rows
+// an item needs (gy from the row above its first pair) arrive as two bulk
+// copies into the exchange buffers, and each thread forms its packed values
+// L[2 pair][j] + i L[2 pair + 1][j] (Eq. 3) from shared memory with the same
+// arithmetic as pass L, so the packed rows never go through HBM. The rest is
+// k_fast_rows_fwd. The next item's rows are requested once this item's
+// spectrum is stored (the staging area spans both exchange buffers).
+// Requires W sizeof(T) to be a multiple of 16 and the staging to fit
+// (fused_div_fits).
+// ---------------------------------------------------------------------------
+template <class S, typename T>
+__host__ __device__ constexpr size_t fused_stage_bytes(int W) {
+  return (size_t)(4 * S::F + 1) * W * sizeof(T);
+}
+template <class S>
+__host__ __device__ constexpr size_t fused_exchange_bytes() {
+  return (size_t)(S::F * S::NP + S::F * S::NO) * sizeof(float2);
+}
+
+template <class S, typename T>
+__global__ void __launch_bounds__(S::THREADS, 2) k_fast_rows_fwd_div(const T* __restrict__ gx,
+                                                                     const T* __restrict__ gy,
+                                                                     float2* __restrict__ spec,
+                                                                     const float2* __restrict__ twg, FastArgs A) {
+  extern __shared__ __align__(16) float2 sm[];
+  float2* tw2 = sm;
+  float2* buf = sm + S::R1 * S::R2;
+  float2* buf2 = buf + S::F * S::NP;
+  constexpr int RW = 2 * S::F;  // image rows per item
+  T* sgx = reinterpret_cast<T*>(buf);  // gx rows r0 .. r0 + RW - 1
+  T* sgy = sgx + (size_t)RW * A.W;     // gy rows r0 - 1 .. r0 + RW - 1
+  __shared__ __align__(8) uint64_t bar;
+  const int tid = threadIdx.x;
+  const int f = tid / S::T, t = tid - f * S::T;
+  const bool act = f < S::F;
+  for (int i = tid; i < S::R1 * S::R2; i += blockDim.x) {
+    const int j = i / S::R2, r = i - j * S::R2;
+    tw2[i] = twg[r * j];
+  }
+  float2* mybuf = buf + (act ? f : 0) * S::NP;
+  float2* mybuf2 = buf2 + (act ? f : 0) * S::NO;
+  const int uf = tid % S::F, uk0 = tid / S::F;
+  const bool uact = tid < S::F * S::T;
+  const int items = A.nf * A.ngroups;
+  const size_t fe = (size_t)A.H * A.W;
+  auto issue = [&](int w) {  // one thread: stage the gradient rows of item w
+    const int field = w / A.ngroups, g = w - field * A.ngroups;
+    const int r0 = g * RW;
+    const int nx = (A.H - r0) < RW ? (A.H - r0) : RW;             // gx rows r0 .. r0 + nx - 1 (nx may be 0)
+    const int y0 = r0 > 0 ? r0 - 1 : 0, y1 = (A.H < r0 + RW) ? A.H : r0 + RW;  // gy rows y0 .. y1 - 1
+    const unsigned row = (unsigned)(A.W * sizeof(T));
+    mbar_expect_tx(&bar, (unsigned)(nx > 0 ? nx : 0) * row + (unsigned)(y1 - y0) * row);
+    if (nx > 0) bulk_copy(sgx, gx + field * fe + (size_t)r0 * A.W, (unsigned)nx * row, &bar);
+    bulk_copy(sgy + (size_t)(y0 - (r0 - 1)) * A.W, gy + field * fe + (size_t)y0 * A.W, (unsigned)(y1 - y0) * row,
+              &bar);
+  };
+  if (tid == 0) mbar_init(&bar, 1);
+  __syncthreads();
+  if (tid == 0 && (int)blockIdx.x < items) issue(blockIdx.x);
+  unsigned phase = 0;
+#pragma unroll 1
+  for (int w = blockIdx.x; w < items; w += gridDim.x, phase ^= 1u) {
+    const int field = w / A.ngroups, g = w - field * A.ngroups;
+    const bool landed = mbar_wait(&bar, phase);
+    if (__syncthreads_or(!landed)) {  // the copies never completed: report, let them drain, stop
+      if (tid == 0) atomicExch(A.err, kErrBulkWait);
+      mbar_wait(&bar, phase);
+      return;
+    }
+    float2 v[S::R1];
+    if (act) {
+      const int r0 = g * RW, ia = r0 + 2 * f, ib = ia + 1;
+      const bool ha = ia < A.H, hb = ib < A.H, hm = ia >= 1;  // rows present (ia - 1 < H always)
+      const bool sa = ia < A.nrows, sb = ib < A.nrows;         // rows inside the support
+      const T* xa = sgx + (size_t)(2 * f) * A.W;
+      const T* xb = xa + A.W;
+      const T* ym = sgy + (size_t)(2 * f) * A.W;  // gy row ia - 1
+      const T* ya = ym + A.W;
+      const T* yb = ya + A.W;
+#pragma unroll
+      for (int r = 0; r < S::R1; ++r) {
+        const int j = t + S::R2 * r - kP;
+        // columns j - 1 .. j inside [0, W) for every t and every width padding to N
+        const bool sure = (S::R2 * r >= kP + 1) && (S::R2 * r + S::R2 - 1 - kP < S::WMIN);
+        const bool c1 = sure || (j >= 0 && j < A.W), c0 = sure || (j >= 1 && j - 1 < A.W);
+        const bool inj = sure || (j >= 0 && j < A.ncols);
+        const float xa1 = (ha && c1) ? f_to_f(xa[j]) : 0.0f, xa0 = (ha && c0) ? f_to_f(xa[j - 1]) : 0.0f;
+        const float xb1 = (hb && c1) ? f_to_f(xb[j]) : 0.0f, xb0 = (hb && c0) ? f_to_f(xb[j - 1]) : 0.0f;
+        const float ya1 = (ha && c1) ? f_to_f(ya[j]) : 0.0f, yb1 = (hb && c1) ? f_to_f(yb[j]) : 0.0f;
+        const float ym1 = (hm && c1) ? f_to_f(ym[j]) : 0.0f;
+        const float la = (xa1 - xa0) + (ya1 - ym1);
+        const float lb = (xb1 - xb0) + (yb1 - ya1);
+        v[r] = make_float2((sa && inj) ? la : 0.0f, (sb && inj) ? lb : 0.0f);
+      }
+    }
+    __syncthreads();  // every staged row read: the buffers become the exchange buffers
+    if (act) {
+      dft_reg<S::R1, -1>(v);
+#pragma unroll
+      for (int s2 = 0; s2 < S::R1; ++s2) mybuf[t * (S::R1 + 1) + s2] = v[s2];
+    }
+    __syncthreads();
+    if (act && t < S::JSPAN) {
+#pragma unroll
+      for (int jj = 0; jj < S::J2; ++jj) {
+        const int j = t + S::R2 * jj;
+        float2 u[S::R2];
+        u[0] = mybuf[j];
+#pragma unroll
+        for (int r = 1; r < S::R2; ++r) u[r] = cmul(mybuf[j + (S::R1 + 1) * r], tw2[j * S::R2 + r]);
+        dft_reg<S::R2, -1>(u);
+#pragma unroll
+        for (int s2 = 0; s2 < S::R2; ++s2) mybuf2[j + S::R1 * s2] = u[s2];
+      }
+    }
+    __syncthreads();  // stage-2 results visible
+    if (g == 0) {
+      float2* Sz = spec + (size_t)field * A.Nh * A.ldM;
+      const int nz = A.M - A.nrows;
+      for (int idx = tid; idx < A.Nh * nz; idx += blockDim.x) {
+        const int k = idx / nz, q = idx - k * nz;
+        Sz[(size_t)k * A.ldM + (q < kP ? q : q + A.nrows)] = make_float2(0.0f, 0.0f);
+      }
+    }
+    const int ra = g * 2 * S::F + 2 * uf;
+    if (uact && ra < A.nrows) {
+      float2* Sp = spec + (size_t)field * A.Nh * A.ldM + A.p + ra;
+      const float2* zb = buf2 + uf * S::NO;
+      const bool two = ra + 1 < A.nrows, vec = ((A.p + ra) & 1) == 0;
+      for (int k = uk0; k < A.Nh; k += S::T) {
+        const float2 zk = zb[k], zm = zb[k == 0 ? 0 : S::N - k];
+        const float2 xa = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
+        const float2 xb = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
+        float2* dst = Sp + (size_t)k * A.ldM;
+        if (two && vec) {
+          *reinterpret_cast<float4*>(dst) = make_float4(xa.x, xa.y, xb.x, xb.y);
+        } else {
+          dst[0] = xa;
+          if (two) dst[1] = xb;
+        }
+      }
+    }
+    fence_proxy_async_smem();  // this thread's accesses of the buffers precede the next bulk copies
+    __syncthreads();
+    if (tid == 0 && w + (int)gridDim.x < items) issue(w + gridDim.x);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // pass B: column transform, Green multiply, inverse column transform; one
 // block per (field, block of C columns).
 // ---------------------------------------------------------------------------
@@ -837,7 +986,7 @@ static cudaError_t run_fast_mode(gfc_plan* P, const Bufs& bf, const T* in0, cons
   // the row passes stage their F packed rows / 2F rows of Y in the exchange buffer
   if ((size_t)2 * RS::F * A.ldY > (size_t)RS::F * RS::NP || A.ldz > RS::NP) return cudaErrorInvalidConfiguration;
   static std::mutex mu;
-  static int slots_a = 0, slots_c = 0;
+  static int slots_a = 0, slots_c = 0, slots_d = 0;
   cudaError_t e;
   {
     std::lock_guard<std::mutex> lock(mu);
@@ -851,10 +1000,24 @@ static cudaError_t run_fast_mode(gfc_plan* P, const Bufs& bf, const T* in0, cons
         if ((e = fast_setup(k_fast_rows_inv<RS, T>, RS::THREADS, RS::smem_bytes(), &slots_c)) != cudaSuccess) return e;
       }
       if ((e = fast_setup(k_fast_rows_fwd<RS>, RS::THREADS, RS::smem_bytes_fwd(), &slots_a)) != cudaSuccess) return e;
+      if (MODE == 0 &&
+          (e = fast_setup(k_fast_rows_fwd_div<RS, T>, RS::THREADS, RS::smem_bytes_fwd(), &slots_d)) != cudaSuccess)
+        return e;
     }
   }
   auto grid_for = [](long items, int slots) { return (int)(items < slots ? items : slots); };
-  prof_begin(P, 3, st);
+  // plain gradient solves fold pass L into the row pass when the gradient rows
+  // can be bulk-copied and their staging fits the exchange buffers
+  const bool fused_div = MODE == 0 && !(ed && ed->kind != kEditNone) && (P->W * sizeof(T)) % 16 == 0 &&
+                         fused_stage_bytes<RS, T>(P->W) <= fused_exchange_bytes<RS>() &&
+                         getenv("GFC_UNFUSED_DIV") == nullptr;
+  if (fused_div) {
+    prof_begin(P, 0, st);
+    k_fast_rows_fwd_div<RS, T><<<grid_for((long)nf * A.ngroups, slots_d), RS::THREADS, RS::smem_bytes_fwd(), st>>>(
+        in0, in1, bf.spec, P->twN, A);
+    prof_end(P, st);
+  }
+  if (!fused_div) prof_begin(P, 3, st);
   {
     const int nq = A.ldz / 4;
     const int bx = (MODE == 2) ? ((nq + 31) / 32) * 32 : (nq >= 256 ? 256 : ((nq + 31) / 32) * 32);
@@ -867,15 +1030,17 @@ static cudaError_t run_fast_mode(gfc_plan* P, const Bufs& bf, const T* in0, cons
     else if (kind == kEditMerge)
       k_fast_div_edit<T, kEditMerge><<<egrid, ex, 0, st>>>(in0, in1, static_cast<const T*>(ed->edges), nullptr,
                                                            ed->alpha, bf.zbuf, A);
-    else
+    else if (!fused_div)
       k_fast_div<T, MODE><<<grid, bx, 0, st>>>(in0, in1, bf.zbuf, bf.partial, A);
   }
-  prof_end(P, st);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  prof_begin(P, 0, st);
-  k_fast_rows_fwd<RS><<<grid_for((long)nf * A.ngroups, slots_a), RS::THREADS, RS::smem_bytes_fwd(), st>>>(
-      bf.zbuf, bf.spec, P->twN, A);
-  prof_end(P, st);
+  if (!fused_div) {
+    prof_end(P, st);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    prof_begin(P, 0, st);
+    k_fast_rows_fwd<RS><<<grid_for((long)nf * A.ngroups, slots_a), RS::THREADS, RS::smem_bytes_fwd(), st>>>(
+        bf.zbuf, bf.spec, P->twN, A);
+    prof_end(P, st);
+  }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   prof_begin(P, 1, st);
   k_fast_cols<CS, MODE><<<dim3(A.nparts, nf), CS::THREADS, CS::smem_bytes(), st>>>(bf.spec, bf.zbuf, P->GT, P->twM,

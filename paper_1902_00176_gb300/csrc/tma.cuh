@@ -12,9 +12,16 @@ namespace gfc {
 // error codes written to the device error word
 constexpr int kErrBulkWait = 0x7401;  // an mbarrier wait for a bulk copy ran out
 
-// upper bound on try_wait polls before a wait is declared failed (each poll
-// returns after at most a short hardware-defined suspension)
-constexpr unsigned kMbarPolls = 1u << 24;
+// a wait for a bulk copy gives up after this long (the copies here take
+// microseconds), or after kMbarPolls polls if the global timer does not advance
+constexpr unsigned long long kMbarTimeoutNs = 2000000000ull;
+constexpr unsigned kMbarPolls = 1u << 28;
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
 
 __device__ __forceinline__ unsigned smem_addr(const void* p) {
   return (unsigned)__cvta_generic_to_shared(p);
@@ -31,11 +38,15 @@ __device__ __forceinline__ void fence_proxy_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
 }
 
-// one thread: expect `bytes` on the barrier's current phase and start the copy
-// of `bytes` (a multiple of 16; both addresses 16-byte aligned) from global to shared
-__device__ __forceinline__ void bulk_load(void* dst_smem, const void* src_gmem, unsigned bytes, uint64_t* bar) {
+// one thread: expect `bytes` more on the barrier's current phase (one arrival)
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(bytes)
                : "memory");
+}
+
+// start a copy of `bytes` (a multiple of 16; both addresses 16-byte aligned)
+// from global to shared memory that completes on `bar`
+__device__ __forceinline__ void bulk_copy(void* dst_smem, const void* src_gmem, unsigned bytes, uint64_t* bar) {
   asm volatile(
       "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
           smem_addr(dst_smem)),
@@ -43,9 +54,17 @@ __device__ __forceinline__ void bulk_load(void* dst_smem, const void* src_gmem, 
       : "memory");
 }
 
-// wait until the barrier's phase `parity` has completed; false if the bound ran out
+// one thread: expect and start one copy
+__device__ __forceinline__ void bulk_load(void* dst_smem, const void* src_gmem, unsigned bytes, uint64_t* bar) {
+  mbar_expect_tx(bar, bytes);
+  bulk_copy(dst_smem, src_gmem, bytes, bar);
+}
+
+// wait until the barrier's phase `parity` has completed; false if the time
+// bound ran out
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
   const unsigned a = smem_addr(bar);
+  const unsigned long long t0 = global_ns();
   for (unsigned i = 0; i < kMbarPolls; ++i) {
     unsigned done;
     asm volatile(
@@ -58,6 +77,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
         : "r"(a), "r"(parity)
         : "memory");
     if (done) return true;
+    if (global_ns() - t0 > kMbarTimeoutNs) return false;
   }
   return false;
 }

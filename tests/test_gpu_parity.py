@@ -397,3 +397,16 @@ def test_blend_workload_16bit_storage(dtype):
     ref = O.solve_from_gradient(_np(tx)[0, 1], _np(ty)[0, 1], p.M, p.N, p.pad)
     assert _rel(out[0, 1], ref) <= REL_16
     p.close()
+
+
+@pytest.mark.parametrize("H,W,dt", [(801, 1200, torch.float32), (64, 96, torch.bfloat16), (256, 256, torch.float32)])
+def test_fused_divergence_row_pass_matches_separate_passes(H, W, dt, monkeypatch):
+    """Pass L folded into the forward row pass gives the same bits as the two passes."""
+    gx, gy = synth.perturbed_gradient_batch(2, H, W, seed=8100)
+    p = gfc.Plan(H, W, 1, 2, dtype=dt, device=DEV)
+    tx, ty = _to_dev(gx, dt), _to_dev(gy, dt)
+    fused = p.solve_from_gradient(tx, ty)
+    monkeypatch.setenv("GFC_UNFUSED_DIV", "1")
+    separate = p.solve_from_gradient(tx, ty)
+    assert torch.equal(fused, separate)
+    p.close()
