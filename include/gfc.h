@@ -155,10 +155,11 @@ gfc_status gfc_fft_c2c(int n, int count, int dir, const void* in, void* out, voi
 
 /* Solve from gradients held in HOST memory (Eq. 3, Eq. 23, Algorithm B), the
  * same computation as gfc_solve_from_gradient with the transfers included:
- * per chunk of fields, gx and gy are copied host-to-device, solved, and the
- * result copied device-to-host, with the copies of one chunk overlapping the
- * solve of the next (two staging buffers, two copy streams owned by the plan,
- * allocated on the first call). gx, gy, out: [batch, C, H, W] host arrays in
+ * the batch is cut into about 32 steps; per step gx and gy are copied
+ * host-to-device, solved, and the result copied device-to-host, with the
+ * copies of each step overlapping the solves and copies of the others (three
+ * rotating staging buffers and two copy streams owned by the plan, allocated
+ * on the first call). gx, gy, out: [batch, C, H, W] host arrays in
  * the plan's dtype; page-locked memory gives asynchronous, overlapped copies.
  * Asynchronous on the plan's stream: `out` is complete once the plan's stream
  * (or gfc_plan_sync) has completed. */
@@ -280,6 +281,15 @@ gfc_status gfc_graph_create(gfc_plan* plan, int op, const void* in0, const void*
 gfc_status gfc_graph_launch(gfc_graph* graph, void* stream);
 /* Free the graph. NULL is accepted. */
 gfc_status gfc_graph_destroy(gfc_graph* graph);
+
+/* Self-test of the failure path of the bounded device-side waits (not from the
+ * paper): queues one block on the plan's stream that waits on an mbarrier
+ * nothing ever arrives at, with a limit of timeout_ms (1..2000). The wait runs
+ * out and records its error code in the plan's device error word, exactly as
+ * a bulk copy that never completed would, so the next gfc_plan_sync returns
+ * GFC_ERR_TIMEOUT (and clears the word). No GPU fault or hang is involved and
+ * the context stays usable. */
+gfc_status gfc_plan_selftest_wait(gfc_plan* plan, int timeout_ms);
 
 /* Wait for the plan's stream and report any device-side error since the last
  * sync (GFC_ERR_TIMEOUT for a bounded wait that ran out, GFC_ERR_CUDA otherwise). */

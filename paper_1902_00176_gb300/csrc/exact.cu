@@ -2,8 +2,8 @@
 // M = H + 2p, N = W + 2p, whatever their prime factors (801x1200 -> 809x1208,
 // where 809 is prime and 1208 = 8 x 151).
 //
-// The field is carried as a full complex M x N array (the real Laplacian in
-// the real part): row DFTs of length N, a tiled transpose, column DFTs of
+// Two fields are carried as one complex M x N torus (one Laplacian in the real
+// part, the next in the imaginary part): row DFTs of length N, a tiled transpose, column DFTs of
 // length M with the Green multiply (Eq. 23) between the forward and the
 // inverse transform, a transpose back, inverse row DFTs, then Algorithm B's
 // offset and crop. A length that is 7-smooth runs the shared-memory Stockham
@@ -140,48 +140,54 @@ __global__ void k_exact_transpose(const float2* __restrict__ src, float2* __rest
   }
 }
 
-// X[f][r][c] = L on the M x N torus (real part), image block at (p, p);
-// MODE 0: L = div E (Eq. 3) of the (optionally edited) gradient, MODE 1: L given
+// L of field f at torus cell (r, c): image block at (p, p); MODE 0: L = div E
+// (Eq. 3) of the (optionally edited) gradient, MODE 1: L given
 template <typename T, int MODE, int EDIT>
-__global__ void k_exact_load(const T* __restrict__ in0, const T* __restrict__ in1, float2* __restrict__ X, int H,
-                             int W, int M, int N, int p, EditArgs ed) {
-  const size_t fe = (size_t)H * W;
-  const int f = blockIdx.y;
-  const T* a = in0 + f * fe;
-  const T* b = (MODE == 0) ? in1 + f * fe : nullptr;
-  const T* e = (MODE == 0 && EDIT == kEditMerge) ? static_cast<const T*>(ed.edges) + f * fe : nullptr;
-  const float t2 = (MODE == 0 && EDIT == kEditThreshold) ? ed.t2[f] : 0.0f;
-  float2* x = X + (size_t)f * M * N;
+__device__ __forceinline__ float exact_lap(const T* __restrict__ in0, const T* __restrict__ in1, int f, int r, int c,
+                                           int H, int W, int p, const EditArgs& ed) {
+  const int i = r - p, j = c - p;
   const int nrows = (MODE == 0) ? H + 1 : H, ncols = (MODE == 0) ? W + 1 : W;
+  if (i < 0 || i >= nrows || j < 0 || j >= ncols) return 0.0f;
+  const size_t fe = (size_t)H * W;
+  const T* a = in0 + f * fe;
+  if (MODE != 0) return ex_ld(a + (size_t)i * W + j);
+  const T* b = in1 + f * fe;
+  const T* e = (EDIT == kEditMerge) ? static_cast<const T*>(ed.edges) + f * fe : nullptr;
+  const float t2 = (EDIT == kEditThreshold) ? ed.t2[f] : 0.0f;
+  const float2 c0 = edit_pixel<T, EDIT>(a, b, e, i, j, H, W, t2, ed.alpha);
+  return (c0.x - edit_pixel<T, EDIT>(a, b, e, i, j - 1, H, W, t2, ed.alpha).x) +
+         (c0.y - edit_pixel<T, EDIT>(a, b, e, i - 1, j, H, W, t2, ed.alpha).y);
+}
+
+// Two fields per complex torus: X[q] = L[2q] + i L[2q + 1] (the second 0 when
+// nf is odd). G is real and even, so the convolution maps the real and the
+// imaginary part each to its own real solution.
+template <typename T, int MODE, int EDIT>
+__global__ void k_exact_load(const T* __restrict__ in0, const T* __restrict__ in1, float2* __restrict__ X, int nf,
+                             int H, int W, int M, int N, int p, EditArgs ed) {
+  const int q = blockIdx.y, f0 = 2 * q, f1 = f0 + 1;
+  float2* x = X + (size_t)q * M * N;
   for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < (long long)M * N;
        idx += (long long)gridDim.x * blockDim.x) {
     const int r = (int)(idx / N), c = (int)(idx - (long long)r * N);
-    const int i = r - p, j = c - p;
-    float v = 0.0f;
-    if (i >= 0 && i < nrows && j >= 0 && j < ncols) {
-      if (MODE == 0) {
-        const float2 c0 = edit_pixel<T, EDIT>(a, b, e, i, j, H, W, t2, ed.alpha);
-        v = (c0.x - edit_pixel<T, EDIT>(a, b, e, i, j - 1, H, W, t2, ed.alpha).x) +
-            (c0.y - edit_pixel<T, EDIT>(a, b, e, i - 1, j, H, W, t2, ed.alpha).y);
-      } else {
-        v = ex_ld(a + (size_t)i * W + j);
-      }
-    }
-    x[idx] = make_float2(v, 0.0f);
+    const float v0 = exact_lap<T, MODE, EDIT>(in0, in1, f0, r, c, H, W, p, ed);
+    const float v1 = f1 < nf ? exact_lap<T, MODE, EDIT>(in0, in1, f1, r, c, H, W, p, ed) : 0.0f;
+    x[idx] = make_float2(v0, v1);
   }
 }
 
-// out[i][j] = Re u[p + i][p + j] - Re u[0][0] (Algorithm B)
+// out[i][j] = u[p + i][p + j] - u[0][0] (Algorithm B), u the real (even field)
+// or imaginary (odd field) part of the pair's solution
 template <typename T>
 __global__ void k_exact_out(const float2* __restrict__ X, T* __restrict__ out, int H, int W, int M, int N, int p) {
   const int f = blockIdx.y;
-  const float2* x = X + (size_t)f * M * N;
-  const float u00 = x[0].x;
+  const float* x = reinterpret_cast<const float*>(X + (size_t)(f / 2) * M * N) + (f & 1);
+  const float u00 = x[0];
   T* o = out + (size_t)f * H * W;
   for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < (long long)H * W;
        idx += (long long)gridDim.x * blockDim.x) {
     const int i = (int)(idx / W), j = (int)(idx - (long long)i * W);
-    o[idx] = ex_st<T>(x[(size_t)(p + i) * N + (p + j)].x - u00);
+    o[idx] = ex_st<T>(x[2 * ((size_t)(p + i) * N + (p + j))] - u00);
   }
 }
 
@@ -273,8 +279,9 @@ template <typename T, int MODE>
 cudaError_t run_exact(gfc_plan* P, const Bufs& bf, const T* in0, const T* in1, T* out0, int nf, cudaStream_t st,
                       const EditArgs* ed) {
   const int M = P->M, N = P->N;
+  const int np = (nf + 1) / 2;  // complex tori: two fields each
   float2* X = bf.spec;
-  float2* XT = bf.spec + (size_t)nf * M * N;
+  float2* XT = bf.spec + (size_t)np * M * N;
   const EditArgs none{kEditNone, 0.0f, nullptr, nullptr};
   const EditArgs& E = ed ? *ed : none;
   int dev = 0, sms = 148;
@@ -283,23 +290,23 @@ cudaError_t run_exact(gfc_plan* P, const Bufs& bf, const T* in0, const T* in1, T
   const DimArgs dr = dim_args(P->ex_row), dc = dim_args(P->ex_col);
   const size_t sr = dim_smem(P->ex_row), sc = dim_smem(P->ex_col);
   cudaError_t e;
-  // divergence / Laplacian into the complex torus
+  // divergence / Laplacian into the complex tori
   {
     const long long cells = (long long)M * N;
     int gx = (int)((cells + kExactThreads - 1) / kExactThreads);
     if (gx > 4 * sms) gx = 4 * sms;
-    const dim3 g(gx, nf);
+    const dim3 g(gx, np);
     if (MODE == 1)
-      k_exact_load<T, 1, kEditNone><<<g, kExactThreads, 0, st>>>(in0, in1, X, P->H, P->W, M, N, P->pad, E);
+      k_exact_load<T, 1, kEditNone><<<g, kExactThreads, 0, st>>>(in0, in1, X, nf, P->H, P->W, M, N, P->pad, E);
     else if (E.kind == kEditThreshold)
-      k_exact_load<T, 0, kEditThreshold><<<g, kExactThreads, 0, st>>>(in0, in1, X, P->H, P->W, M, N, P->pad, E);
+      k_exact_load<T, 0, kEditThreshold><<<g, kExactThreads, 0, st>>>(in0, in1, X, nf, P->H, P->W, M, N, P->pad, E);
     else if (E.kind == kEditMerge)
-      k_exact_load<T, 0, kEditMerge><<<g, kExactThreads, 0, st>>>(in0, in1, X, P->H, P->W, M, N, P->pad, E);
+      k_exact_load<T, 0, kEditMerge><<<g, kExactThreads, 0, st>>>(in0, in1, X, nf, P->H, P->W, M, N, P->pad, E);
     else
-      k_exact_load<T, 0, kEditNone><<<g, kExactThreads, 0, st>>>(in0, in1, X, P->H, P->W, M, N, P->pad, E);
+      k_exact_load<T, 0, kEditNone><<<g, kExactThreads, 0, st>>>(in0, in1, X, nf, P->H, P->W, M, N, P->pad, E);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
-  const long long rows = (long long)nf * M;
+  const long long rows = (long long)np * M;
   const int grow = (int)(rows < 8LL * sms ? rows : 8LL * sms);
   if ((e = raise_smem(k_exact_rows<-1>, sr)) != cudaSuccess) return e;
   if ((e = raise_smem(k_exact_rows<+1>, sr)) != cudaSuccess) return e;
@@ -309,14 +316,14 @@ cudaError_t run_exact(gfc_plan* P, const Bufs& bf, const T* in0, const T* in1, T
   prof_end(P, st);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   const dim3 tb(32, 8);
-  k_exact_transpose<<<dim3((N + 31) / 32, (M + 31) / 32, nf), tb, 0, st>>>(X, XT, M, N);
+  k_exact_transpose<<<dim3((N + 31) / 32, (M + 31) / 32, np), tb, 0, st>>>(X, XT, M, N);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  const long long cols = (long long)nf * N;
+  const long long cols = (long long)np * N;
   prof_begin(P, 1, st);
-  k_exact_cols<<<(int)(cols < 8LL * sms ? cols : 8LL * sms), kExactThreads, sc, st>>>(XT, nf, M, N, P->Nh, P->G, dc);
+  k_exact_cols<<<(int)(cols < 8LL * sms ? cols : 8LL * sms), kExactThreads, sc, st>>>(XT, np, M, N, P->Nh, P->G, dc);
   prof_end(P, st);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  k_exact_transpose<<<dim3((M + 31) / 32, (N + 31) / 32, nf), tb, 0, st>>>(XT, X, N, M);
+  k_exact_transpose<<<dim3((M + 31) / 32, (N + 31) / 32, np), tb, 0, st>>>(XT, X, N, M);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   prof_begin(P, 2, st);
   k_exact_rows<+1><<<grow, kExactThreads, sr, st>>>(X, rows, N, dr);

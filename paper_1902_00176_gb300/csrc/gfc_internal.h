@@ -17,6 +17,7 @@ struct Bufs {
   float* partial;  // per-block sums
 };
 constexpr int kMaxSlots = 4;
+constexpr int kHostBufs = 4;  // most staging buffers of the host-buffer pipeline
 
 // One transform length of an EXACT-size plan (exact.cu).
 struct ExactDim {
@@ -73,10 +74,11 @@ struct gfc_plan {
   cudaEvent_t ev_fork;
   int* dev_err;   // device error word
   // host-buffer path (allocated on first use)
-  void* stage_in[2][2];   // [buffer][gx, gy] device staging for one chunk
-  void* stage_out[2];
+  void* stage_in[gfc::kHostBufs][2];  // [buffer][gx, gy] device staging for one host step
+  void* stage_out[gfc::kHostBufs];
   cudaStream_t copy_in, copy_out;
-  cudaEvent_t ev_in[2], ev_comp[2], ev_out[2];
+  cudaEvent_t ev_in[gfc::kHostBufs], ev_comp[gfc::kHostBufs], ev_out[gfc::kHostBufs];
+  int host_bufs;          // staging buffers in rotation (<= kHostBufs)
   bool host_ready;
   int host_chunk;         // fields per host-pipeline step (copies of one step overlap the solve of another)
   // ragged batch (gfc_plan_create_ragged)

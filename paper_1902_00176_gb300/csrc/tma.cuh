@@ -62,7 +62,8 @@ __device__ __forceinline__ void bulk_load(void* dst_smem, const void* src_gmem, 
 
 // wait until the barrier's phase `parity` has completed; false if the time
 // bound ran out
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity,
+                                          unsigned long long timeout_ns = kMbarTimeoutNs) {
   const unsigned a = smem_addr(bar);
   const unsigned long long t0 = global_ns();
   for (unsigned i = 0; i < kMbarPolls; ++i) {
@@ -77,7 +78,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
         : "r"(a), "r"(parity)
         : "memory");
     if (done) return true;
-    if (global_ns() - t0 > kMbarTimeoutNs) return false;
+    if (global_ns() - t0 > timeout_ns) return false;
   }
   return false;
 }

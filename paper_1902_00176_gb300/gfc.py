@@ -99,6 +99,7 @@ _SIGNATURES = {
                          ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)],
     "gfc_graph_launch": [ctypes.c_void_p, ctypes.c_void_p],
     "gfc_graph_destroy": [ctypes.c_void_p],
+    "gfc_plan_selftest_wait": [ctypes.c_void_p, ctypes.c_int],
     "gfc_plan_sync": [ctypes.c_void_p],
     "gfc_destroy": [ctypes.c_void_p],
     "gfc_last_error": [],
@@ -335,6 +336,12 @@ class Plan:
 
     def sync(self):
         _check(lib().gfc_plan_sync(self._h))
+
+    def selftest_wait(self, timeout_ms: int = 50):
+        """Queue a device wait that runs out after ``timeout_ms``; the next ``sync``
+        raises with GFC_ERR_TIMEOUT (checks the bounded-wait failure path)."""
+        self._bind_stream()
+        _check(lib().gfc_plan_selftest_wait(self._h, int(timeout_ms)))
 
 
 _plans: dict = {}

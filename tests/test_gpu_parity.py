@@ -410,3 +410,21 @@ def test_fused_divergence_row_pass_matches_separate_passes(H, W, dt, monkeypatch
     separate = p.solve_from_gradient(tx, ty)
     assert torch.equal(fused, separate)
     p.close()
+
+
+def test_bounded_wait_reports_timeout_and_context_survives():
+    """A device wait that nothing completes runs out after its limit and is
+    reported as GFC_ERR_TIMEOUT by the next sync; later solves still work."""
+    H, W = 64, 96
+    _, gx, gy = synth.gradient_removal_image(seed=3)
+    p = gfc.Plan(H, W, device=DEV)
+    tx, ty = _to_dev(gx[None, None]), _to_dev(gy[None, None])
+    before = p.solve_from_gradient(tx, ty)
+    p.selftest_wait(50)
+    with pytest.raises(gfc.GFCError) as exc:
+        p.sync()
+    assert exc.value.status == 5  # GFC_ERR_TIMEOUT
+    p.sync()  # the error word was cleared
+    after = p.solve_from_gradient(tx, ty)
+    assert torch.equal(before, after)
+    p.close()
