@@ -418,7 +418,24 @@ def extra_workloads(dev):
     p.close()
     res["edit_100x801x1200_fp32"] = _edit_workload(dev)
     res["exact_809x1208_100x801x1200_fp32"] = _exact_workload(dev)
+    res["backward_100x801x1200_fp32"] = _backward_workload(dev)
     return res
+
+
+def _backward_workload(dev):
+    """The hand-written adjoint (gfc_backward) on the benchmark shape, beside the forward."""
+    import torch
+
+    from paper_1902_00176_gb300 import gfc
+
+    B, H, W = 100, 801, 1200
+    go = torch.randn(B, 1, H, W, device=dev)
+    gx, gy = torch.empty_like(go), torch.empty_like(go)
+    p = gfc.Plan(H, W, 1, B, device=dev)
+    ms_b = _time_ms(lambda: p.backward(go, gx, gy), dev, 10)
+    ms_f = _time_ms(lambda: p.solve_from_gradient(go, go, gx), dev, 10)
+    p.close()
+    return {"ms_forward": ms_f, "ms_backward": ms_b, "fwd_bwd_solves_per_s": B * 1000.0 / (ms_f + ms_b)}
 
 
 def _exact_workload(dev):

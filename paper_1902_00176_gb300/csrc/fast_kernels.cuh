@@ -218,7 +218,10 @@ __global__ void __launch_bounds__(512) k_fast_div(const T* __restrict__ in0, con
     dst[1] = make_float4(la[2], lb[2], la[3], lb[3]);
   }
   if (MODE == 2) {
-    double v = ((double)la[0] + la[1]) + ((double)la[2] + la[3]) + (((double)lb[0] + lb[1]) + ((double)lb[2] + lb[3]));
+    // a thread's 8 values summed in FP32 (error a few ulp of their magnitudes),
+    // the block's in FP64: FP64 arithmetic is scarce on this GPU
+    const float s8 = ((la[0] + la[1]) + (la[2] + la[3])) + ((lb[0] + lb[1]) + (lb[2] + lb[3]));
+    double v = (double)s8;
     __shared__ double red[32];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
