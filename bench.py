@@ -262,10 +262,28 @@ def run_gfc(args, rank, world, local_rank):
     min_bytes = 3 * 4 * fe * B + G_bytes  # read gx, gy, write out (fp32), read G once
     achieved = min_bytes / (ms_step / 1000.0) / 1e9
     names = ["row pass (div + pad + row FFT)", "column pass (FFT, x G, inverse FFT)",
-             "inverse row pass (FFT, offset, crop)", "other"]
+             "inverse row pass (FFT, offset, crop)", "divergence pass (when not folded into the row pass)"]
     tot_ms = sum(prof["pass_ms"]) or 1.0
-    per_kernel = [{"kernel": names[i], "launches": prof["launches"][i], "ms": prof["pass_ms"][i],
-                   "share": prof["pass_ms"][i] / tot_ms} for i in range(4) if prof["launches"][i]]
+    # algorithmic bytes each pass moves per launch (its inputs read and outputs
+    # written once): gradient 8 B/pixel, output 4 B/pixel, packed rows, the
+    # column-major spectrum and the row-major Y at the plan's padded strides
+    ld4 = lambda n: (n + 3) // 4 * 4
+    nh = plan.N // 2 + 1
+    spec_b = nh * ld4(plan.M) * 8
+    y_b = H * ld4(nh) * 8
+    z_b = ((H + 2) // 2) * ld4(plan.N) * 8
+    fused = prof["launches"][3] == 0
+    pass_bytes = [B * ((8 * fe if fused else z_b) + spec_b), B * (spec_b + y_b) + G_bytes, B * (y_b + 4 * fe),
+                  B * (8 * fe + z_b)]
+    per_kernel = []
+    for i in range(4):
+        if not prof["launches"][i]:
+            continue
+        ms1 = prof["pass_ms"][i] / prof["launches"][i]
+        gbs = pass_bytes[i] / (ms1 / 1000.0) / 1e9
+        per_kernel.append({"kernel": names[i], "launches": prof["launches"][i], "ms": prof["pass_ms"][i],
+                           "share": prof["pass_ms"][i] / tot_ms, "ms_per_launch": ms1,
+                           "algorithmic_bytes_per_launch": pass_bytes[i], "gb_per_s": gbs, "frac": gbs / peak})
     traffic = None
     tr_path = os.path.join(ROOT, "profiles", "traffic_solve_801x1200_b100.txt")
     if os.path.exists(tr_path):

@@ -112,8 +112,9 @@ struct RowShape {
   static constexpr int WMIN = cx_min_width(N);
   static constexpr size_t smem_bytes() { return (size_t)(R1 * R2 + F * NP) * sizeof(float2); }
   static constexpr size_t smem_bytes_fwd() { return (size_t)(R1 * R2 + F * NP + F * NO) * sizeof(float2); }
-  // padded index: one spare slot every R1 elements (conflict-free stage-1 writes)
-  static __device__ __forceinline__ int pad(int m) { return m + m / R1; }
+  // The exchange keeps one spare slot every R1 elements (element m at
+  // m + m / R1, conflict-free stage-1 writes); the kernels use the closed forms
+  // t (R1 + 1) + s for m = t R1 + s and j + (R1 + 1) r for m = j + R1 r.
 };
 
 template <int M_, int R1_, int R2_, int C_>
@@ -133,7 +134,8 @@ struct ColShape {
     return (size_t)C * GS * sizeof(float) +
            (size_t)(R1 * TWF_STRIDE + R2 * TWI_STRIDE + WORK) * sizeof(float2) + C * sizeof(double);
   }
-  static __device__ __forceinline__ int pad(int m) { return m + m / R2; }
+  // The inverse exchange keeps one spare slot every R2 elements (element m at
+  // m + m / R2); the kernel uses the closed forms t (R2 + 1) + s and t + (R2 + 1) r.
 };
 
 // ---------------------------------------------------------------------------
