@@ -130,9 +130,11 @@ struct ColShape {
   static constexpr int MINB = (THREADS <= 256) ? 2 : 1;  // blocks per SM the registers must allow
   static_assert(R1 <= R2, "column schedule needs R1 <= R2");
   static constexpr int GS = ((M + 3) / 4) * 4;  // floats per staged Green column (16-byte multiple)
+  // one float2 of padding keeps the exchange buffer 16-byte aligned (bulk copy destination)
+  static constexpr int BUF_PAD = ((C * GS * 4 + (R1 * TWF_STRIDE + R2 * TWI_STRIDE) * 8) % 16) ? 1 : 0;
   static constexpr size_t smem_bytes() {
     return (size_t)C * GS * sizeof(float) +
-           (size_t)(R1 * TWF_STRIDE + R2 * TWI_STRIDE + WORK) * sizeof(float2) + C * sizeof(double);
+           (size_t)(R1 * TWF_STRIDE + R2 * TWI_STRIDE + BUF_PAD + WORK) * sizeof(float2) + C * sizeof(double);
   }
   // The inverse exchange keeps one spare slot every R2 elements (element m at
   // m + m / R2); the kernel uses the closed forms t (R2 + 1) + s and t + (R2 + 1) r.
@@ -596,44 +598,60 @@ __global__ void __launch_bounds__(S::THREADS, 2) k_fast_rows_fwd_div(const T* __
 
 // ---------------------------------------------------------------------------
 // pass B: column transform, Green multiply, inverse column transform; one
-// block per (field, block of C columns).
+// block per (field, block of C columns). The block's Green columns and its C
+// spectrum columns (contiguous in the column-major layout) arrive as two bulk
+// copies while the twiddle tables are built.
 // ---------------------------------------------------------------------------
 template <class S, int MODE>
 __global__ void __launch_bounds__(S::THREADS, S::MINB) k_fast_cols(const float2* __restrict__ spec, float2* __restrict__ Y,
                                                           const float* __restrict__ GT, const float2* __restrict__ twg,
                                                           float* __restrict__ partial, FastArgs A) {
-  extern __shared__ float2 sm[];
+  extern __shared__ __align__(16) float2 sm[];
   float* gsm = reinterpret_cast<float*>(sm);            // [C][GS] this block's Green columns
   float2* twF = reinterpret_cast<float2*>(gsm + S::C * S::GS);  // [R1][TWF_STRIDE]: w_M^(r j), j < R1, r < R2
   float2* twI = twF + S::R1 * S::TWF_STRIDE;            // [R2][TWI_STRIDE]: w_M^(r j), j < R2, r < R1
-  float2* buf = twI + S::R2 * S::TWI_STRIDE;            // [C][MP]
+  float2* buf = twI + S::R2 * S::TWI_STRIDE + S::BUF_PAD;  // staged columns [C][ldM], then [C][MP]
   double* colval = reinterpret_cast<double*>(buf + S::WORK);  // [C] row-0 contributions
   const int tid = threadIdx.x;
   const int c = tid / S::T, t = tid - c * S::T;
   const int field = blockIdx.y, blk = blockIdx.x;
   const int l = blk * S::C + c;
   const bool act = (c < S::C) && (l < A.Nh);
-  const float2* col = spec + (size_t)field * A.Nh * A.ldM + (size_t)(act ? l : 0) * A.ldM;
-  // stage this block's Green columns into shared memory asynchronously; they are
-  // first needed after the first exchange
-  {
+  // this block's Green columns and spectrum columns arrive as two bulk copies
+  __shared__ __align__(8) uint64_t bar;
+  if (tid == 0) {
     const int ncol = (A.Nh - blk * S::C) < S::C ? (A.Nh - blk * S::C) : S::C;
-    const float* gsrc = GT + (size_t)blk * S::C * A.ldM;
-    constexpr int CH = S::GS / 4;  // 16-byte chunks per column
-    for (int i = tid; i < ncol * CH; i += blockDim.x) {
-      const int cc = i / CH, q = i - cc * CH;
-      const unsigned dst = (unsigned)__cvta_generic_to_shared(gsm + cc * S::GS + 4 * q);
-      const float* src = gsrc + (size_t)cc * A.ldM + 4 * q;
-      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src) : "memory");
-    }
-    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    const unsigned gb = (unsigned)(ncol * A.ldM * sizeof(float)), xb = (unsigned)(ncol * A.ldM * sizeof(float2));
+    mbar_init(&bar, 1);
+    mbar_expect_tx(&bar, gb + xb);
+    bulk_copy(gsm, GT + (size_t)blk * S::C * A.ldM, gb, &bar);
+    bulk_copy(buf, spec + ((size_t)field * A.Nh + (size_t)blk * S::C) * A.ldM, xb, &bar);
   }
   const float* gcol = gsm + (c < S::C ? c : 0) * S::GS;
   float2* mybuf = buf + (c < S::C ? c : 0) * S::MP;
+  for (int i = tid; i < S::R1 * S::R2; i += blockDim.x) {
+    const int j = i / S::R2, r = i - j * S::R2;
+    twF[j * S::TWF_STRIDE + r] = twg[r * j];
+  }
+  for (int i = tid; i < S::R2 * S::R1; i += blockDim.x) {
+    const int j = i / S::R1, r = i - j * S::R1;
+    twI[j * S::TWI_STRIDE + r] = twg[r * j];
+  }
+  __syncthreads();  // barrier initialised, twiddles in place
+  const bool landed = mbar_wait(&bar, 0);
+  if (__syncthreads_or(!landed)) {  // the copies never completed: report, let them drain, stop
+    if (tid == 0) atomicExch(A.err, kErrBulkWait);
+    mbar_wait(&bar, 0);
+    return;
+  }
   // rows outside the support were zeroed by the row pass
   float2 v[S::R1];
+  {
+    const float2* colS = buf + (size_t)(act ? c : 0) * A.ldM;
 #pragma unroll
-  for (int r = 0; r < S::R1; ++r) v[r] = col[t + S::R2 * r];
+    for (int r = 0; r < S::R1; ++r) v[r] = colS[t + S::R2 * r];
+  }
+  __syncthreads();  // every staged column read: buf becomes the exchange buffer
   if (MODE == 2) {
     // adjoint: z = Crop^T(grad_out) - (sum grad_out) e_00; the row DFT of the
     // second term is -sum in every column, at torus row 0. The sum is reduced
@@ -650,20 +668,11 @@ __global__ void __launch_bounds__(S::THREADS, S::MINB) k_fast_cols(const float2*
     __syncthreads();
     if (t == 0) v[0] = make_float2((float)(-tot_s), 0.0f);
   }
-  for (int i = tid; i < S::R1 * S::R2; i += blockDim.x) {
-    const int j = i / S::R2, r = i - j * S::R2;
-    twF[j * S::TWF_STRIDE + r] = twg[r * j];
-  }
-  for (int i = tid; i < S::R2 * S::R1; i += blockDim.x) {
-    const int j = i / S::R1, r = i - j * S::R1;
-    twI[j * S::TWI_STRIDE + r] = twg[r * j];
-  }
   if (act) {
     dft_reg<S::R1, -1>(v);
 #pragma unroll
     for (int s2 = 0; s2 < S::R1; ++s2) mybuf[t * S::R1 + s2] = v[s2];
   }
-  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
   __syncthreads();
   float2 u[S::R2];
   const bool act2 = act && t < S::R1;
@@ -763,9 +772,21 @@ __global__ void __launch_bounds__(S::THREADS, 3) k_fast_rows_inv(const float2* _
     const int r0 = g * RW, nr = (A.H - r0) < RW ? (A.H - r0) : RW;
     bulk_load(buf, Y + ((size_t)field * A.H + r0) * A.ldY, (unsigned)(nr * A.ldY * sizeof(float2)), &bar);
   };
+  // warp 0 loads the u[0,0] partial sums of the next item while this one is
+  // transformed (lane-strided, the same order as a plain loop over them)
+  constexpr int KPF = 5;
+  double pf[KPF];
+  auto prefetch = [&](int w) {
+    if (tid < 32 && w < items) {
+      const double* pp = reinterpret_cast<const double*>(partial) + (size_t)(w / A.ngroups) * (kMaxRowBlocks / 2);
+#pragma unroll
+      for (int k = 0; k < KPF; ++k) pf[k] = (tid + 32 * k < A.nparts) ? pp[tid + 32 * k] : 0.0;
+    }
+  };
   if (tid == 0) mbar_init(&bar, 1);
   __syncthreads();
   if (tid == 0 && (int)blockIdx.x < items) issue(blockIdx.x);
+  prefetch(blockIdx.x);
   int parity = 0;
   unsigned phase = 0;
 #pragma unroll 1
@@ -774,9 +795,14 @@ __global__ void __launch_bounds__(S::THREADS, 3) k_fast_rows_inv(const float2* _
     if (tid < 32) {
       // u[0,0] from the column blocks' FP64 partial sums: lane-strided, then a
       // fixed shuffle tree (the same order on every call)
-      const double* pp = reinterpret_cast<const double*>(partial) + (size_t)field * (kMaxRowBlocks / 2);
       double s2 = 0.0;
-      for (int i = tid; i < A.nparts; i += 32) s2 += pp[i];
+      if (A.nparts <= 32 * KPF) {
+#pragma unroll
+        for (int k = 0; k < KPF; ++k) s2 += pf[k];
+      } else {
+        const double* pp = reinterpret_cast<const double*>(partial) + (size_t)field * (kMaxRowBlocks / 2);
+        for (int i = tid; i < A.nparts; i += 32) s2 += pp[i];
+      }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) s2 += __shfl_down_sync(0xffffffffu, s2, o);
       if (tid == 0) u00s[parity] = (float)s2;
@@ -834,6 +860,7 @@ __global__ void __launch_bounds__(S::THREADS, 3) k_fast_rows_inv(const float2* _
         fence_proxy_async_smem();  // this thread's accesses of buf precede the next bulk copy into it
         __syncthreads();           // buf free
         if (tid == 0 && w + (int)gridDim.x < items) issue(w + gridDim.x);
+        prefetch(w + gridDim.x);
       }
       if (act2) {
         dft_reg<S::R2, +1>(u);
