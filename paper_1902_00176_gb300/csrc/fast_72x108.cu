@@ -1,11 +1,11 @@
 // fast_72x108.cu -- register-resident passes for the 72 x 108 padded domain
-// (row schedule RowShape<108, 9, 12, 10>, column schedule ColShape<72, 8, 9, 28>).
+// (row schedule RowShape<108, 9, 12, 10>, column schedule ColShape<72, 8, 9, 16>).
 #include "fast_kernels.cuh"
 
 namespace gfc {
 
 using RowS_72x108 = RowShape<108, 9, 12, 10>;
-using ColS_72x108 = ColShape<72, 8, 9, 28>;
+using ColS_72x108 = ColShape<72, 8, 9, 16>;
 
 cudaError_t fast_run_72x108(gfc_plan* P, const Bufs& bf, int mode, const void* in0, const void* in1, void* out0,
                           void* out1, int nf, cudaStream_t st, const EditArgs* ed) {

@@ -10,8 +10,8 @@
 //           transpose is folded into the two-for-one split it does through
 //           shared memory anyway;
 //   pass B  loads whole columns of spec straight into registers and writes its
-//           result row-major, Y[i][l] (image rows i < H), through a padded
-//           shared-memory transpose, into the buffer that held z;
+//           result row-major, Y[i][l] (image rows i < H), straight from
+//           registers, into the buffer that held z;
 //   pass C  loads rows of Y straight into registers.
 //
 // Row transforms (length N = R1 R2, T = R2 threads per transform, F transforms
@@ -117,27 +117,63 @@ struct RowShape {
   // t (R1 + 1) + s for m = t R1 + s and j + (R1 + 1) r for m = j + R1 r.
 };
 
+// Shared-memory wavefronts of the column pass's four exchange accesses for a
+// per-column stride MP (8-byte elements, thread tid = t C + c, each half-warp
+// one request): forward write t R1 + s, forward read t + R1 r (t < R1),
+// inverse write t (R2 + 1) + s (t < R1), inverse read t + (R2 + 1) r (t < R2).
+constexpr int cols_exchange_wavefronts(int C, int R1, int R2, int threads, int MP) {
+  int total = 0;
+  for (int h = 0; h < threads / 16; ++h) {
+    for (int pat = 0; pat < 4; ++pat) {
+      int addr[16] = {}, n = 0;
+      for (int L = 0; L < 16; ++L) {
+        const int tid = 16 * h + L, c = tid % C, t = tid / C;
+        const int tmax = (pat == 1 || pat == 2) ? R1 : R2;
+        if (t >= tmax) continue;
+        const int stride = pat == 0 ? R1 : (pat == 2 ? R2 + 1 : 1);
+        const int a = c * MP + t * stride;
+        bool seen = false;
+        for (int k = 0; k < n; ++k) seen = seen || addr[k] == a;
+        if (!seen) addr[n++] = a;
+      }
+      int worst = 0;
+      for (int b = 0; b < 16; ++b) {
+        int cnt = 0;
+        for (int k = 0; k < n; ++k) cnt += ((addr[k] % 16) == b) ? 1 : 0;
+        worst = cnt > worst ? cnt : worst;
+      }
+      total += worst;
+    }
+  }
+  return total;
+}
+// the smallest stride >= lo with the fewest wavefronts among the next 32
+constexpr int cols_exchange_stride(int C, int R1, int R2, int threads, int lo) {
+  int best = lo, bw = cols_exchange_wavefronts(C, R1, R2, threads, lo);
+  for (int mp = lo + 1; mp < lo + 32; ++mp) {
+    const int w = cols_exchange_wavefronts(C, R1, R2, threads, mp);
+    if (w < bw) { bw = w; best = mp; }
+  }
+  return best;
+}
+
 template <int M_, int R1_, int R2_, int C_>
 struct ColShape {
   static constexpr int M = M_, R1 = R1_, R2 = R2_, C = C_;
   static constexpr int T = R2;             // threads per column
-  static constexpr int MP = M + M / R2;    // padded column buffer
-  static constexpr int OS = C + 1;         // row stride of the output transpose tile [M][OS]
-  static constexpr int WORK = (C * MP > M * OS) ? C * MP : M * OS;
-  static constexpr int TWF_STRIDE = (R2 % 2 == 0) ? R2 + 1 : R2;
-  static constexpr int TWI_STRIDE = (R1 % 2 == 0) ? R1 + 1 : R1;
   static constexpr int THREADS = ((C * T + 31) / 32) * 32;
   static constexpr int MINB = (THREADS <= 256) ? 2 : 1;  // blocks per SM the registers must allow
   static_assert(R1 <= R2, "column schedule needs R1 <= R2");
+  static_assert(C <= 32, "the u[0,0] partial of a block is gathered in one warp");
+  // per-column exchange stride: the inverse exchange keeps one spare slot every
+  // R2 elements (t (R2 + 1) + s, t + (R2 + 1) r), so it needs M + R1 - 1
+  static constexpr int MP = cols_exchange_stride(C, R1, R2, THREADS, M + R1 - 1);
+  static constexpr int TWF_STRIDE = (R2 % 2 == 0) ? R2 + 1 : R2;
+  static constexpr int TWI_STRIDE = (R1 % 2 == 0) ? R1 + 1 : R1;
   static constexpr int GS = ((M + 3) / 4) * 4;  // floats per staged Green column (16-byte multiple)
-  // one float2 of padding keeps the exchange buffer 16-byte aligned (bulk copy destination)
-  static constexpr int BUF_PAD = ((C * GS * 4 + (R1 * TWF_STRIDE + R2 * TWI_STRIDE) * 8) % 16) ? 1 : 0;
   static constexpr size_t smem_bytes() {
-    return (size_t)C * GS * sizeof(float) +
-           (size_t)(R1 * TWF_STRIDE + R2 * TWI_STRIDE + BUF_PAD + WORK) * sizeof(float2) + C * sizeof(double);
+    return (size_t)C * GS * sizeof(float) + (size_t)(R1 * TWF_STRIDE + R2 * TWI_STRIDE + C * MP) * sizeof(float2);
   }
-  // The inverse exchange keeps one spare slot every R2 elements (element m at
-  // m + m / R2); the kernel uses the closed forms t (R2 + 1) + s and t + (R2 + 1) r.
 };
 
 // ---------------------------------------------------------------------------
@@ -597,38 +633,43 @@ __global__ void __launch_bounds__(S::THREADS, 2) k_fast_rows_fwd_div(const T* __
 }
 
 // ---------------------------------------------------------------------------
-// pass B: column transform, Green multiply, inverse column transform; one
-// block per (field, block of C columns). The block's Green columns and its C
-// spectrum columns (contiguous in the column-major layout) arrive as two bulk
-// copies while the twiddle tables are built.
+// pass B: column transform, Green multiply, inverse column transform, over
+// items (field, block of C columns); persistent. Thread tid = t C + c works on
+// column c of the block, so a warp's loads and stores cover whole 32-byte
+// sectors of C neighbouring columns: the spectrum columns are read straight
+// into registers (the next item's columns are prefetched into L2 meanwhile)
+// and the result rows p .. p+H-1 (adjoint: p .. p+H) are written row-major
+// straight from registers. The block's Green columns arrive by bulk copy,
+// issued one item ahead.
 // ---------------------------------------------------------------------------
 template <class S, int MODE>
 __global__ void __launch_bounds__(S::THREADS, S::MINB) k_fast_cols(const float2* __restrict__ spec, float2* __restrict__ Y,
                                                           const float* __restrict__ GT, const float2* __restrict__ twg,
                                                           float* __restrict__ partial, FastArgs A) {
   extern __shared__ __align__(16) float2 sm[];
-  float* gsm = reinterpret_cast<float*>(sm);            // [C][GS] this block's Green columns
-  float2* twF = reinterpret_cast<float2*>(gsm + S::C * S::GS);  // [R1][TWF_STRIDE]: w_M^(r j), j < R1, r < R2
-  float2* twI = twF + S::R1 * S::TWF_STRIDE;            // [R2][TWI_STRIDE]: w_M^(r j), j < R2, r < R1
-  float2* buf = twI + S::R2 * S::TWI_STRIDE + S::BUF_PAD;  // staged columns [C][ldM], then [C][MP]
-  double* colval = reinterpret_cast<double*>(buf + S::WORK);  // [C] row-0 contributions
-  const int tid = threadIdx.x;
-  const int c = tid / S::T, t = tid - c * S::T;
-  const int field = blockIdx.y, blk = blockIdx.x;
-  const int l = blk * S::C + c;
-  const bool act = (c < S::C) && (l < A.Nh);
-  // this block's Green columns and spectrum columns arrive as two bulk copies
+  float* gsm = reinterpret_cast<float*>(sm);                       // [C][GS] Green columns of the item
+  float2* twF = reinterpret_cast<float2*>(gsm + S::C * S::GS);     // [R1][TWF_STRIDE]: w_M^(r j), j < R1, r < R2
+  float2* twI = twF + S::R1 * S::TWF_STRIDE;                       // [R2][TWI_STRIDE]: w_M^(r j), j < R2, r < R1
+  float2* xbuf = twI + S::R2 * S::TWI_STRIDE;                      // [C][MP] exchange
   __shared__ __align__(8) uint64_t bar;
-  if (tid == 0) {
-    const int ncol = (A.Nh - blk * S::C) < S::C ? (A.Nh - blk * S::C) : S::C;
-    const unsigned gb = (unsigned)(ncol * A.ldM * sizeof(float)), xb = (unsigned)(ncol * A.ldM * sizeof(float2));
-    mbar_init(&bar, 1);
-    mbar_expect_tx(&bar, gb + xb);
-    bulk_copy(gsm, GT + (size_t)blk * S::C * A.ldM, gb, &bar);
-    bulk_copy(buf, spec + ((size_t)field * A.Nh + (size_t)blk * S::C) * A.ldM, xb, &bar);
-  }
-  const float* gcol = gsm + (c < S::C ? c : 0) * S::GS;
-  float2* mybuf = buf + (c < S::C ? c : 0) * S::MP;
+  const int tid = threadIdx.x;
+  const int c = tid % S::C, t = tid / S::C;
+  const bool act = t < S::R2, act2 = t < S::R1;
+  const int items = A.nf * A.nparts;
+  const int yrows = (MODE == 2) ? A.H + 1 : A.H;
+  float2* mybuf = xbuf + c * S::MP;
+  const float* gcol = gsm + c * S::GS;
+  auto ncols_of = [&](int blk) { return (A.Nh - blk * S::C) < S::C ? (A.Nh - blk * S::C) : S::C; };
+  auto issue_green = [&](int w) {  // one thread
+    const int blk = w % A.nparts;
+    const unsigned gb = (unsigned)(ncols_of(blk) * A.ldM * sizeof(float));
+    bulk_load(gsm, GT + (size_t)blk * S::C * A.ldM, gb, &bar);
+  };
+  auto prefetch_spec = [&](int w) {  // one thread: the item's spectrum columns into L2
+    const int field = w / A.nparts, blk = w - field * A.nparts;
+    l2_prefetch(spec + ((size_t)field * A.Nh + (size_t)blk * S::C) * A.ldM,
+                (unsigned)(ncols_of(blk) * A.ldM * sizeof(float2)));
+  };
   for (int i = tid; i < S::R1 * S::R2; i += blockDim.x) {
     const int j = i / S::R2, r = i - j * S::R2;
     twF[j * S::TWF_STRIDE + r] = twg[r * j];
@@ -637,105 +678,99 @@ __global__ void __launch_bounds__(S::THREADS, S::MINB) k_fast_cols(const float2*
     const int j = i / S::R1, r = i - j * S::R1;
     twI[j * S::TWI_STRIDE + r] = twg[r * j];
   }
+  if (tid == 0) {
+    mbar_init(&bar, 1);
+    if ((int)blockIdx.x < items) issue_green(blockIdx.x);
+  }
   __syncthreads();  // barrier initialised, twiddles in place
-  const bool landed = mbar_wait(&bar, 0);
-  if (__syncthreads_or(!landed)) {  // the copies never completed: report, let them drain, stop
-    if (tid == 0) atomicExch(A.err, kErrBulkWait);
-    mbar_wait(&bar, 0);
-    return;
-  }
-  // rows outside the support were zeroed by the row pass
-  float2 v[S::R1];
-  {
-    const float2* colS = buf + (size_t)(act ? c : 0) * A.ldM;
+  unsigned phase = 0;
+#pragma unroll 1
+  for (int w = blockIdx.x; w < items; w += gridDim.x, phase ^= 1u) {
+    const int field = w / A.nparts, blk = w - field * A.nparts;
+    const int l = blk * S::C + c;
+    const bool colok = l < A.Nh;
+    if (tid == 0 && w + (int)gridDim.x < items) prefetch_spec(w + gridDim.x);
+    // rows outside the support were zeroed by the row pass
+    float2 v[S::R1];
+    {
+      const float2* col = spec + ((size_t)field * A.Nh + (colok ? l : 0)) * A.ldM;
 #pragma unroll
-    for (int r = 0; r < S::R1; ++r) v[r] = colS[t + S::R2 * r];
-  }
-  __syncthreads();  // every staged column read: buf becomes the exchange buffer
-  if (MODE == 2) {
-    // adjoint: z = Crop^T(grad_out) - (sum grad_out) e_00; the row DFT of the
-    // second term is -sum in every column, at torus row 0. The sum is reduced
-    // in a fixed order from the per-row-pair FP64 sums of the packing pass.
-    __shared__ double tot_s;
-    if (tid < 32) {
-      const double* pp = reinterpret_cast<const double*>(partial) + (size_t)field * (kMaxRowBlocks / 2);
-      double a = 0.0;
-      for (int i = tid; i < A.zpairs; i += 32) a += pp[i];
+      for (int r = 0; r < S::R1; ++r) v[r] = (act && colok) ? col[t + S::R2 * r] : make_float2(0.0f, 0.0f);
+    }
+    if (MODE == 2) {
+      // adjoint: z = Crop^T(grad_out) - (sum grad_out) e_00; the row DFT of the
+      // second term is -sum in every column, at torus row 0. The sum is reduced
+      // in a fixed order from the per-row-pair FP64 sums of the packing pass;
+      // the threads with t = 0 are lanes 0 .. C-1 of warp 0.
+      if (tid < 32) {
+        const double* pp = reinterpret_cast<const double*>(partial) + (size_t)field * (kMaxRowBlocks / 2);
+        double a = 0.0;
+        for (int i = tid; i < A.zpairs; i += 32) a += pp[i];
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-      if (tid == 0) tot_s = a;
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+        if (t == 0) v[0] = make_float2((float)(-a), 0.0f);
+      }
+    }
+    if (act) dft_reg<S::R1, -1>(v);
+    __syncthreads();  // the previous item's reads of the exchange are done
+    if (act) {
+#pragma unroll
+      for (int s2 = 0; s2 < S::R1; ++s2) mybuf[t * S::R1 + s2] = v[s2];
     }
     __syncthreads();
-    if (t == 0) v[0] = make_float2((float)(-tot_s), 0.0f);
-  }
-  if (act) {
-    dft_reg<S::R1, -1>(v);
+    float2 u[S::R2];
+    if (act2) {
+      u[0] = mybuf[t];
 #pragma unroll
-    for (int s2 = 0; s2 < S::R1; ++s2) mybuf[t * S::R1 + s2] = v[s2];
-  }
-  __syncthreads();
-  float2 u[S::R2];
-  const bool act2 = act && t < S::R1;
-  if (act2) {
-    u[0] = mybuf[t];
+      for (int r = 1; r < S::R2; ++r) u[r] = cmul(mybuf[t + S::R1 * r], twF[t * S::TWF_STRIDE + r]);
+      dft_reg<S::R2, -1>(u);
+    }
+    const bool landed = mbar_wait(&bar, phase);
+    if (act2) {
+      // bins k = t + R1 s: multiply by the real Green spectrum (Eq. 23)
 #pragma unroll
-    for (int r = 1; r < S::R2; ++r) u[r] = cmul(mybuf[t + S::R1 * r], twF[t * S::TWF_STRIDE + r]);
-    dft_reg<S::R2, -1>(u);
-    // bins k = t + R1 s: multiply by the real Green spectrum (Eq. 23)
+      for (int s2 = 0; s2 < S::R2; ++s2) u[s2] = cscale(u[s2], gcol[t + S::R1 * s2]);
+      // inverse stage 1 (span 1): butterfly t takes exactly the bins t + R1 r held here
+      dft_reg<S::R2, +1>(u);
+    }
+    fence_proxy_async_smem();  // this thread's reads of the Green columns precede the next bulk copy
+    if (__syncthreads_or(!landed)) {  // the copy never completed: report, let it drain, stop
+      if (tid == 0) atomicExch(A.err, kErrBulkWait);
+      mbar_wait(&bar, phase);
+      return;
+    }
+    if (tid == 0 && w + (int)gridDim.x < items) issue_green(w + gridDim.x);
+    if (act2) {
 #pragma unroll
-    for (int s2 = 0; s2 < S::R2; ++s2) u[s2] = cscale(u[s2], gcol[t + S::R1 * s2]);
-    // inverse stage 1 (span 1): butterfly t takes exactly the bins t + R1 r held here
-    dft_reg<S::R2, +1>(u);
-  }
-  __syncthreads();
-  if (act2) {
+      for (int s2 = 0; s2 < S::R2; ++s2) mybuf[t * (S::R2 + 1) + s2] = u[s2];  // pad(t R2 + s2), s2 < R2
+    }
+    __syncthreads();
+    if (act) {
+      // pad(t + R2 r) = t + (R2 + 1) r for t < R2
+      v[0] = mybuf[t];
 #pragma unroll
-    for (int s2 = 0; s2 < S::R2; ++s2) mybuf[t * (S::R2 + 1) + s2] = u[s2];  // pad(t R2 + s2), s2 < R2
-  }
-  __syncthreads();
-  if (act) {
-    // pad(t + R2 r) = t + (R2 + 1) r for t < R2
-    v[0] = mybuf[t];
+      for (int r = 1; r < S::R1; ++r) v[r] = cmul(mybuf[t + (S::R2 + 1) * r], cconj(twI[t * S::TWI_STRIDE + r]));
+      dft_reg<S::R1, +1>(v);
+    }
+    if (MODE != 2 && tid < 32) {
+      // u[0,0] = sum over the row-0 spectrum, weight 1 at l = 0 and N/2, 2
+      // elsewhere; FP64, columns added in order (an error in u[0,0] shifts
+      // every output pixel)
+      const double cv = (tid < S::C && colok) ? ((l == 0 || 2 * l == A.N) ? (double)v[0].x : 2.0 * (double)v[0].x)
+                                              : 0.0;
+      double s2 = 0.0;
 #pragma unroll
-    for (int r = 1; r < S::R1; ++r) v[r] = cmul(mybuf[t + (S::R2 + 1) * r], cconj(twI[t * S::TWI_STRIDE + r]));
-    dft_reg<S::R1, +1>(v);
-    // u[0,0] = sum over the row-0 spectrum, weight 1 at l = 0 and N/2, 2 elsewhere
-    if (MODE != 2 && t == 0) colval[c] = (l == 0 || 2 * l == A.N) ? (double)v[0].x : 2.0 * (double)v[0].x;
-  }
-  __syncthreads();  // everyone is done reading buf: reuse it as the [M][OS] transpose tile
-  if (act) {
+      for (int cc = 0; cc < S::C; ++cc) s2 += __shfl_sync(0xffffffffu, cv, cc);
+      if (tid == 0) reinterpret_cast<double*>(partial)[(size_t)field * (kMaxRowBlocks / 2) + blk] = s2;
+    }
+    if (act && colok) {
+      float2* Yc = Y + (size_t)field * yrows * A.ldY + l;
 #pragma unroll
-    for (int s2 = 0; s2 < S::R1; ++s2) buf[(t + S::R2 * s2) * S::OS + c] = v[s2];
-  }
-  __syncthreads();
-  {
-    // rows p .. p+H-1 (adjoint: p .. p+H) of this block's columns, C consecutive
-    // complex per row segment
-    const int ncol = (A.Nh - blk * S::C) < S::C ? (A.Nh - blk * S::C) : S::C;
-    const int yrows = (MODE == 2) ? A.H + 1 : A.H;
-    float2* Yf = Y + (size_t)field * yrows * A.ldY + blk * S::C;
-    if constexpr (S::THREADS % S::C == 0) {
-      // every thread keeps one column and steps over rows
-      constexpr int RSTEP = S::THREADS / S::C;
-      const int cc = tid % S::C;
-      if (cc < ncol) {
-        const float2* src = buf + (A.p + tid / S::C) * S::OS + cc;
-        float2* dst = Yf + (size_t)(tid / S::C) * A.ldY + cc;
-        for (int i = tid / S::C; i < yrows; i += RSTEP, src += RSTEP * S::OS, dst += (size_t)RSTEP * A.ldY) *dst = *src;
-      }
-    } else {
-      for (int idx = tid; idx < yrows * S::C; idx += blockDim.x) {
-        const int i = idx / S::C, cc = idx - i * S::C;
-        if (cc < ncol) Yf[(size_t)i * A.ldY + cc] = buf[(A.p + i) * S::OS + cc];
+      for (int r = 0; r < S::R1; ++r) {
+        const int i = t + S::R2 * r - A.p;  // image row of torus row t + R2 r
+        if (i >= 0 && i < yrows) Yc[(size_t)i * A.ldY] = v[r];
       }
     }
-  }
-  if (MODE != 2 && tid == 0) {
-    // FP64 accumulation: an error in u[0,0] shifts every output pixel
-    double s2 = 0.0;
-    for (int cc = 0; cc < S::C; ++cc)
-      if (blk * S::C + cc < A.Nh) s2 += colval[cc];
-    reinterpret_cast<double*>(partial)[(size_t)field * (kMaxRowBlocks / 2) + blk] = s2;
   }
 }
 
@@ -1018,14 +1053,14 @@ static cudaError_t run_fast_mode(gfc_plan* P, const Bufs& bf, const T* in0, cons
   // the row passes stage their F packed rows / 2F rows of Y in the exchange buffer
   if ((size_t)2 * RS::F * A.ldY > (size_t)RS::F * RS::NP || A.ldz > RS::NP) return cudaErrorInvalidConfiguration;
   static std::mutex mu;
-  static int slots_a = 0, slots_c = 0, slots_d = 0;
+  static int slots_a = 0, slots_b = 0, slots_c = 0, slots_d = 0;
   cudaError_t e;
   {
     std::lock_guard<std::mutex> lock(mu);
     if (!slots_a) {
       int unused = 0;
       if ((e = fast_setup(k_fast_div<T, MODE>, 512, 0, &unused)) != cudaSuccess) return e;
-      if ((e = fast_setup(k_fast_cols<CS, MODE>, CS::THREADS, CS::smem_bytes(), &unused)) != cudaSuccess) return e;
+      if ((e = fast_setup(k_fast_cols<CS, MODE>, CS::THREADS, CS::smem_bytes(), &slots_b)) != cudaSuccess) return e;
       if (MODE == 2) {
         if ((e = fast_setup(k_fast_rows_adj<RS, T>, RS::THREADS, RS::smem_bytes(), &slots_c)) != cudaSuccess) return e;
       } else {
@@ -1075,8 +1110,8 @@ static cudaError_t run_fast_mode(gfc_plan* P, const Bufs& bf, const T* in0, cons
   }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   prof_begin(P, 1, st);
-  k_fast_cols<CS, MODE><<<dim3(A.nparts, nf), CS::THREADS, CS::smem_bytes(), st>>>(bf.spec, bf.zbuf, P->GT, P->twM,
-                                                                                     bf.partial, A);
+  k_fast_cols<CS, MODE><<<grid_for((long)nf * A.nparts, slots_b), CS::THREADS, CS::smem_bytes(), st>>>(
+      bf.spec, bf.zbuf, P->GT, P->twM, bf.partial, A);
   prof_end(P, st);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   FastArgs C = A;

@@ -60,6 +60,12 @@ __device__ __forceinline__ void bulk_load(void* dst_smem, const void* src_gmem, 
   bulk_copy(dst_smem, src_gmem, bytes, bar);
 }
 
+// start fetching `bytes` (a multiple of 16) of global memory at a 16-byte
+// aligned address into L2; nothing waits for it
+__device__ __forceinline__ void l2_prefetch(const void* src_gmem, unsigned bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(src_gmem), "r"(bytes) : "memory");
+}
+
 // wait until the barrier's phase `parity` has completed; false if the time
 // bound ran out
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity,
