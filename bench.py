@@ -437,7 +437,51 @@ def extra_workloads(dev):
     res["edit_100x801x1200_fp32"] = _edit_workload(dev)
     res["exact_809x1208_100x801x1200_fp32"] = _exact_workload(dev)
     res["backward_100x801x1200_fp32"] = _backward_workload(dev)
+    res["cufft_comparison_100x801x1200_fp32"] = _cufft_comparison(dev)
     return res
+
+
+def _cufft_comparison(dev):
+    """The same solve written with torch.fft (cuFFT) on this GPU, for comparison only:
+    divergence (Eq. 3) on the zero-padded 810x1250 torus, rfft2, multiply by the
+    Green spectrum 1/lambda (Eq. 23; irfft2 carries the 1/(MN)), irfft2, subtract
+    u[0,0], crop. Not a path of the library."""
+    import torch
+
+    from paper_1902_00176_gb300 import gfc, synth
+
+    B, H, W = 100, 801, 1200
+    gx, gy = synth.perturbed_gradient_batch(batch=B, H=H, W=W, seed=1001)
+    tx = torch.from_numpy(gx).to(dev).view(B, H, W)
+    ty = torch.from_numpy(gy).to(dev).view(B, H, W)
+    del gx, gy
+    plan = gfc.Plan(H, W, 1, B, device=dev)
+    M, N, p = plan.M, plan.N, plan.pad
+    k = torch.arange(M, dtype=torch.float64, device=dev).view(M, 1)
+    l = torch.arange(N // 2 + 1, dtype=torch.float64, device=dev).view(1, -1)
+    lam = -4.0 * (torch.sin(torch.pi * k / M) ** 2 + torch.sin(torch.pi * l / N) ** 2)
+    lam[0, 0] = 1.0
+    G = (1.0 / lam).float()
+    G[0, 0] = 0.0
+    L = torch.zeros(B, M, N, device=dev)
+
+    def solve():
+        L.zero_()
+        L[:, p:p + H, p:p + W] += tx
+        L[:, p:p + H, p + 1:p + W + 1] -= tx
+        L[:, p:p + H, p:p + W] += ty
+        L[:, p + 1:p + H + 1, p:p + W] -= ty
+        u = torch.fft.irfft2(torch.fft.rfft2(L) * G, s=(M, N))
+        return u[:, p:p + H, p:p + W] - u[:, :1, :1]
+
+    ms = _time_ms(solve, dev, 5)
+    ref = solve()
+    out = plan.solve_from_gradient(tx.view(B, 1, H, W), ty.view(B, 1, H, W)).view(B, H, W)
+    ms_lib = _time_ms(lambda: plan.solve_from_gradient(tx.view(B, 1, H, W), ty.view(B, 1, H, W)), dev, 10)
+    rel = float(torch.linalg.vector_norm(out - ref) / torch.linalg.vector_norm(ref))
+    plan.close()
+    return {"ms_per_batch_cufft": ms, "solves_per_s_cufft": B * 1000.0 / ms, "ms_per_batch_library": ms_lib,
+            "speedup_vs_cufft": ms / ms_lib, "rel_l2_library_vs_cufft": rel}
 
 
 def _backward_workload(dev):
