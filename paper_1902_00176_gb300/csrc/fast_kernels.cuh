@@ -112,6 +112,14 @@ struct RowShape {
   static constexpr int WMIN = cx_min_width(N);
   static constexpr size_t smem_bytes() { return (size_t)(R1 * R2 + F * NP) * sizeof(float2); }
   static constexpr size_t smem_bytes_fwd() { return (size_t)(R1 * R2 + F * NP + F * NO) * sizeof(float2); }
+  // adjoint inverse row pass: twiddles, exchange, the factor table
+  // 1 - exp(2 pi i l / N) for l <= N/2, then (16-byte aligned) the F + 1 rows of
+  // Y an item needs, LDY complex each
+  static constexpr int LDY = ((N / 2 + 1) + 3) & ~3;
+  static constexpr size_t adj_stage_offset() {
+    return (((size_t)(R1 * R2 + F * NP + (N / 2 + 1)) * sizeof(float2)) + 15) / 16 * 16;
+  }
+  static constexpr size_t smem_bytes_adj() { return adj_stage_offset() + (size_t)(F + 1) * LDY * sizeof(float2); }
   // The exchange keeps one spare slot every R1 elements (element m at
   // m + m / R1, conflict-free stage-1 writes); the kernels use the closed forms
   // t (R1 + 1) + s for m = t R1 + s and j + (R1 + 1) r for m = j + R1 r.
@@ -491,6 +499,9 @@ __global__ void __launch_bounds__(S::THREADS, 2) k_fast_rows_fwd(const float2* _
 // arithmetic as pass L, so the packed rows never go through HBM. The rest is
 // k_fast_rows_fwd. The next item's rows are requested once this item's
 // spectrum is stored (the staging area spans both exchange buffers).
+// ADJ: the adjoint's first step instead, z = Crop^T(grad_out) from the 2F
+// staged rows of grad_out, with each row pair's FP64 sum written where pass B
+// reads it for the -(sum grad_out) e_00 term (as k_fast_div<T, 2>).
 // Requires W sizeof(T) to be a multiple of 16 and the staging to fit
 // (fused_div_fits).
 // ---------------------------------------------------------------------------
@@ -503,19 +514,21 @@ __host__ __device__ constexpr size_t fused_exchange_bytes() {
   return (size_t)(S::F * S::NP + S::F * S::NO) * sizeof(float2);
 }
 
-template <class S, typename T>
+template <class S, typename T, bool ADJ>
 __global__ void __launch_bounds__(S::THREADS, 2) k_fast_rows_fwd_div(const T* __restrict__ gx,
                                                                      const T* __restrict__ gy,
                                                                      float2* __restrict__ spec,
-                                                                     const float2* __restrict__ twg, FastArgs A) {
+                                                                     const float2* __restrict__ twg,
+                                                                     float* __restrict__ partial, FastArgs A) {
   extern __shared__ __align__(16) float2 sm[];
   float2* tw2 = sm;
   float2* buf = sm + S::R1 * S::R2;
   float2* buf2 = buf + S::F * S::NP;
   constexpr int RW = 2 * S::F;  // image rows per item
-  T* sgx = reinterpret_cast<T*>(buf);  // gx rows r0 .. r0 + RW - 1
+  T* sgx = reinterpret_cast<T*>(buf);  // gx rows (ADJ: grad_out rows) r0 .. r0 + RW - 1
   T* sgy = sgx + (size_t)RW * A.W;     // gy rows r0 - 1 .. r0 + RW - 1
   __shared__ __align__(8) uint64_t bar;
+  __shared__ double red[ADJ ? S::F * S::T : 1];  // ADJ: per-thread sums of the item's row pairs
   const int tid = threadIdx.x;
   const int f = tid / S::T, t = tid - f * S::T;
   const bool act = f < S::F;
@@ -535,10 +548,14 @@ __global__ void __launch_bounds__(S::THREADS, 2) k_fast_rows_fwd_div(const T* __
     const int nx = (A.H - r0) < RW ? (A.H - r0) : RW;             // gx rows r0 .. r0 + nx - 1 (nx may be 0)
     const int y0 = r0 > 0 ? r0 - 1 : 0, y1 = (A.H < r0 + RW) ? A.H : r0 + RW;  // gy rows y0 .. y1 - 1
     const unsigned row = (unsigned)(A.W * sizeof(T));
-    mbar_expect_tx(&bar, (unsigned)(nx > 0 ? nx : 0) * row + (unsigned)(y1 - y0) * row);
-    if (nx > 0) bulk_copy(sgx, gx + field * fe + (size_t)r0 * A.W, (unsigned)nx * row, &bar);
-    bulk_copy(sgy + (size_t)(y0 - (r0 - 1)) * A.W, gy + field * fe + (size_t)y0 * A.W, (unsigned)(y1 - y0) * row,
-              &bar);
+    if constexpr (ADJ) {
+      bulk_load(sgx, gx + field * fe + (size_t)r0 * A.W, (unsigned)nx * row, &bar);  // nx >= 1 here
+    } else {
+      mbar_expect_tx(&bar, (unsigned)(nx > 0 ? nx : 0) * row + (unsigned)(y1 - y0) * row);
+      if (nx > 0) bulk_copy(sgx, gx + field * fe + (size_t)r0 * A.W, (unsigned)nx * row, &bar);
+      bulk_copy(sgy + (size_t)(y0 - (r0 - 1)) * A.W, gy + field * fe + (size_t)y0 * A.W, (unsigned)(y1 - y0) * row,
+                &bar);
+    }
   };
   if (tid == 0) mbar_init(&bar, 1);
   __syncthreads();
@@ -554,7 +571,31 @@ __global__ void __launch_bounds__(S::THREADS, 2) k_fast_rows_fwd_div(const T* __
       return;
     }
     float2 v[S::R1];
-    if (act) {
+    if (ADJ && act) {
+      // z = Crop^T(grad_out): rows ia, ib at torus rows p + ia, p + ib, columns
+      // j < W at p + j; and the row pair's sum for the (sum grad_out) e_00 term,
+      // in FP32 over chunks of 10 values, then FP64
+      const int ia = g * RW + 2 * f, ib = ia + 1;
+      const bool ha = ia < A.H, hb = ib < A.H;
+      const T* xa = sgx + (size_t)(2 * f) * A.W;
+      const T* xb = xa + A.W;
+      double acc = 0.0;
+      float chunk = 0.0f;
+#pragma unroll
+      for (int r = 0; r < S::R1; ++r) {
+        const int j = t + S::R2 * r - kP;
+        const bool sure = (S::R2 * r >= kP) && (S::R2 * r + S::R2 - 1 - kP < S::WMIN);
+        const bool c1 = sure || (j >= 0 && j < A.W);
+        const float a = (ha && c1) ? f_to_f(xa[j]) : 0.0f, b = (hb && c1) ? f_to_f(xb[j]) : 0.0f;
+        v[r] = make_float2(a, b);
+        chunk += a + b;
+        if (r % 10 == 9 || r == S::R1 - 1) {
+          acc += (double)chunk;
+          chunk = 0.0f;
+        }
+      }
+      red[tid] = acc;
+    } else if (act) {
       const int r0 = g * RW, ia = r0 + 2 * f, ib = ia + 1;
       const bool ha = ia < A.H, hb = ib < A.H, hm = ia >= 1;  // rows present (ia - 1 < H always)
       const bool sa = ia < A.nrows, sb = ib < A.nrows;         // rows inside the support
@@ -580,6 +621,12 @@ __global__ void __launch_bounds__(S::THREADS, 2) k_fast_rows_fwd_div(const T* __
       }
     }
     __syncthreads();  // every staged row read: the buffers become the exchange buffers
+    if (ADJ && act && t == 0) {
+      // the row pair's FP64 sum, threads in order
+      double sp = 0.0;
+      for (int k = 0; k < S::T; ++k) sp += red[f * S::T + k];
+      reinterpret_cast<double*>(partial)[(size_t)field * (kMaxRowBlocks / 2) + g * S::F + f] = sp;
+    }
     if (act) {
       dft_reg<S::R1, -1>(v);
 #pragma unroll
@@ -925,28 +972,48 @@ __global__ void __launch_bounds__(S::THREADS, 3) k_fast_rows_inv(const float2* _
 // A + i B gives grad_gx in its real part and grad_gy in its imaginary part.
 // ---------------------------------------------------------------------------
 template <class S, typename T>
-__global__ void __launch_bounds__(S::THREADS) k_fast_rows_adj(const float2* __restrict__ Y, T* __restrict__ ggx,
-                                                              T* __restrict__ ggy, const float2* __restrict__ twg,
-                                                              FastArgs A) {
-  extern __shared__ float2 sm[];
-  float2* tw2 = sm;
-  float2* buf = sm + S::R1 * S::R2;
+__global__ void __launch_bounds__(S::THREADS, 2) k_fast_rows_adj(const float2* __restrict__ Y, T* __restrict__ ggx,
+                                                                 T* __restrict__ ggy, const float2* __restrict__ twg,
+                                                                 FastArgs A) {
+  extern __shared__ __align__(16) float2 sm[];
+  float2* tw2 = sm;                          // [R1][R2]: w_N^(r j)
+  float2* buf = sm + S::R1 * S::R2;          // [F][NP] exchange
+  float2* dtab = buf + S::F * S::NP;         // [N/2 + 1] 1 - exp(2 pi i l / N)
+  float2* stg = reinterpret_cast<float2*>(reinterpret_cast<char*>(sm) + S::adj_stage_offset());  // [F + 1][ldY]
+  __shared__ __align__(8) uint64_t bar;
   const int tid = threadIdx.x;
   const int f = tid / S::T, t = tid - f * S::T;
   const bool act = f < S::F;
+  const int half = S::N / 2;
   for (int i = tid; i < S::R1 * S::R2; i += blockDim.x) {
     const int j = i / S::R2, r = i - j * S::R2;
     tw2[i] = twg[r * j];
   }
+  for (int l = tid; l <= half; l += blockDim.x) {
+    // 1 - cos is formed as sin^2 / (1 + cos) where cos > 0, avoiding the
+    // cancellation near DC; the imaginary part is -sin
+    const float2 e = twg[l];
+    const float cs = e.x, sn = -e.y;
+    dtab[l] = make_float2((cs > 0.0f) ? __fdividef(sn * sn, 1.0f + cs) : 1.0f - cs, -sn);
+  }
   float2* mybuf = buf + (act ? f : 0) * S::NP;
-  const int half = S::N / 2;
   const int items = A.nf * A.ngroups;
+  auto issue = [&](int w) {  // one thread: rows gF .. gF + F of Y (fewer at the end of a field)
+    const int field = w / A.ngroups, g = w - field * A.ngroups;
+    const int r0 = g * S::F, nr = (A.H + 1 - r0) < S::F + 1 ? (A.H + 1 - r0) : S::F + 1;
+    bulk_load(stg, Y + ((size_t)field * (A.H + 1) + r0) * A.ldY, (unsigned)(nr * A.ldY * sizeof(float2)), &bar);
+  };
+  if (tid == 0) mbar_init(&bar, 1);
+  __syncthreads();
+  if (tid == 0 && (int)blockIdx.x < items) issue(blockIdx.x);
+  unsigned phase = 0;
 #pragma unroll 1
-  for (int w = blockIdx.x; w < items; w += gridDim.x) {
+  for (int w = blockIdx.x; w < items; w += gridDim.x, phase ^= 1u) {
     const int field = w / A.ngroups, g = w - field * A.ngroups;
     const int i = g * S::F + f;  // output row of this transform
     const bool vi = act && i < A.H;
-    const float2* y0 = Y + ((size_t)field * (A.H + 1) + (vi ? i : 0)) * A.ldY;
+    const bool landed = mbar_wait(&bar, phase);
+    const float2* y0 = stg + (size_t)(vi ? f : 0) * A.ldY;
     const float2* y1 = y0 + A.ldY;  // row i + 1 (Y holds H + 1 rows)
     float2 v[S::R1];
 #pragma unroll
@@ -963,18 +1030,20 @@ __global__ void __launch_bounds__(S::THREADS) k_fast_rows_adj(const float2* __re
         ya.y = 0.0f;
         yb.y = 0.0f;
       }
-      // d = 1 - exp(+2 pi i src / N) = (1 - cos, -sin); 1 - cos is formed as
-      // sin^2 / (1 + cos) where cos > 0, avoiding the cancellation near DC
-      const float2 e = twg[src];
-      const float cs = e.x, sn = -e.y;
-      const float dx = (cs > 0.0f) ? __fdividef(sn * sn, 1.0f + cs) : 1.0f - cs;
-      const float2 a = cmul(ya, make_float2(dx, -sn));
+      const float2 a = cmul(ya, dtab[src]);
       const float2 b = csub(ya, yb);
       v[r] = lo ? make_float2(a.x - b.y, a.y + b.x) : make_float2(a.x + b.y, b.x - a.y);
     }
-    if (act) dft_reg<S::R1, +1>(v);
-    __syncthreads();  // previous item's stage 2 done with buf
+    fence_proxy_async_smem();  // this thread's reads of the staged rows precede the next bulk copy
+    if (__syncthreads_or(!landed)) {  // the copy never completed: report, let it drain, stop
+      if (tid == 0) atomicExch(A.err, kErrBulkWait);
+      mbar_wait(&bar, phase);
+      return;
+    }
+    // every staged row read, and the previous item's stage 2 done with buf
+    if (tid == 0 && w + (int)gridDim.x < items) issue(w + gridDim.x);
     if (act) {
+      dft_reg<S::R1, +1>(v);
 #pragma unroll
       for (int s2 = 0; s2 < S::R1; ++s2) mybuf[t * (S::R1 + 1) + s2] = v[s2];
     }
@@ -1062,26 +1131,29 @@ static cudaError_t run_fast_mode(gfc_plan* P, const Bufs& bf, const T* in0, cons
       if ((e = fast_setup(k_fast_div<T, MODE>, 512, 0, &unused)) != cudaSuccess) return e;
       if ((e = fast_setup(k_fast_cols<CS, MODE>, CS::THREADS, CS::smem_bytes(), &slots_b)) != cudaSuccess) return e;
       if (MODE == 2) {
-        if ((e = fast_setup(k_fast_rows_adj<RS, T>, RS::THREADS, RS::smem_bytes(), &slots_c)) != cudaSuccess) return e;
+        if ((e = fast_setup(k_fast_rows_adj<RS, T>, RS::THREADS, RS::smem_bytes_adj(), &slots_c)) != cudaSuccess)
+          return e;
       } else {
         if ((e = fast_setup(k_fast_rows_inv<RS, T>, RS::THREADS, RS::smem_bytes(), &slots_c)) != cudaSuccess) return e;
       }
       if ((e = fast_setup(k_fast_rows_fwd<RS>, RS::THREADS, RS::smem_bytes_fwd(), &slots_a)) != cudaSuccess) return e;
-      if (MODE == 0 &&
-          (e = fast_setup(k_fast_rows_fwd_div<RS, T>, RS::THREADS, RS::smem_bytes_fwd(), &slots_d)) != cudaSuccess)
+      if (MODE != 1 && (e = fast_setup(k_fast_rows_fwd_div<RS, T, MODE == 2>, RS::THREADS, RS::smem_bytes_fwd(),
+                                       &slots_d)) != cudaSuccess)
         return e;
     }
   }
   auto grid_for = [](long items, int slots) { return (int)(items < slots ? items : slots); };
-  // plain gradient solves fold pass L into the row pass when the gradient rows
-  // can be bulk-copied and their staging fits the exchange buffers
-  const bool fused_div = MODE == 0 && !(ed && ed->kind != kEditNone) && (P->W * sizeof(T)) % 16 == 0 &&
-                         fused_stage_bytes<RS, T>(P->W) <= fused_exchange_bytes<RS>() &&
-                         getenv("GFC_UNFUSED_DIV") == nullptr;
+  // Plain gradient solves fold pass L into the row pass, and the adjoint folds
+  // its packing of grad_out (with the row-pair sums) into it, when the rows can
+  // be bulk-copied and their staging fits the exchange buffers.
+  const size_t stage = (MODE == 2) ? (size_t)2 * RS::F * P->W * sizeof(T) : fused_stage_bytes<RS, T>(P->W);
+  const bool fused_div = MODE != 1 && !(ed && ed->kind != kEditNone) && (P->W * sizeof(T)) % 16 == 0 &&
+                         stage <= fused_exchange_bytes<RS>() && getenv("GFC_UNFUSED_DIV") == nullptr;
   if (fused_div) {
     prof_begin(P, 0, st);
-    k_fast_rows_fwd_div<RS, T><<<grid_for((long)nf * A.ngroups, slots_d), RS::THREADS, RS::smem_bytes_fwd(), st>>>(
-        in0, in1, bf.spec, P->twN, A);
+    k_fast_rows_fwd_div<RS, T, MODE == 2>
+        <<<grid_for((long)nf * A.ngroups, slots_d), RS::THREADS, RS::smem_bytes_fwd(), st>>>(
+            in0, in1, bf.spec, P->twN, bf.partial, A);
     prof_end(P, st);
   }
   if (!fused_div) prof_begin(P, 3, st);
@@ -1118,7 +1190,7 @@ static cudaError_t run_fast_mode(gfc_plan* P, const Bufs& bf, const T* in0, cons
   prof_begin(P, 2, st);
   if (MODE == 2) {
     C.ngroups = (P->H + RS::F - 1) / RS::F;
-    k_fast_rows_adj<RS, T><<<grid_for((long)nf * C.ngroups, slots_c), RS::THREADS, RS::smem_bytes(), st>>>(
+    k_fast_rows_adj<RS, T><<<grid_for((long)nf * C.ngroups, slots_c), RS::THREADS, RS::smem_bytes_adj(), st>>>(
         bf.zbuf, out0, out1, P->twN, C);
   } else {
     C.ngroups = ((P->H + 1) / 2 + RS::F - 1) / RS::F;
