@@ -412,6 +412,36 @@ def test_fused_divergence_row_pass_matches_separate_passes(H, W, dt, monkeypatch
     p.close()
 
 
+@pytest.mark.parametrize("H,W,dt", [(801, 1200, torch.float32), (64, 96, torch.bfloat16), (256, 256, torch.float32)])
+def test_fused_adjoint_packing_matches_separate_passes(H, W, dt, monkeypatch):
+    """The adjoint's packing of grad_out folded into the row pass against the
+    separate packing pass. Only the order of the row-pair sums differs; with
+    N(0,1) upstream gradients that sum is large and its round-off reaches the
+    output through the most amplified Green bins (the FP32 conditioning limit of
+    white-noise inputs), so both paths are held to the oracle with the bound used
+    for a plain FP32 adjoint, and to each other within that bound."""
+    gout = synth.upstream_gradient((2, 1, H, W), seed=8200)
+    p = gfc.Plan(H, W, 1, 2, dtype=dt, device=DEV)
+    tg = _to_dev(gout, dt)
+    fx, fy = torch.empty_like(tg), torch.empty_like(tg)
+    p.backward(tg, fx, fy)
+    monkeypatch.setenv("GFC_UNFUSED_DIV", "1")
+    sx, sy = torch.empty_like(tg), torch.empty_like(tg)
+    p.backward(tg, sx, sy)
+    monkeypatch.delenv("GFC_UNFUSED_DIV")
+    g0 = _np(tg)[0, 0].astype(np.float64)
+    rx, ry = O.backward(g0, p.M, p.N, p.pad)
+    if dt == torch.float32:
+        tx_, ty_ = _torch_fp32_adjoint(g0.astype(np.float32), p.M, p.N, p.pad)
+        bx, by = max(REL_F32, 3.0 * _rel(tx_, rx)), max(REL_F32, 3.0 * _rel(ty_, ry))
+    else:
+        bx = by = REL_16
+    for ox, oy in ((fx, fy), (sx, sy)):
+        assert _rel(_np(ox)[0, 0], rx) <= bx and _rel(_np(oy)[0, 0], ry) <= by
+    assert _rel(_np(fx), _np(sx)) <= bx and _rel(_np(fy), _np(sy)) <= by
+    p.close()
+
+
 def test_bounded_wait_reports_timeout_and_context_survives():
     """A device wait that nothing completes runs out after its limit and is
     reported as GFC_ERR_TIMEOUT by the next sync; later solves still work."""
