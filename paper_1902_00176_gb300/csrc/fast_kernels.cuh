@@ -4,15 +4,18 @@
 // (fast_<M>x<N>.cu) so the library builds in parallel.
 //
 // Hand-offs between the passes:
-//   pass L  writes the packed rows z[pair][j] = L[2 pair][j] + i L[2 pair+1][j]
-//   pass A  reads z, writes the row spectrum column-major, spec[l][r] (l < N/2+1
-//           Hermitian columns), one 2F-row column segment at a time: the
-//           transpose is folded into the two-for-one split it does through
-//           shared memory anyway;
+//   pass L  (edited solves, Laplacian input, or rows too wide to stage) writes
+//           the packed rows z[pair][j] = L[2 pair][j] + i L[2 pair+1][j];
+//   pass A  stages the gradient rows of an item by bulk copy and forms L itself
+//           (or stages z, or the adjoint's grad_out rows), and writes the row
+//           spectrum column-major, spec[l][r] (l < N/2+1 Hermitian columns), one
+//           2F-row column segment at a time: the transpose is folded into the
+//           two-for-one split it does through shared memory anyway;
 //   pass B  loads whole columns of spec straight into registers and writes its
-//           result row-major, Y[i][l] (image rows i < H), straight from
-//           registers, into the buffer that held z;
-//   pass C  loads rows of Y straight into registers.
+//           result row-major, Y[i][l] (image rows i < H; H + 1 for the
+//           adjoint), straight from registers, into the buffer that held z;
+//   pass C  stages the rows of Y an item needs by bulk copy (the adjoint's
+//           inverse row pass likewise) and writes the cropped output.
 //
 // Row transforms (length N = R1 R2, T = R2 threads per transform, F transforms
 // per block): stage 1 is one radix-R1 DFT per thread on x[t + R2 r]; one
