@@ -692,6 +692,19 @@ __global__ void __launch_bounds__(S::THREADS, 2) k_fast_rows_fwd_div(const T* __
 // straight from registers. The block's Green columns arrive by bulk copy,
 // issued one item ahead.
 // ---------------------------------------------------------------------------
+// adjoint: sum(grad_out) of each field from its row-pair FP64 sums, lane-strided
+// then a fixed shuffle tree (the same order on every call), into the field's
+// slot kAdjTotal for the column pass; one warp per field
+constexpr int kAdjTotal = kMaxRowBlocks / 2 - 1;
+static __global__ void __launch_bounds__(32) k_adj_total(double* __restrict__ partial, int zpairs) {
+  double* pp = partial + (size_t)blockIdx.x * (kMaxRowBlocks / 2);
+  double a = 0.0;
+  for (int i = threadIdx.x; i < zpairs; i += 32) a += pp[i];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+  if (threadIdx.x == 0) pp[kAdjTotal] = a;
+}
+
 template <class S, int MODE>
 __global__ void __launch_bounds__(S::THREADS, S::MINB) k_fast_cols(const float2* __restrict__ spec, float2* __restrict__ Y,
                                                           const float* __restrict__ GT, const float2* __restrict__ twg,
@@ -749,16 +762,11 @@ __global__ void __launch_bounds__(S::THREADS, S::MINB) k_fast_cols(const float2*
     }
     if (MODE == 2) {
       // adjoint: z = Crop^T(grad_out) - (sum grad_out) e_00; the row DFT of the
-      // second term is -sum in every column, at torus row 0. The sum is reduced
-      // in a fixed order from the per-row-pair FP64 sums of the packing pass;
-      // the threads with t = 0 are lanes 0 .. C-1 of warp 0.
-      if (tid < 32) {
-        const double* pp = reinterpret_cast<const double*>(partial) + (size_t)field * (kMaxRowBlocks / 2);
-        double a = 0.0;
-        for (int i = tid; i < A.zpairs; i += 32) a += pp[i];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-        if (t == 0) v[0] = make_float2((float)(-a), 0.0f);
+      // second term is -sum in every column, at torus row 0 (the sum from
+      // k_adj_total); the threads with t = 0 are lanes 0 .. C-1 of warp 0.
+      if (t == 0) {
+        const double a = reinterpret_cast<const double*>(partial)[(size_t)field * (kMaxRowBlocks / 2) + kAdjTotal];
+        v[0] = make_float2((float)(-a), 0.0f);
       }
     }
     if (act) dft_reg<S::R1, -1>(v);
@@ -1123,7 +1131,8 @@ static cudaError_t run_fast_mode(gfc_plan* P, const Bufs& bf, const T* in0, cons
   A.ldY = (P->Nh + 3) & ~3;
   A.err = P->dev_err;
   // the row passes stage their F packed rows / 2F rows of Y in the exchange buffer
-  if ((size_t)2 * RS::F * A.ldY > (size_t)RS::F * RS::NP || A.ldz > RS::NP) return cudaErrorInvalidConfiguration;
+  if ((size_t)2 * RS::F * A.ldY > (size_t)RS::F * RS::NP || A.ldz > RS::NP || A.zpairs > kAdjTotal)
+    return cudaErrorInvalidConfiguration;
   static std::mutex mu;
   static int slots_a = 0, slots_b = 0, slots_c = 0, slots_d = 0;
   cudaError_t e;
@@ -1185,6 +1194,7 @@ static cudaError_t run_fast_mode(gfc_plan* P, const Bufs& bf, const T* in0, cons
   }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   prof_begin(P, 1, st);
+  if (MODE == 2) k_adj_total<<<nf, 32, 0, st>>>(reinterpret_cast<double*>(bf.partial), A.zpairs);
   k_fast_cols<CS, MODE><<<grid_for((long)nf * A.nparts, slots_b), CS::THREADS, CS::smem_bytes(), st>>>(
       bf.spec, bf.zbuf, P->GT, P->twM, bf.partial, A);
   prof_end(P, st);
