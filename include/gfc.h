@@ -99,7 +99,15 @@ gfc_status gfc_padded_size(int H, int W, int pad, int size_policy, int* M, int* 
  * time). Synchronous. On success *plan owns device memory until gfc_destroy. */
 gfc_status gfc_plan_create(gfc_plan** plan, int H, int W, int C, int batch, gfc_dtype dtype);
 
-/* As gfc_plan_create, with the options above. */
+/* As gfc_plan_create, with the options above.
+ *
+ * Two environment variables select equivalent paths, for comparisons (both
+ * give results within FP32 rounding of the default; nothing is skipped):
+ *   GFC_FORCE_GENERIC (read at plan creation): the shared-memory Stockham
+ *     passes instead of the register-resident ones for every size;
+ *   GFC_UNFUSED_DIV (read at each call): the divergence of the gradient, or the
+ *     adjoint's packing of grad_out, as its own pass before the row transforms
+ *     instead of inside them (bit-identical for the forward solve). */
 gfc_status gfc_plan_create_ex(gfc_plan** plan, const gfc_plan_opts* opts);
 
 /* Create a plan for a ragged batch of n items of different sizes (each field
