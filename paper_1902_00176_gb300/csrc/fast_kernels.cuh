@@ -115,6 +115,10 @@ struct RowShape {
   static constexpr int WMIN = cx_min_width(N);
   static constexpr size_t smem_bytes() { return (size_t)(R1 * R2 + F * NP) * sizeof(float2); }
   static constexpr size_t smem_bytes_fwd() { return (size_t)(R1 * R2 + F * NP + F * NO) * sizeof(float2); }
+  // blocks per SM the register allocation must allow: long rows fill shared
+  // memory at 2 (3 for the inverse pass); short rows leave room for 4
+  static constexpr bool SHORT = N <= 512;
+  static constexpr int MINB_FWD = SHORT ? 4 : 2, MINB_INV = SHORT ? 4 : 3, MINB_ADJ = SHORT ? 4 : 2;
   // adjoint inverse row pass: twiddles, exchange, the factor table
   // 1 - exp(2 pi i l / N) for l <= N/2, then (16-byte aligned) the F + 1 rows of
   // Y an item needs, LDY complex each
@@ -173,7 +177,8 @@ struct ColShape {
   static constexpr int M = M_, R1 = R1_, R2 = R2_, C = C_;
   static constexpr int T = R2;             // threads per column
   static constexpr int THREADS = ((C * T + 31) / 32) * 32;
-  static constexpr int MINB = (THREADS <= 256) ? 2 : 1;  // blocks per SM the registers must allow
+  // blocks per SM the registers must allow (short columns leave room for 4)
+  static constexpr int MINB = (M <= 512 && THREADS <= 160) ? 4 : ((THREADS <= 256) ? 2 : 1);
   static_assert(R1 <= R2, "column schedule needs R1 <= R2");
   static_assert(C <= 32, "the u[0,0] partial of a block is gathered in one warp");
   // per-column exchange stride: the inverse exchange keeps one spare slot every
@@ -387,7 +392,7 @@ __global__ void __launch_bounds__(512) k_fast_div_edit(const T* __restrict__ gx,
 // and the transposed store of the spectrum.
 // ---------------------------------------------------------------------------
 template <class S>
-__global__ void __launch_bounds__(S::THREADS, 2) k_fast_rows_fwd(const float2* __restrict__ z,
+__global__ void __launch_bounds__(S::THREADS, S::MINB_FWD) k_fast_rows_fwd(const float2* __restrict__ z,
                                                                  float2* __restrict__ spec,
                                                                  const float2* __restrict__ twg, FastArgs A) {
   extern __shared__ __align__(16) float2 sm[];
@@ -518,7 +523,7 @@ __host__ __device__ constexpr size_t fused_exchange_bytes() {
 }
 
 template <class S, typename T, bool ADJ>
-__global__ void __launch_bounds__(S::THREADS, 2) k_fast_rows_fwd_div(const T* __restrict__ gx,
+__global__ void __launch_bounds__(S::THREADS, S::MINB_FWD) k_fast_rows_fwd_div(const T* __restrict__ gx,
                                                                      const T* __restrict__ gy,
                                                                      float2* __restrict__ spec,
                                                                      const float2* __restrict__ twg,
@@ -841,7 +846,7 @@ __global__ void __launch_bounds__(S::THREADS, S::MINB) k_fast_cols(const float2*
 // in registers, so it overlaps the stage-2 transforms and the output stores.
 // ---------------------------------------------------------------------------
 template <class S, typename T>
-__global__ void __launch_bounds__(S::THREADS, 3) k_fast_rows_inv(const float2* __restrict__ Y,
+__global__ void __launch_bounds__(S::THREADS, S::MINB_INV) k_fast_rows_inv(const float2* __restrict__ Y,
                                                               const float* __restrict__ partial, T* __restrict__ out,
                                                               const float2* __restrict__ twg, FastArgs A) {
   extern __shared__ __align__(16) float2 sm[];
@@ -983,7 +988,7 @@ __global__ void __launch_bounds__(S::THREADS, 3) k_fast_rows_inv(const float2* _
 // A + i B gives grad_gx in its real part and grad_gy in its imaginary part.
 // ---------------------------------------------------------------------------
 template <class S, typename T>
-__global__ void __launch_bounds__(S::THREADS, 2) k_fast_rows_adj(const float2* __restrict__ Y, T* __restrict__ ggx,
+__global__ void __launch_bounds__(S::THREADS, S::MINB_ADJ) k_fast_rows_adj(const float2* __restrict__ Y, T* __restrict__ ggx,
                                                                  T* __restrict__ ggy, const float2* __restrict__ twg,
                                                                  FastArgs A) {
   extern __shared__ __align__(16) float2 sm[];
