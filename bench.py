@@ -382,6 +382,19 @@ def extra_workloads(dev):
                                 "solves_per_s_graph": 1000.0 / msg}
     g.close()
     p.close()
+    # one 801x1200 field alone (the benchmark shape at batch 1): plain call vs graph replay
+    gx1, gy1 = synth.perturbed_gradient_batch(batch=1, H=801, W=1200, seed=1000)
+    p = gfc.Plan(801, 1200, 1, 1, device=dev)
+    tx = torch.from_numpy(gx1).to(dev).view(1, 1, 801, 1200)
+    ty = torch.from_numpy(gy1).to(dev).view(1, 1, 801, 1200)
+    out = torch.empty_like(tx)
+    ms = _time_ms(lambda: p.solve_from_gradient(tx, ty, out), dev, 100)
+    g = gfc.Graph(p, "gradient", tx, ty, out)
+    msg = _time_ms(g.launch, dev, 100)
+    res["single_801x1200_fp32"] = {"ms_per_solve": ms, "ms_per_solve_graph": msg, "solves_per_s": 1000.0 / ms,
+                                   "solves_per_s_graph": 1000.0 / msg}
+    g.close()
+    p.close()
     # Poisson blending batch 16 x 3 x 1024x1536, fp32 and fp16 storage
     bx, by, _ = synth.poisson_blend_batch()
     for dt, name in ((torch.float32, "fp32"), (torch.float16, "fp16")):
