@@ -284,15 +284,7 @@ def run_gfc(args, rank, world, local_rank):
         per_kernel.append({"kernel": names[i], "launches": prof["launches"][i], "ms": prof["pass_ms"][i],
                            "share": prof["pass_ms"][i] / tot_ms, "ms_per_launch": ms1,
                            "algorithmic_bytes_per_launch": pass_bytes[i], "gb_per_s": gbs, "frac": gbs / peak})
-    traffic = None
-    tr_path = os.path.join(ROOT, "profiles", "traffic_solve_801x1200_b100.txt")
-    if os.path.exists(tr_path):
-        try:
-            kv = dict(ln.split(":", 1) for ln in open(tr_path).read().splitlines() if ":" in ln)
-            if kv.get("kernel_build", "").strip() == _kernel_build_id():
-                traffic = float(kv["dram_bytes_per_step"])
-        except Exception:
-            traffic = None
+    traffic = stored_traffic()
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
@@ -581,6 +573,21 @@ def _edit_workload(dev):
     res["solve_merge_fused"] = {"ms": ms, "solves_per_s": B * 1000.0 / ms}
     p.close()
     return res
+
+
+def stored_traffic(path=None):
+    """DRAM bytes per step from the committed ncu capture, or None when the CUDA
+    sources have changed since it was taken (or the record is missing)."""
+    path = path or os.path.join(ROOT, "profiles", "traffic_solve_801x1200_b100.txt")
+    if not os.path.exists(path):
+        return None
+    try:
+        kv = dict(ln.split(":", 1) for ln in open(path).read().splitlines() if ":" in ln and not ln.startswith("#"))
+        if kv.get("kernel_build", "").strip() != _kernel_build_id():
+            return None
+        return float(kv["dram_bytes_per_step"])
+    except (KeyError, ValueError):
+        return None
 
 
 def _kernel_build_id() -> str:
