@@ -64,8 +64,8 @@ typedef enum {
 /* GFC_SIZE_SMOOTH: M, N = smallest even 7-smooth sizes >= H + 2p, W + 2p (the
  * register-resident transforms). GFC_SIZE_EXACT: Algorithm A's own size,
  * M = H + 2p, N = W + 2p, whatever their prime factors (Bluestein's chirp-z
- * for lengths that are not 7-smooth); H + 2p and W + 2p <= 2048, uniform plans,
- * forward solves only (gfc_backward returns GFC_ERR_UNSUPPORTED). */
+ * for lengths that are not 7-smooth); H + 2p and W + 2p <= 2048, uniform plans;
+ * solves, edited solves and the adjoint (gfc_backward) on that torus. */
 typedef enum { GFC_SIZE_SMOOTH = 0, GFC_SIZE_EXACT = 1 } gfc_size_policy;
 
 typedef struct {

@@ -141,10 +141,12 @@ __global__ void k_exact_transpose(const float2* __restrict__ src, float2* __rest
 }
 
 // L of field f at torus cell (r, c): image block at (p, p); MODE 0: L = div E
-// (Eq. 3) of the (optionally edited) gradient, MODE 1: L given
+// (Eq. 3) of the (optionally edited) gradient, MODE 1: L given, MODE 2 (the
+// adjoint): z = Crop^T(grad_out) - (sum grad_out) e_00, the sum from `gsum`
 template <typename T, int MODE, int EDIT>
 __device__ __forceinline__ float exact_lap(const T* __restrict__ in0, const T* __restrict__ in1, int f, int r, int c,
-                                           int H, int W, int p, const EditArgs& ed) {
+                                           int H, int W, int p, const EditArgs& ed, const double* __restrict__ gsum) {
+  if (MODE == 2 && r == 0 && c == 0) return (float)(-gsum[f]);  // the image block starts at (p, p), p >= 1
   const int i = r - p, j = c - p;
   const int nrows = (MODE == 0) ? H + 1 : H, ncols = (MODE == 0) ? W + 1 : W;
   if (i < 0 || i >= nrows || j < 0 || j >= ncols) return 0.0f;
@@ -164,15 +166,48 @@ __device__ __forceinline__ float exact_lap(const T* __restrict__ in0, const T* _
 // imaginary part each to its own real solution.
 template <typename T, int MODE, int EDIT>
 __global__ void k_exact_load(const T* __restrict__ in0, const T* __restrict__ in1, float2* __restrict__ X, int nf,
-                             int H, int W, int M, int N, int p, EditArgs ed) {
+                             int H, int W, int M, int N, int p, EditArgs ed, const double* __restrict__ gsum) {
   const int q = blockIdx.y, f0 = 2 * q, f1 = f0 + 1;
   float2* x = X + (size_t)q * M * N;
   for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < (long long)M * N;
        idx += (long long)gridDim.x * blockDim.x) {
     const int r = (int)(idx / N), c = (int)(idx - (long long)r * N);
-    const float v0 = exact_lap<T, MODE, EDIT>(in0, in1, f0, r, c, H, W, p, ed);
-    const float v1 = f1 < nf ? exact_lap<T, MODE, EDIT>(in0, in1, f1, r, c, H, W, p, ed) : 0.0f;
+    const float v0 = exact_lap<T, MODE, EDIT>(in0, in1, f0, r, c, H, W, p, ed, gsum);
+    const float v1 = f1 < nf ? exact_lap<T, MODE, EDIT>(in0, in1, f1, r, c, H, W, p, ed, gsum) : 0.0f;
     x[idx] = make_float2(v0, v1);
+  }
+}
+
+// adjoint: the sum of each field's grad_out, one block per field; each thread
+// adds its elements in FP32 in runs of 16, then in FP64; the block combines the
+// threads in a fixed order
+constexpr int kSumThreads = 1024;
+template <typename T>
+__global__ void __launch_bounds__(kSumThreads) k_exact_gsum(const T* __restrict__ g, int H, int W,
+                                                           double* __restrict__ gsum) {
+  const size_t fe = (size_t)H * W;
+  const T* a = g + (size_t)blockIdx.x * fe;
+  double acc = 0.0;
+  float run = 0.0f;
+  int k = 0;
+  for (size_t i = threadIdx.x; i < fe; i += kSumThreads) {
+    run += ex_ld(a + i);
+    if (++k == 16) {
+      acc += (double)run;
+      run = 0.0f;
+      k = 0;
+    }
+  }
+  acc += (double)run;
+  __shared__ double red[kSumThreads / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < kSumThreads / 32; ++w) s += red[w];
+    gsum[blockIdx.x] = s;
   }
 }
 
@@ -188,6 +223,26 @@ __global__ void k_exact_out(const float2* __restrict__ X, T* __restrict__ out, i
        idx += (long long)gridDim.x * blockDim.x) {
     const int i = (int)(idx / W), j = (int)(idx - (long long)i * W);
     o[idx] = ex_st<T>(x[2 * ((size_t)(p + i) * N + (p + j))] - u00);
+  }
+}
+
+// adjoint: grad_gx[i][j] = w[p+i][p+j] - w[p+i][p+j+1], grad_gy[i][j] =
+// w[p+i][p+j] - w[p+i+1][p+j] (the transpose of the divergence), w the real
+// (even field) or imaginary (odd field) part of the pair's convolution
+template <typename T>
+__global__ void k_exact_out_adj(const float2* __restrict__ X, T* __restrict__ ggx, T* __restrict__ ggy, int H, int W,
+                                int M, int N, int p) {
+  const int f = blockIdx.y;
+  const float* x = reinterpret_cast<const float*>(X + (size_t)(f / 2) * M * N) + (f & 1);
+  T* ox = ggx + (size_t)f * H * W;
+  T* oy = ggy + (size_t)f * H * W;
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < (long long)H * W;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(idx / W), j = (int)(idx - (long long)i * W);
+    const size_t at = (size_t)(p + i) * N + (p + j);  // p + W < N, p + H < M
+    const float w0 = x[2 * at];
+    ox[idx] = ex_st<T>(w0 - x[2 * (at + 1)]);
+    oy[idx] = ex_st<T>(w0 - x[2 * (at + N)]);
   }
 }
 
@@ -276,8 +331,8 @@ cudaError_t setup_dim(ExactDim* d, int n, cudaStream_t s) {
 }
 
 template <typename T, int MODE>
-cudaError_t run_exact(gfc_plan* P, const Bufs& bf, const T* in0, const T* in1, T* out0, int nf, cudaStream_t st,
-                      const EditArgs* ed) {
+cudaError_t run_exact(gfc_plan* P, const Bufs& bf, const T* in0, const T* in1, T* out0, T* out1, int nf,
+                      cudaStream_t st, const EditArgs* ed) {
   const int M = P->M, N = P->N;
   const int np = (nf + 1) / 2;  // complex tori: two fields each
   float2* X = bf.spec;
@@ -290,20 +345,30 @@ cudaError_t run_exact(gfc_plan* P, const Bufs& bf, const T* in0, const T* in1, T
   const DimArgs dr = dim_args(P->ex_row), dc = dim_args(P->ex_col);
   const size_t sr = dim_smem(P->ex_row), sc = dim_smem(P->ex_col);
   cudaError_t e;
-  // divergence / Laplacian into the complex tori
+  double* gsum = reinterpret_cast<double*>(bf.partial);  // MODE 2: sum(grad_out) per field
+  if (MODE == 2) {
+    prof_begin(P, 3, st);
+    k_exact_gsum<T><<<nf, kSumThreads, 0, st>>>(in0, P->H, P->W, gsum);
+    prof_end(P, st);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  // divergence / Laplacian / Crop^T(grad_out) into the complex tori
   {
     const long long cells = (long long)M * N;
     int gx = (int)((cells + kExactThreads - 1) / kExactThreads);
     if (gx > 4 * sms) gx = 4 * sms;
     const dim3 g(gx, np);
-    if (MODE == 1)
-      k_exact_load<T, 1, kEditNone><<<g, kExactThreads, 0, st>>>(in0, in1, X, nf, P->H, P->W, M, N, P->pad, E);
+    const int H = P->H, W = P->W, p = P->pad;
+    if (MODE == 2)
+      k_exact_load<T, 2, kEditNone><<<g, kExactThreads, 0, st>>>(in0, in1, X, nf, H, W, M, N, p, E, gsum);
+    else if (MODE == 1)
+      k_exact_load<T, 1, kEditNone><<<g, kExactThreads, 0, st>>>(in0, in1, X, nf, H, W, M, N, p, E, gsum);
     else if (E.kind == kEditThreshold)
-      k_exact_load<T, 0, kEditThreshold><<<g, kExactThreads, 0, st>>>(in0, in1, X, nf, P->H, P->W, M, N, P->pad, E);
+      k_exact_load<T, 0, kEditThreshold><<<g, kExactThreads, 0, st>>>(in0, in1, X, nf, H, W, M, N, p, E, gsum);
     else if (E.kind == kEditMerge)
-      k_exact_load<T, 0, kEditMerge><<<g, kExactThreads, 0, st>>>(in0, in1, X, nf, P->H, P->W, M, N, P->pad, E);
+      k_exact_load<T, 0, kEditMerge><<<g, kExactThreads, 0, st>>>(in0, in1, X, nf, H, W, M, N, p, E, gsum);
     else
-      k_exact_load<T, 0, kEditNone><<<g, kExactThreads, 0, st>>>(in0, in1, X, nf, P->H, P->W, M, N, P->pad, E);
+      k_exact_load<T, 0, kEditNone><<<g, kExactThreads, 0, st>>>(in0, in1, X, nf, H, W, M, N, p, E, gsum);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   const long long rows = (long long)np * M;
@@ -333,7 +398,10 @@ cudaError_t run_exact(gfc_plan* P, const Bufs& bf, const T* in0, const T* in1, T
     const long long cells = (long long)P->H * P->W;
     int gx = (int)((cells + kExactThreads - 1) / kExactThreads);
     if (gx > 4 * sms) gx = 4 * sms;
-    k_exact_out<T><<<dim3(gx, nf), kExactThreads, 0, st>>>(X, out0, P->H, P->W, M, N, P->pad);
+    if (MODE == 2)
+      k_exact_out_adj<T><<<dim3(gx, nf), kExactThreads, 0, st>>>(X, out0, out1, P->H, P->W, M, N, P->pad);
+    else
+      k_exact_out<T><<<dim3(gx, nf), kExactThreads, 0, st>>>(X, out0, P->H, P->W, M, N, P->pad);
   }
   return cudaGetLastError();
 }
@@ -356,14 +424,17 @@ void exact_release(gfc_plan* P) {
 }
 
 cudaError_t run_chunk_exact(gfc_plan* P, const Bufs& bf, int mode, const void* in0, const void* in1, void* out0,
-                            int nf, cudaStream_t st, const EditArgs* ed) {
-  if (mode != 0 && mode != 1) return cudaErrorNotSupported;
+                            void* out1, int nf, cudaStream_t st, const EditArgs* ed) {
+  if (mode < 0 || mode > 2) return cudaErrorNotSupported;
   auto go = [&](auto tag) -> cudaError_t {
     using T = decltype(tag);
     const T* a = static_cast<const T*>(in0);
     const T* b = static_cast<const T*>(in1);
     T* o = static_cast<T*>(out0);
-    return mode == 0 ? run_exact<T, 0>(P, bf, a, b, o, nf, st, ed) : run_exact<T, 1>(P, bf, a, b, o, nf, st, ed);
+    T* o1 = static_cast<T*>(out1);
+    if (mode == 0) return run_exact<T, 0>(P, bf, a, b, o, o1, nf, st, ed);
+    if (mode == 1) return run_exact<T, 1>(P, bf, a, b, o, o1, nf, st, ed);
+    return run_exact<T, 2>(P, bf, a, b, o, o1, nf, st, ed);
   };
   switch (P->dtype) {
     case GFC_F32: return go(float{});

@@ -137,12 +137,12 @@ inline size_t dtype_size(gfc_dtype d) { return d == GFC_F32 ? 4 : 2; }
 void prof_begin(gfc_plan* P, int pass, cudaStream_t st);
 void prof_end(gfc_plan* P, cudaStream_t st);
 // EXACT-size plans (exact.cu): tables, teardown, one chunk (mode 0 gradient,
-// 1 Laplacian; `ed` as for run_chunk_fast). The chunk scratch holds 2 M N
-// complex per field.
+// 1 Laplacian, 2 adjoint into out0 = grad_gx, out1 = grad_gy; `ed` as for
+// run_chunk_fast). The chunk scratch holds 2 M N complex per field.
 cudaError_t exact_setup(gfc_plan* P, cudaStream_t s);
 void exact_release(gfc_plan* P);
 cudaError_t run_chunk_exact(gfc_plan* P, const Bufs& B, int mode, const void* in0, const void* in1, void* out0,
-                            int nf, cudaStream_t st, const EditArgs* ed);
+                            void* out1, int nf, cudaStream_t st, const EditArgs* ed);
 
 // per-field squared thresholds of Sec. 3.2.3 into P->edit_t2 (edit.cu): from
 // the fields' largest gradient magnitudes when ref <= 0, else from ref

@@ -474,7 +474,7 @@ static cudaError_t launch_b_any(gfc_plan* P, const Bufs& bf, PassArgs B, int nf,
 template <typename T, int MODE>
 static cudaError_t run_chunk(gfc_plan* P, const Bufs& bf, const T* in0, const T* in1, T* out0, T* out1, int nf,
                              cudaStream_t st, const EditArgs* ed = nullptr) {
-  if (P->exact) return run_chunk_exact(P, bf, MODE, in0, in1, out0, nf, st, ed);
+  if (P->exact) return run_chunk_exact(P, bf, MODE, in0, in1, out0, out1, nf, st, ed);
   if (P->fast) return run_chunk_fast(P, bf, MODE, in0, in1, out0, out1, nf, st, ed);
   const EditArgs none{kEditNone, 0.0f, nullptr, nullptr};
   const EditArgs& E = ed ? *ed : none;
@@ -820,7 +820,6 @@ gfc_status gfc_solve_from_laplacian(gfc_plan* plan, const void* lap, void* out) 
 
 gfc_status gfc_backward(gfc_plan* plan, const void* grad_out, void* grad_gx, void* grad_gy) {
   clear_error();
-  if (plan && plan->exact) return fail(GFC_ERR_UNSUPPORTED, "gfc_backward: EXACT-size plans solve forward only");
   if (!plan || !grad_out || !grad_gx || !grad_gy) return fail(GFC_ERR_INVALID_ARG, "gfc_backward: null argument");
   if (misaligned(grad_out) || misaligned(grad_gx) || misaligned(grad_gy))
     return fail(GFC_ERR_INVALID_ARG, "gfc_backward: pointers must be 16-byte aligned");

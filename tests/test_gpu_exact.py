@@ -104,9 +104,56 @@ def test_exact_against_smooth_sizes():
     ps.close()
 
 
-def test_exact_rejects_backward():
-    p = gfc.Plan(20, 30, device=DEV, exact=True)
-    g = torch.zeros((1, 1, 20, 30), device=DEV)
-    with pytest.raises(gfc.GFCError):
-        p.backward(g)
+def _torch_fp32_adjoint(gout, M, N, p):
+    """The adjoint in plain PyTorch FP32 (rfft2 / irfft2 on the same torus): the
+    FP32 baseline error for white-noise upstream gradients."""
+    H, W = gout.shape
+    G = torch.from_numpy(O.green_spectrum(M, N)[:, : N // 2 + 1]).float().to(DEV)
+    z = torch.zeros((M, N), device=DEV)
+    g = torch.from_numpy(np.ascontiguousarray(gout)).float().to(DEV)
+    z[p:p + H, p:p + W] = g
+    z[0, 0] -= g.sum()
+    w = torch.fft.irfft2(torch.fft.rfft2(z) * G, s=(M, N))
+    gx = (w - torch.roll(w, -1, -1))[p:p + H, p:p + W]
+    gy = (w - torch.roll(w, -1, -2))[p:p + H, p:p + W]
+    return gx.double().cpu().numpy(), gy.double().cpu().numpy()
+
+
+# 72x104 (Bluestein along rows), 31x37 (both prime), 18x25 (direct), 809x1208
+@pytest.mark.parametrize("H,W,B", [(64, 96, 2), (23, 29, 3), (10, 17, 1), (801, 1200, 1)])
+def test_exact_backward_matches_oracle(H, W, B):
+    """The adjoint on Algorithm A's own torus against the oracle's transpose,
+    bounded like the other white-noise adjoint checks."""
+    gout = synth.upstream_gradient((B, 1, H, W), seed=7500 + H)
+    p = gfc.Plan(H, W, 1, B, device=DEV, exact=True)
+    bx, by = p.backward(_dev(gout))
+    bx, by = _np(bx), _np(by)
+    for b in range(B):
+        g0 = gout[b, 0].astype(np.float64)
+        rx, ry = O.backward(g0, p.M, p.N, p.pad)
+        tx, ty = _torch_fp32_adjoint(gout[b, 0], p.M, p.N, p.pad)
+        assert _rel(bx[b, 0], rx) <= max(REL_F32, 3.0 * _rel(tx, rx)), (b, _rel(bx[b, 0], rx), _rel(tx, rx))
+        assert _rel(by[b, 0], ry) <= max(REL_F32, 3.0 * _rel(ty, ry)), (b, _rel(by[b, 0], ry), _rel(ty, ry))
     p.close()
+
+
+def test_exact_backward_is_the_transpose_and_bf16():
+    """<solve(gx, gy), g> = <(gx, gy), backward(g)> on the EXACT torus (the
+    forward is linear), and BF16 storage against the oracle on the dequantised
+    upstream gradient."""
+    H, W = 30, 44
+    gx, gy = synth.perturbed_gradient_batch(1, H, W, seed=7600)
+    g = synth.upstream_gradient((1, 1, H, W), seed=7601)
+    p = gfc.Plan(H, W, device=DEV, exact=True)
+    y = _np(p.solve_from_gradient(_dev(gx), _dev(gy)))
+    bx, by = p.backward(_dev(g))
+    lhs = float((y * g).sum())
+    rhs = float((gx * _np(bx)).sum() + (gy * _np(by)).sum())
+    assert abs(lhs - rhs) <= 1e-5 * (abs(lhs) + abs(rhs) + 1.0), (lhs, rhs)
+    p.close()
+    q = gfc.Plan(H, W, dtype=torch.bfloat16, device=DEV, exact=True)
+    dg = _dev(g, torch.bfloat16)
+    qx, qy = q.backward(dg)
+    rx, ry = O.backward(_np(dg)[0, 0], q.M, q.N, q.pad)
+    assert _rel(_np(qx)[0, 0], rx) <= REL_16 and _rel(_np(qy)[0, 0], ry) <= REL_16
+    q.close()
