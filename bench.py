@@ -518,8 +518,11 @@ def _exact_workload(dev):
     p = gfc.Plan(H, W, 1, B, device=dev, exact=True)
     out = torch.empty_like(gx)
     ms = _time_ms(lambda: p.solve_from_gradient(gx, gy, out), dev, 5)
+    bx, by = torch.empty_like(gx), torch.empty_like(gx)
+    ms_b = _time_ms(lambda: p.backward(out, bx, by), dev, 5)
     p.close()
-    return {"padded": [H + 8, W + 8], "ms_per_batch": ms, "solves_per_s": B * 1000.0 / ms}
+    return {"padded": [H + 8, W + 8], "ms_per_batch": ms, "solves_per_s": B * 1000.0 / ms,
+            "ms_backward_per_batch": ms_b}
 
 
 def _edit_workload(dev):
