@@ -55,7 +55,7 @@ typedef enum { GFC_F32 = 0, GFC_F16 = 1, GFC_BF16 = 2 } gfc_dtype;
 typedef enum {
   GFC_OK = 0,
   GFC_ERR_INVALID_ARG = 1, /* bad size, null or misaligned pointer, bad enum */
-  GFC_ERR_UNSUPPORTED = 2, /* size or feature outside what this build handles */
+  GFC_ERR_UNSUPPORTED = 2, /* size or feature the library does not support */
   GFC_ERR_ALLOC = 3,       /* device or host allocation failed */
   GFC_ERR_CUDA = 4,        /* a CUDA runtime call or a launch failed */
   GFC_ERR_TIMEOUT = 5      /* a bounded device-side wait ran out */
