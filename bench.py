@@ -501,8 +501,26 @@ def _backward_workload(dev):
     p = gfc.Plan(H, W, 1, B, device=dev)
     ms_b = _time_ms(lambda: p.backward(go, gx, gy), dev, 10)
     ms_f = _time_ms(lambda: p.solve_from_gradient(go, go, gx), dev, 10)
+    # per-pass device time of the adjoint (profiling hook), and its minimum bytes:
+    # grad_out read once, grad_gx and grad_gy written once, G once
+    reps = 10
+    p.profile(reset=True)  # drop the counts of the calls above
+    p.set_profiling(True)
+    for _ in range(reps):
+        p.backward(go, gx, gy)
+    prof = p.profile()
+    p.set_profiling(False)
     p.close()
-    return {"ms_forward": ms_f, "ms_backward": ms_b, "fwd_bwd_solves_per_s": B * 1000.0 / (ms_f + ms_b)}
+    peak, kind = _peaks()
+    min_bytes = 3 * 4 * H * W * B + 4 * p.M * (p.N // 2 + 1)
+    gbs = min_bytes / (ms_b / 1000.0) / 1e9
+    names = ["row pass (grad_out packing folded in)", "sum(grad_out) + column pass",
+             "inverse row pass (grad_gx, grad_gy)"]
+    passes = [{"pass": names[i], "ms": prof["pass_ms"][i] / reps, "launches_per_call": prof["launches"][i] / reps}
+              for i in range(3)]
+    return {"ms_forward": ms_f, "ms_backward": ms_b, "fwd_bwd_solves_per_s": B * 1000.0 / (ms_f + ms_b),
+            "backward_min_bytes": min_bytes, "backward_gb_per_s": gbs, "backward_frac_of_hbm": gbs / peak,
+            "peak_kind": kind, "backward_passes": passes}
 
 
 def _exact_workload(dev):
