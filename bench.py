@@ -41,6 +41,45 @@ UNIT = "solves/s"
 WORKLOAD = "GFC solve from gradient, 100 x 1 x 801x1200 fp32 per GPU (perturbed smooth images)"
 
 
+def smooth_even_at_least(n: int) -> int:
+    """Smallest even integer >= n whose prime factors are all <= 7 (the SMOOTH size policy)."""
+    n += n & 1
+    while True:
+        m = n
+        for f in (2, 3, 5, 7):
+            while m % f == 0:
+                m //= f
+        if m == 1:
+            return n
+        n += 2
+
+
+def padded_size(H: int, W: int, pad: int = 4):
+    """(M, N) of the SMOOTH padded torus, computed here so that the oracle legs never
+    load the product library (a CPU test checks it against the library's rule)."""
+    return smooth_even_at_least(H + 2 * pad), smooth_even_at_least(W + 2 * pad)
+
+
+def torchrun_command(gpus: int, argv, env, python=None):
+    """The command that relaunches this script as ``gpus`` ranks under torch.distributed.run,
+    or None when no relaunch is needed (one GPU, or already a rank of a job). A rank whose
+    job size disagrees with ``--gpus`` is an error."""
+    world = env.get("WORLD_SIZE")
+    if world is not None:
+        if int(world) != gpus:
+            raise ValueError(f"--gpus {gpus} but WORLD_SIZE={world}")
+        return None
+    if gpus <= 1:
+        return None
+    import socket
+
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    return [python or sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={gpus}",
+            "--master-addr", "127.0.0.1", "--master-port", str(port), os.path.abspath(__file__)] + list(argv)
+
+
 def rank_seed(rank: int, batch: int) -> int:
     """First generator seed of a rank's shard: ranks solve disjoint sets of fields
     (weak scaling: every rank holds `batch` fields, no data-path collective)."""
@@ -132,26 +171,44 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def cpu_oracle_rate(budget_s: float, fields: int = 64):
-    """Time the FP64 oracle on successive fields of the workload until ``budget_s`` of CPU work."""
+def _err(got, ref):
+    """Relative L2 and max-abs error of a result against the oracle's."""
+    import numpy as np
+
+    got = np.asarray(got, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    return {"rel_l2": float(np.linalg.norm(got - ref) / max(np.linalg.norm(ref), 1e-300)),
+            "max_abs": float(np.abs(got - ref).max())}
+
+
+def cpu_oracle_rate(budget_s: float, fields: int = 64, gpu_fields=None):
+    """Time the FP64 oracle on successive fields of the workload until ``budget_s`` of CPU work.
+
+    ``gpu_fields`` maps field indices to the GPU's results for them: those fields are
+    solved first and their errors against the oracle are returned as well."""
     import numpy as np
 
     import oracle.gfc_oracle as O
     from paper_1902_00176_gb300 import synth
-    from paper_1902_00176_gb300 import gfc
 
-    M, N = gfc.padded_size(H, W)
-    done, t0 = 0, time.perf_counter()
-    while done < fields:
-        gx, gy = synth.perturbed_gradient_batch(batch=B, H=H, W=W, items=[done % B])
-        t1 = time.perf_counter()
-        O.solve_from_gradient(gx[0, 0].astype(np.float64), gy[0, 0].astype(np.float64), M, N, 4)
+    M, N = padded_size(H, W)
+    first = sorted(gpu_fields or {})
+    order = first + [i for i in range(fields) if i not in first]
+    done, errs, t0 = 0, [], time.perf_counter()
+    for i in order:
+        gx, gy = synth.perturbed_gradient_batch(batch=B, H=H, W=W, items=[i % B])
+        ref = O.solve_from_gradient(gx[0, 0].astype(np.float64), gy[0, 0].astype(np.float64), M, N, 4)
         done += 1
-        if time.perf_counter() - t0 >= budget_s:
+        if gpu_fields and i in gpu_fields:
+            errs.append(_err(gpu_fields[i], ref))
+        if time.perf_counter() - t0 >= budget_s and len(errs) == len(first):
             break
-        _ = t1
     el = time.perf_counter() - t0
-    return done / el, done, el
+    err = None
+    if errs:
+        err = {"rel_l2": max(e["rel_l2"] for e in errs), "max_abs": max(e["max_abs"] for e in errs),
+               "fields": first}
+    return done / el, done, el, err
 
 
 def run_reference(args, rank, world):
@@ -162,9 +219,9 @@ def run_reference(args, rank, world):
     import numpy as np
 
     import oracle.gfc_oracle as O
-    from paper_1902_00176_gb300 import gfc, synth
+    from paper_1902_00176_gb300 import synth
 
-    M, N = gfc.padded_size(H, W)
+    M, N = padded_size(H, W)
 
     def one(i):
         gx, gy = synth.perturbed_gradient_batch(batch=B, H=H, W=W, items=[i % B])
@@ -219,8 +276,6 @@ def run_gfc(args, rank, world, local_rank):
     for _ in range(args.warmup):
         plan.solve_from_gradient(tx, ty, out)
     torch.cuda.synchronize(dev)
-    plan.profile(reset=True)
-    plan.set_profiling(True)
 
     vis = [v.strip() for v in os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",") if v.strip()]
     sampler = ClockSampler(vis[local_rank] if local_rank < len(vis) else str(local_rank))
@@ -229,7 +284,7 @@ def run_gfc(args, rank, world, local_rank):
     while time.time() < t_end:
         plan.solve_from_gradient(tx, ty, out)
         torch.cuda.synchronize(dev)
-    plan.profile(reset=True)
+    # the timed region: per-launch profiling is off, only two events bracket the steps
     barrier()
     torch.cuda.synchronize(dev)
     e0 = torch.cuda.Event(enable_timing=True)
@@ -242,11 +297,20 @@ def run_gfc(args, rank, world, local_rank):
     barrier()
     clocks = sampler.stop()
     ms_total = e0.elapsed_time(e1)
-    prof = plan.profile(reset=True)
-    plan.set_profiling(False)
     ms_total = max_over_ranks(ms_total, world, dev)
     ms_step = ms_total / args.steps
     value = job_rate(B, world, args.steps, ms_total)
+    # per-pass device times and launch counts from a separate profiled run (events
+    # around every launch), on the same stream
+    prof_steps = max(3, min(args.steps, 20))
+    plan.profile(reset=True)
+    plan.set_profiling(True)
+    for _ in range(prof_steps):
+        plan.solve_from_gradient(tx, ty, out)
+    prof = plan.profile(reset=True)
+    plan.set_profiling(False)
+    launches_per_step = sum(prof["launches"]) / prof_steps
+    gpu_fields = {i: out[i, 0].double().cpu().numpy() for i in sorted({0, B // 2, B - 1})}
 
     e2e = None
     if not args.no_e2e:
@@ -255,7 +319,6 @@ def run_gfc(args, rank, world, local_rank):
     if rank != 0:
         return
     peak, peak_kind = _peaks()
-    hy = torch.from_numpy(gy).pin_memory()
 
     fe = H * W
     G_bytes = plan.M * (plan.N // 2 + 1) * 4
@@ -281,9 +344,10 @@ def run_gfc(args, rank, world, local_rank):
             continue
         ms1 = prof["pass_ms"][i] / prof["launches"][i]
         gbs = pass_bytes[i] / (ms1 / 1000.0) / 1e9
-        per_kernel.append({"kernel": names[i], "launches": prof["launches"][i], "ms": prof["pass_ms"][i],
-                           "share": prof["pass_ms"][i] / tot_ms, "ms_per_launch": ms1,
-                           "algorithmic_bytes_per_launch": pass_bytes[i], "gb_per_s": gbs, "frac": gbs / peak})
+        per_kernel.append({"kernel": names[i], "launches_per_step": prof["launches"][i] / prof_steps,
+                           "ms_per_step": prof["pass_ms"][i] / prof_steps, "share": prof["pass_ms"][i] / tot_ms,
+                           "ms_per_launch": ms1, "algorithmic_bytes_per_launch": pass_bytes[i], "gb_per_s": gbs,
+                           "frac": gbs / peak})
     traffic = stored_traffic()
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -295,17 +359,24 @@ def run_gfc(args, rank, world, local_rank):
         "roofline": {"bound": "hbm", "kernel": "solve call (row, column, inverse-row passes)",
                      "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "min_bytes_per_step": min_bytes,
-                     "per_kernel": per_kernel},
+                     "per_kernel": per_kernel,
+                     "per_kernel_note": f"per-pass times from a separate run of {prof_steps} steps with CUDA "
+                                        "events around every launch; the headline is timed without them"},
         "e2e": e2e,
-        "gpu_launches": int(sum(prof["launches"])),
+        "gpu_launches": int(round(launches_per_step * args.steps)),
         "clocks": clocks,
     }
+    samples = []
     if not args.no_extra:
-        line["extra_workloads"] = extra_workloads(torch.device("cuda", local_rank))
+        line["extra_workloads"] = extra_workloads(torch.device("cuda", local_rank), samples)
     if not args.no_cpu_baseline:
-        rate, n, el = cpu_oracle_rate(args.cpu_budget)
+        rate, n, el, err = cpu_oracle_rate(args.cpu_budget, gpu_fields=gpu_fields)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                                 "sample": f"{n} fields of the 801x1200 batch, FP64 oracle, {el:.1f} s"}
+        line["oracle_error"] = err
+        if samples:
+            for name, e in oracle_errors(samples).items():
+                line["extra_workloads"][name]["oracle_error"] = e
     print(json.dumps(line), flush=True)
 
 
@@ -354,8 +425,57 @@ def _time_ms(fn, dev, reps):
     return e0.elapsed_time(e1) / reps
 
 
-def extra_workloads(dev):
-    """The other workload shapes of the method, each timed on this GPU (inputs resident)."""
+def _h(t):
+    """A device field as a host FP64 array (the dequantised value of 16-bit storage)."""
+    return t.double().cpu().numpy()
+
+
+def _sample(samples, workload, kind, got, M, N, **inputs):
+    """Record one field of a workload's GPU result, with what the oracle needs to
+    recompute it, for the oracle-error leg. ``got`` is one array or a tuple."""
+    samples.append({"workload": workload, "kind": kind, "got": got, "M": M, "N": N, "inputs": inputs})
+
+
+def oracle_errors(samples):
+    """Errors of the sampled GPU fields against the FP64 oracle (the CPU leg of the
+    benchmark), per workload: the largest relative L2 and max-abs over its fields."""
+    import oracle.gfc_edit_oracle as E
+    import oracle.gfc_oracle as O
+
+    res = {}
+    for smp in samples:
+        kind, M, N, x = smp["kind"], smp["M"], smp["N"], smp["inputs"]
+        t0 = time.perf_counter()
+        if kind == "grad":
+            refs = (O.solve_from_gradient(x["gx"], x["gy"], M, N, 4),)
+        elif kind == "bwd":
+            refs = O.backward(x["gout"], M, N, 4)
+        elif kind == "threshold":
+            ex, ey, _ = E.gradient_threshold(x["gx"].astype("float32"), x["gy"].astype("float32"), x["frac"])
+            refs = (O.solve_from_gradient(ex.astype("float64"), ey.astype("float64"), M, N, 4),)
+        elif kind == "merge":
+            ex, ey = E.gradient_merge(x["gx"], x["gy"], x["edges"], x["alpha"])
+            refs = (O.solve_from_gradient(ex, ey, M, N, 4),)
+        elif kind == "correct":
+            ex, ey, _ = E.gradient_threshold(x["gx"].astype("float32"), x["gy"].astype("float32"), x["frac"])
+            u = O.solve_from_gradient(ex.astype("float64"), ey.astype("float64"), M, N, 4)
+            m, sd = E.field_stats(x["img"])
+            refs = (E.color_correct_with(u, m, sd),)
+        else:
+            raise ValueError(kind)
+        got = smp["got"] if isinstance(smp["got"], tuple) else (smp["got"],)
+        errs = [_err(g, r) for g, r in zip(got, refs)]
+        e = res.setdefault(smp["workload"], {"rel_l2": 0.0, "max_abs": 0.0, "fields": 0, "oracle_s": 0.0})
+        e["rel_l2"] = max([e["rel_l2"]] + [v["rel_l2"] for v in errs])
+        e["max_abs"] = max([e["max_abs"]] + [v["max_abs"] for v in errs])
+        e["fields"] += 1
+        e["oracle_s"] += time.perf_counter() - t0
+    return res
+
+
+def extra_workloads(dev, samples):
+    """The other workload shapes of the method, each timed on this GPU (inputs resident);
+    a few fields of each are recorded in ``samples`` for the oracle-error leg."""
     import torch
 
     from paper_1902_00176_gb300 import gfc, synth
@@ -372,6 +492,7 @@ def extra_workloads(dev):
     msg = _time_ms(g.launch, dev, 200)
     res["single_64x96_fp32"] = {"ms_per_solve": ms, "ms_per_solve_graph": msg, "solves_per_s": 1000.0 / ms,
                                 "solves_per_s_graph": 1000.0 / msg}
+    _sample(samples, "single_64x96_fp32", "grad", _h(out[0, 0]), p.M, p.N, gx=_h(tx[0, 0]), gy=_h(ty[0, 0]))
     g.close()
     p.close()
     # one 801x1200 field alone (the benchmark shape at batch 1): plain call vs graph replay
@@ -385,6 +506,7 @@ def extra_workloads(dev):
     msg = _time_ms(g.launch, dev, 100)
     res["single_801x1200_fp32"] = {"ms_per_solve": ms, "ms_per_solve_graph": msg, "solves_per_s": 1000.0 / ms,
                                    "solves_per_s_graph": 1000.0 / msg}
+    _sample(samples, "single_801x1200_fp32", "grad", _h(out[0, 0]), p.M, p.N, gx=_h(tx[0, 0]), gy=_h(ty[0, 0]))
     g.close()
     p.close()
     # Poisson blending batch 16 x 3 x 1024x1536, fp32 and fp16 storage
@@ -395,40 +517,20 @@ def extra_workloads(dev):
         p = gfc.Plan(1024, 1536, 3, 16, dt, device=dev)
         out = torch.empty_like(tx)
         ms = _time_ms(lambda: p.solve_from_gradient(tx, ty, out), dev, 10)
-        res[f"blend_16x3x1024x1536_{name}"] = {"ms_per_batch": ms, "solves_per_s": 48 * 1000.0 / ms}
+        key = f"blend_16x3x1024x1536_{name}"
+        res[key] = {"ms_per_batch": ms, "solves_per_s": 48 * 1000.0 / ms}
+        for b, c in ((0, 0), (15, 2)):
+            _sample(samples, key, "grad", _h(out[b, c]), p.M, p.N, gx=_h(tx[b, c]), gy=_h(ty[b, c]))
         p.close()
+        del tx, ty, out
     del bx, by
-    # ragged batch of 64 items vs 64 sequential plain solves
-    items = synth.ragged_items()
-    rp = gfc.RaggedPlan(items, device=dev)
-    gxr = torch.randn(rp.total, device=dev) * 0.01
-    gyr = torch.randn(rp.total, device=dev) * 0.01
-    outr = rp.empty()
-    ms = _time_ms(lambda: rp.solve_from_gradient(gxr, gyr, outr), dev, 5)
-    gr = gfc.Graph(rp, "gradient", gxr, gyr, outr)
-    msg = _time_ms(gr.launch, dev, 5)
-    plans = [gfc.Plan(h, w, c, 1, device=dev) for c, h, w in items]
-    views = [(gxr[o:o + c * h * w].view(1, c, h, w), gyr[o:o + c * h * w].view(1, c, h, w),
-              outr[o:o + c * h * w].view(1, c, h, w)) for (c, h, w), o in zip(items, rp.offsets)]
-
-    def seq():
-        for pl, (a, b, o) in zip(plans, views):
-            pl.solve_from_gradient(a, b, o)
-
-    ms_seq = _time_ms(seq, dev, 3)
-    nf = sum(c for c, h, w in items)
-    res["ragged_64_items"] = {"fields": nf, "ms": ms, "ms_graph": msg, "solves_per_s": nf * 1000.0 / ms,
-                              "ms_sequential_plans": ms_seq, "speedup_vs_sequential": ms_seq / ms}
-    gr.close()
-    rp.close()
-    for pl in plans:
-        pl.close()
+    res["ragged_64_items"] = _ragged_workload(dev, samples)
     # differentiable layer: 32 x 64 x 256x256 bf16 storage, forward + hand-written adjoint
     fx, fy = synth.feature_gradients()
     tx = torch.from_numpy(fx).to(dev).to(torch.bfloat16)
     ty = torch.from_numpy(fy).to(dev).to(torch.bfloat16)
     del fx, fy
-    go = torch.randn(tx.shape, device=dev).to(torch.bfloat16)
+    go = torch.from_numpy(synth.upstream_gradient(tuple(tx.shape))).to(dev).to(torch.bfloat16)
     p = gfc.Plan(256, 256, 64, 32, torch.bfloat16, device=dev)
     out = torch.empty_like(tx)
     gx_, gy_ = torch.empty_like(tx), torch.empty_like(tx)
@@ -438,11 +540,66 @@ def extra_workloads(dev):
     res["layer_32x64x256x256_bf16"] = {"ms_forward": ms_f, "ms_backward": ms_b,
                                        "fwd_solves_per_s": nfld * 1000.0 / ms_f,
                                        "fwd_bwd_solves_per_s": nfld * 1000.0 / (ms_f + ms_b)}
+    for b, c in ((0, 0), (31, 63)):
+        _sample(samples, "layer_32x64x256x256_bf16", "grad", _h(out[b, c]), p.M, p.N, gx=_h(tx[b, c]),
+                gy=_h(ty[b, c]))
+        _sample(samples, "layer_32x64x256x256_bf16", "bwd", (_h(gx_[b, c]), _h(gy_[b, c])), p.M, p.N,
+                gout=_h(go[b, c]))
     p.close()
-    res["edit_100x801x1200_fp32"] = _edit_workload(dev)
-    res["exact_809x1208_100x801x1200_fp32"] = _exact_workload(dev)
-    res["backward_100x801x1200_fp32"] = _backward_workload(dev)
+    del tx, ty, go, out, gx_, gy_
+    res["edit_100x801x1200_fp32"] = _edit_workload(dev, samples)
+    res["exact_809x1208_100x801x1200_fp32"] = _exact_workload(dev, samples)
+    res["backward_100x801x1200_fp32"] = _backward_workload(dev, samples)
     res["cufft_comparison_100x801x1200_fp32"] = _cufft_comparison(dev)
+    return res
+
+
+def _ragged_workload(dev, samples):
+    """64 items of uneven sizes (seeded, built like the benchmark fields) as one ragged
+    plan, plain and as a captured graph, against 64 sequential plain solves."""
+    import torch
+
+    from paper_1902_00176_gb300 import gfc, synth
+
+    items = synth.ragged_items()
+    rp = gfc.RaggedPlan(items, device=dev)
+    gxr, gyr = rp.empty(), rp.empty()
+    for i, ((c, h, w), o) in enumerate(zip(items, rp.offsets)):
+        a, b = synth.ragged_item_gradients((c, h, w), i)
+        gxr[o:o + c * h * w] = torch.from_numpy(a).reshape(-1).to(dev)
+        gyr[o:o + c * h * w] = torch.from_numpy(b).reshape(-1).to(dev)
+    outr = rp.empty()
+    ms = _time_ms(lambda: rp.solve_from_gradient(gxr, gyr, outr), dev, 5)
+    gr = gfc.Graph(rp, "gradient", gxr, gyr, outr)
+    msg = _time_ms(gr.launch, dev, 5)
+    plans = [gfc.Plan(h, w, c, 1, device=dev) for c, h, w in items]
+    outs = rp.empty()
+    views = [(gxr[o:o + c * h * w].view(1, c, h, w), gyr[o:o + c * h * w].view(1, c, h, w),
+              outs[o:o + c * h * w].view(1, c, h, w)) for (c, h, w), o in zip(items, rp.offsets)]
+
+    def seq():
+        for pl, (a, b, o) in zip(plans, views):
+            pl.solve_from_gradient(a, b, o)
+
+    ms_seq = _time_ms(seq, dev, 3)
+    nf = sum(c for c, h, w in items)
+    peak = _peaks()[0]
+    nbytes = sum(12 * c * h * w + 4 * padded_size(h, w)[0] * (padded_size(h, w)[1] // 2 + 1) for c, h, w in items)
+    res = {"fields": nf, "ms": ms, "ms_graph": msg, "solves_per_s": nf * 1000.0 / ms,
+           "ms_sequential_plans": ms_seq, "speedup_vs_sequential": ms_seq / ms, "min_bytes": nbytes,
+           "frac_of_hbm": nbytes / (ms / 1000.0) / 1e9 / peak}
+    # two items (smallest and largest) for the oracle-error leg
+    areas = [h * w for c, h, w in items]
+    for i in (areas.index(min(areas)), areas.index(max(areas))):
+        c, h, w = items[i]
+        o = rp.offsets[i]
+        M, N = padded_size(h, w)
+        v = lambda t: t[o:o + h * w].view(h, w)
+        _sample(samples, "ragged_64_items", "grad", _h(v(outr)), M, N, gx=_h(v(gxr)), gy=_h(v(gyr)))
+    gr.close()
+    rp.close()
+    for pl in plans:
+        pl.close()
     return res
 
 
@@ -489,14 +646,14 @@ def _cufft_comparison(dev):
             "speedup_vs_cufft": ms / ms_lib, "rel_l2_library_vs_cufft": rel}
 
 
-def _backward_workload(dev):
+def _backward_workload(dev, samples):
     """The hand-written adjoint (gfc_backward) on the benchmark shape, beside the forward."""
     import torch
 
-    from paper_1902_00176_gb300 import gfc
+    from paper_1902_00176_gb300 import gfc, synth
 
     B, H, W = 100, 801, 1200
-    go = torch.randn(B, 1, H, W, device=dev)
+    go = torch.from_numpy(synth.upstream_gradient((B, 1, H, W), seed=4700)).to(dev)
     gx, gy = torch.empty_like(go), torch.empty_like(go)
     p = gfc.Plan(H, W, 1, B, device=dev)
     ms_b = _time_ms(lambda: p.backward(go, gx, gy), dev, 10)
@@ -510,6 +667,7 @@ def _backward_workload(dev):
         p.backward(go, gx, gy)
     prof = p.profile()
     p.set_profiling(False)
+    _sample(samples, "backward_100x801x1200_fp32", "bwd", (_h(gx[7, 0]), _h(gy[7, 0])), p.M, p.N, gout=_h(go[7, 0]))
     p.close()
     peak, kind = _peaks()
     min_bytes = 3 * 4 * H * W * B + 4 * p.M * (p.N // 2 + 1)
@@ -523,19 +681,22 @@ def _backward_workload(dev):
             "peak_kind": kind, "backward_passes": passes}
 
 
-def _exact_workload(dev):
+def _exact_workload(dev, samples):
     """Algorithm A's exact padded size (809 x 1208, Bluestein transforms) on the
     benchmark batch, against the SMOOTH size (810 x 1250)."""
     import torch
 
-    from paper_1902_00176_gb300 import gfc
+    from paper_1902_00176_gb300 import gfc, synth
 
     B, H, W = 100, 801, 1200
-    gx = torch.rand(B, 1, H, W, device=dev) - 0.5
-    gy = torch.rand(B, 1, H, W, device=dev) - 0.5
+    ax, ay = synth.perturbed_gradient_batch(batch=B, H=H, W=W, seed=1000)
+    gx, gy = torch.from_numpy(ax).to(dev), torch.from_numpy(ay).to(dev)
+    del ax, ay
     p = gfc.Plan(H, W, 1, B, device=dev, exact=True)
     out = torch.empty_like(gx)
     ms = _time_ms(lambda: p.solve_from_gradient(gx, gy, out), dev, 5)
+    _sample(samples, "exact_809x1208_100x801x1200_fp32", "grad", _h(out[3, 0]), H + 8, W + 8, gx=_h(gx[3, 0]),
+            gy=_h(gy[3, 0]))
     bx, by = torch.empty_like(gx), torch.empty_like(gx)
     ms_b = _time_ms(lambda: p.backward(out, bx, by), dev, 5)
     p.close()
@@ -543,7 +704,7 @@ def _exact_workload(dev):
             "ms_backward_per_batch": ms_b}
 
 
-def _edit_workload(dev):
+def _edit_workload(dev, samples):
     """The editing steps of Sec. 2.3.2 / Sec. 3.2 on 100 fields of 801x1200 (4 distinct images tiled)."""
     import torch
 
@@ -588,10 +749,16 @@ def _edit_workload(dev):
 
     ms = _time_ms(fused, dev, 5)
     res["threshold_solve_correct_fused"] = {"ms": ms, "solves_per_s": B * 1000.0 / ms}
+    _sample(samples, "edit_100x801x1200_fp32", "correct", _h(out[1, 0]), p.M, p.N, gx=_h(tx[1, 0]), gy=_h(ty[1, 0]),
+            img=_h(timg[1, 0]), frac=0.1)
     ms = _time_ms(lambda: p.solve_edited(tx, ty, "threshold", frac=0.1, out=out), dev, 5)
     res["solve_threshold_fused"] = {"ms": ms, "solves_per_s": B * 1000.0 / ms}
+    _sample(samples, "edit_100x801x1200_fp32", "threshold", _h(out[2, 0]), p.M, p.N, gx=_h(tx[2, 0]),
+            gy=_h(ty[2, 0]), frac=0.1)
     ms = _time_ms(lambda: p.solve_edited(tx, ty, "merge", alpha=0.5, edges=te, out=out), dev, 5)
     res["solve_merge_fused"] = {"ms": ms, "solves_per_s": B * 1000.0 / ms}
+    _sample(samples, "edit_100x801x1200_fp32", "merge", _h(out[3, 0]), p.M, p.N, gx=_h(tx[3, 0]), gy=_h(ty[3, 0]),
+            edges=_h(te[3, 0]), alpha=0.5)
     p.close()
     return res
 
@@ -639,6 +806,13 @@ def main():
         args.warmup = 3
     global B
     B = args.batch
+    try:
+        cmd = torchrun_command(args.gpus, sys.argv[1:], os.environ)
+    except ValueError as e:
+        print(f"bench.py: {e}", file=sys.stderr)
+        sys.exit(2)
+    if cmd is not None:  # --gpus N outside a distributed job: run N ranks of this script
+        sys.exit(subprocess.call(cmd))
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

@@ -196,21 +196,29 @@ gfc_status gfc_plan_get_profile(gfc_plan* plan, gfc_profile* out, int reset);
  * device memory: plug-ins whose host application owns all device memory,
  * fixed-budget real-time or embedded pipelines, and latency-bound loops where
  * cudaMalloc/cudaFree would synchronise the device. The paper has no
- * counterpart; it computes exactly what gfc_solve_from_gradient computes for
- * FP32 storage, pad 4 and the SMOOTH size policy, without a plan.
- * gx, gy, out: `fields` contiguous H x W FP32 fields in device memory (the
- * caller still owns inputs and outputs), 16-byte aligned; runs on `stream`
- * (cudaStream_t), asynchronously, one field at a time.
+ * counterpart. It solves the problem gfc_solve_from_gradient solves for FP32
+ * storage, pad 4 and the SMOOTH size policy, without a plan, on the generic
+ * shared-memory passes only (never the register-resident ones a plan uses for
+ * some sizes), so the two agree to FP32 rounding (the tests hold them to 1e-5
+ * relative L2 and 1e-4 max-abs), not bit for bit.
+ * gx, gy, out: `fields` contiguous H x W FP32 fields in device memory of the
+ * current device (the caller still owns inputs and outputs), 16-byte aligned;
+ * runs on `stream` (cudaStream_t of the current device), asynchronously, one
+ * field at a time.
  * Working memory is one library-owned static device array of about 24 MiB that
  * every GPU loading this library holds until the process exits. It limits the
- * padded size to M x (N/2+1) <= 2^21 (about 2040 x 2040 images); larger sizes
- * return GFC_ERR_UNSUPPORTED. The first call on a device looks up the array's
- * device address (cudaGetSymbolAddress, which may load the module), so make
- * that first call before any stream capture. Every call rebuilds the Green
- * spectrum and twiddle tables in the array and clears its error word; all
- * calls share the array, so calls that overlap on the GPU (other streams,
- * other threads) race and must be serialised by the caller. Calls no
- * cudaMalloc, cudaFree or allocating library routine. */
+ * padded size to M x ldS <= 2^21 complex elements, where ldS is N/2 + 1
+ * rounded up to a multiple of 4 (square images up to 2008 x 2008, which pad
+ * to 2016 x 2016); larger sizes return GFC_ERR_UNSUPPORTED before anything is
+ * launched. The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress, which may
+ * load the module; the lookup is guarded by a mutex, so first calls from
+ * several host threads are safe), so make that first call before any stream
+ * capture. Every call rebuilds the Green spectrum and twiddle tables in the
+ * array and clears its error word; all calls share the array, so calls that
+ * overlap on the GPU (other streams, other threads) race and must be
+ * serialised by the caller. Calls no cudaMalloc, cudaFree or allocating
+ * library routine. */
 gfc_status gfc_solve_from_gradient_noalloc(int H, int W, int fields, const void* gx, const void* gy, void* out,
                                            void* stream);
 

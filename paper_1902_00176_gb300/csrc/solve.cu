@@ -931,6 +931,7 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
 constexpr int kNoAllocMaxDevices = 64;
 static void* g_noalloc_base[kNoAllocMaxDevices];
+static std::mutex g_noalloc_mu;  // guards g_noalloc_base (first calls from several host threads)
 
 // Device address of g_noalloc_scratch on the current device, looked up once
 // per device (the host-side name of the array is only a stand-in; kernels must
@@ -940,6 +941,7 @@ static gfc_status noalloc_base(void** out) {
   GFC_CUDA_TRY(cudaGetDevice(&dev));
   if (dev < 0 || dev >= kNoAllocMaxDevices)
     return fail(GFC_ERR_UNSUPPORTED, "gfc_solve_from_gradient_noalloc: device %d out of range", dev);
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
   if (!g_noalloc_base[dev]) {
     void* p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
@@ -968,10 +970,12 @@ extern "C" gfc_status gfc_solve_from_gradient_noalloc(int H, int W, int fields, 
   P.H = H; P.W = W; P.C = 1; P.batch = fields; P.pad = 4; P.dtype = GFC_F32;
   P.M = M; P.N = N; P.Nh = N / 2 + 1; P.ldS = (P.Nh + 3) & ~3; P.chunk = 1; P.nslots = 1;
   P.spec_field = (size_t)M * P.ldS;
+  // the limit the header states: M x ldS <= 2^21 with ldS = N/2 + 1 rounded up to a multiple of 4
   if ((size_t)M * P.ldS > kNoAllocSpecElems || (size_t)M * P.Nh > kNoAllocGreenElems)
     return fail(GFC_ERR_UNSUPPORTED,
-                "gfc_solve_from_gradient_noalloc: padded size %dx%d needs %zu spectrum elements, the static "
-                "scratch holds %zu (about 2040x2040 images at most)",
+                "gfc_solve_from_gradient_noalloc: padded size %dx%d needs M x ldS = %zu spectrum elements "
+                "(ldS = N/2+1 rounded up to a multiple of 4), the static scratch holds %zu (square images up "
+                "to 2008x2008)",
                 M, N, (size_t)M * P.ldS, kNoAllocSpecElems);
   if (!make_fft_plan(N, &P.rowplan) || !make_fft_plan(M, &P.colplan))
     return fail(GFC_ERR_UNSUPPORTED, "gfc_solve_from_gradient_noalloc: no FFT schedule for %dx%d", M, N);

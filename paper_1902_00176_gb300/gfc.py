@@ -373,14 +373,20 @@ def solve_laplacian(lap: torch.Tensor) -> torch.Tensor:
 
 
 def solve_noalloc(gx: torch.Tensor, gy: torch.Tensor, out: torch.Tensor) -> torch.Tensor:
-    """FP32 solve through the allocation-free entry point (no plan; ``out`` preallocated by the caller)."""
+    """FP32 solve through the allocation-free entry point (no plan; ``out`` preallocated by the caller).
+
+    The three tensors must live on one CUDA device; the call runs with that
+    device current and on its current torch stream."""
     b = _as_bchw(gx)
     for t in (gx, gy, out):
         if not t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous() or t.shape != gx.shape:
             raise ValueError("gx, gy, out must be contiguous float32 CUDA tensors of one shape")
-    _check(lib().gfc_solve_from_gradient_noalloc(b.shape[2], b.shape[3], b.shape[0] * b.shape[1], gx.data_ptr(),
-                                                 gy.data_ptr(), out.data_ptr(),
-                                                 ctypes.c_void_p(_stream_ptr(gx.device))))
+    if gy.device != gx.device or out.device != gx.device:
+        raise ValueError(f"gx, gy, out must be on one device (got {gx.device}, {gy.device}, {out.device})")
+    with torch.cuda.device(gx.device):
+        _check(lib().gfc_solve_from_gradient_noalloc(b.shape[2], b.shape[3], b.shape[0] * b.shape[1],
+                                                     gx.data_ptr(), gy.data_ptr(), out.data_ptr(),
+                                                     ctypes.c_void_p(_stream_ptr(gx.device))))
     return out
 
 

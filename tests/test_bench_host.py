@@ -36,3 +36,49 @@ def test_traffic_withheld_when_missing_or_malformed(tmp_path):
 def test_build_id_tracks_the_cuda_sources():
     a = bench._kernel_build_id()
     assert len(a) == 16 and a == bench._kernel_build_id()
+
+
+def test_pure_python_size_rule_matches_the_library(gfc_lib):
+    """The oracle legs take (M, N) from bench.padded_size so they never load the
+    product library; it must agree with the library's SMOOTH policy."""
+    from paper_1902_00176_gb300 import gfc
+
+    for H, W in [(801, 1200), (64, 96), (1024, 1536), (256, 256), (2, 2), (13, 7), (2000, 2000), (2040, 2048),
+                 (127, 1999), (600, 333)]:
+        assert bench.padded_size(H, W) == gfc.padded_size(H, W), (H, W)
+
+
+def test_gpus_flag_relaunches_under_torchrun_outside_a_job():
+    cmd = bench.torchrun_command(4, ["--gpus", "4", "--steps", "5"], {}, python="py")
+    assert cmd[:3] == ["py", "-m", "torch.distributed.run"]
+    assert "--nproc-per-node=4" in cmd and "127.0.0.1" in cmd
+    assert cmd[-4:] == ["--gpus", "4", "--steps", "5"]
+    assert cmd[-5].endswith("bench.py")
+
+
+def test_gpus_flag_inside_a_job():
+    assert bench.torchrun_command(1, [], {}) is None
+    assert bench.torchrun_command(2, [], {"WORLD_SIZE": "2"}) is None
+    import pytest
+
+    with pytest.raises(ValueError):
+        bench.torchrun_command(8, [], {"WORLD_SIZE": "2"})
+
+
+def test_oracle_error_leg_on_cpu():
+    """The oracle-error leg compares recorded fields with the oracle (a field equal to
+    the oracle's own result has zero error; a perturbed one does not)."""
+    import numpy as np
+
+    import oracle.gfc_oracle as O
+
+    rng = np.random.default_rng(0)
+    gx, gy = rng.uniform(-0.1, 0.1, (2, 12, 9))
+    M, N = bench.padded_size(12, 9)
+    ref = O.solve_from_gradient(gx, gy, M, N, 4)
+    smp = []
+    bench._sample(smp, "a", "grad", ref.copy(), M, N, gx=gx, gy=gy)
+    bench._sample(smp, "b", "grad", ref + 1e-3, M, N, gx=gx, gy=gy)
+    e = bench.oracle_errors(smp)
+    assert e["a"]["rel_l2"] < 1e-14 and e["a"]["fields"] == 1
+    assert abs(e["b"]["max_abs"] - 1e-3) < 1e-9

@@ -14,6 +14,7 @@ import numpy as np
 import pytest
 import torch
 
+import oracle.gfc_oracle as O
 from paper_1902_00176_gb300 import gfc, synth
 
 pytestmark = pytest.mark.gpu
@@ -48,9 +49,56 @@ def test_noalloc_matches_plan_entry_on_two_calls_in_a_row(gfc_lib, B, H, W):
     plan.close()
 
 
+def test_noalloc_python_wrapper_matches_oracle(gfc_lib):
+    """Through gfc.solve_noalloc (with its input checks) against the FP64 oracle."""
+    _, gx, gy = synth.gradient_removal_image(seed=0, H=64, W=96)
+    tx = torch.from_numpy(gx).to(DEV).view(1, 1, 64, 96)
+    ty = torch.from_numpy(gy).to(DEV).view(1, 1, 64, 96)
+    out = torch.full_like(tx, float("nan"))
+    gfc.solve_noalloc(tx, ty, out)
+    torch.cuda.synchronize()
+    M, N = gfc.padded_size(64, 96)
+    ref = O.solve_from_gradient(gx.astype(np.float64), gy.astype(np.float64), M, N, 4)
+    got = out.double().cpu().numpy()[0, 0]
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= REL_F32
+    assert np.abs(got - ref).max() <= MAXABS_F32
+    with pytest.raises(ValueError):
+        gfc.solve_noalloc(tx, ty, out.double())
+    with pytest.raises(ValueError):
+        gfc.solve_noalloc(tx, ty.cpu(), out)
+
+
+def test_noalloc_near_the_static_limit_matches_plan_entry(gfc_lib):
+    """A padded size close to the 2^21-element limit (2000 x 2000 -> 2016 x 2016,
+    M x ldS = 2016 x 1012), routed to the generic passes by the plan as well."""
+    H = W = 2000
+    M, N = gfc.padded_size(H, W)
+    ldS = (N // 2 + 1 + 3) // 4 * 4
+    assert M * ldS <= 1 << 21 and M * ldS > 0.9 * (1 << 21)
+    gx, gy = synth.perturbed_gradient_batch(batch=1, H=H, W=W, seed=31000)
+    tx = torch.from_numpy(gx).to(DEV)
+    ty = torch.from_numpy(gy).to(DEV)
+    plan = gfc.Plan(H, W, 1, 1, device=DEV)
+    ref = plan.solve_from_gradient(tx, ty).double().cpu().numpy()
+    plan.close()
+    for _ in range(2):
+        out = torch.full_like(tx, float("nan"))
+        got = _noalloc(gfc_lib, tx, ty, out)
+        torch.cuda.synchronize()
+        got = got.double().cpu().numpy()
+        assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= REL_F32
+        assert np.abs(got - ref).max() <= MAXABS_F32
+
+
 def test_noalloc_rejects_sizes_beyond_its_static_scratch(gfc_lib):
-    x = torch.zeros((1, 1, 16, 16), device=DEV)
-    st = gfc_lib.gfc_solve_from_gradient_noalloc(2040, 2100, 1, x.data_ptr(), x.data_ptr() + 1024,
-                                                 x.data_ptr() + 2048, None)
+    # buffers that really hold the declared 2040 x 2100 field, so the call stays
+    # memory-safe whatever the static limit is
+    H, W = 2040, 2100
+    x = torch.zeros((1, 1, H, W), device=DEV)
+    y = torch.zeros_like(x)
+    o = torch.zeros_like(x)
+    st = gfc_lib.gfc_solve_from_gradient_noalloc(H, W, 1, x.data_ptr(), y.data_ptr(), o.data_ptr(), None)
     assert st == 2
     assert b"static scratch" in gfc_lib.gfc_last_error()
+    torch.cuda.synchronize()
+    assert not bool(o.any())  # nothing was launched
