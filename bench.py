@@ -324,19 +324,21 @@ def run_gfc(args, rank, world, local_rank):
     G_bytes = plan.M * (plan.N // 2 + 1) * 4
     min_bytes = 3 * 4 * fe * B + G_bytes  # read gx, gy, write out (fp32), read G once
     achieved = min_bytes / (ms_step / 1000.0) / 1e9
-    names = ["row pass (div + pad + row FFT)", "column pass (FFT, x G, inverse FFT)",
-             "inverse row pass (FFT, offset, crop)", "divergence pass (when not folded into the row pass)"]
+    names = ["row pass (div + pad + row FFT, band sums)", "band carry sweep (column recursion, u[0,0])",
+             "inverse row pass (column recursion in band, row FFT, offset, crop)",
+             "divergence pass (when not folded into the row pass)"]
     tot_ms = sum(prof["pass_ms"]) or 1.0
     # algorithmic bytes each pass moves per launch (its inputs read and outputs
-    # written once): gradient 8 B/pixel, output 4 B/pixel, packed rows, the
-    # column-major spectrum and the row-major Y at the plan's padded strides
+    # written once): gradient 8 B/pixel, output 4 B/pixel, the row-major spectrum
+    # S of the H + 1 support rows, and per band of 10 rows (F = 5 row pairs on the
+    # 810 x 1250 schedule) two sums per column, replaced by two carries
     ld4 = lambda n: (n + 3) // 4 * 4
     nh = plan.N // 2 + 1
-    spec_b = nh * ld4(plan.M) * 8
-    y_b = H * ld4(nh) * 8
+    s_b = (H + 1) * ld4(nh) * 8
+    band_b = 2 * ((H + 1 + 9) // 10) * ld4(nh) * 8
     z_b = ((H + 2) // 2) * ld4(plan.N) * 8
     fused = prof["launches"][3] == 0
-    pass_bytes = [B * ((8 * fe if fused else z_b) + spec_b), B * (spec_b + y_b) + G_bytes, B * (y_b + 4 * fe),
+    pass_bytes = [B * ((8 * fe if fused else z_b) + s_b + band_b), B * 2 * band_b, B * (s_b + band_b + 4 * fe),
                   B * (8 * fe + z_b)]
     per_kernel = []
     for i in range(4):

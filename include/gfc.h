@@ -68,6 +68,21 @@ typedef enum {
  * solves, edited solves and the adjoint (gfc_backward) on that torus. */
 typedef enum { GFC_SIZE_SMOOTH = 0, GFC_SIZE_EXACT = 1 } gfc_size_policy;
 
+/* How the column direction of Eq. 23's Green multiply is applied on the
+ * register-resident sizes (the row direction is always the real FFT).
+ * GFC_COLUMN_RECURSIVE: after the row transforms, column l of the Green
+ * spectrum 1/lambda(k, l) is the inverse of the cyclic tridiagonal operator
+ * S + S^-1 - b_l along the torus rows (b_l = 4 - 2 cos(2 pi l / N)); it is
+ * applied as convolution with that column's Green's function, a two-sided
+ * geometric sequence, by one causal and one anticausal first-order recursion
+ * (bands of rows with carries swept around the cycle; column l = 0, where the
+ * operator is singular, is solved exactly with its mean removed, the reading
+ * G[0,0] = 0). Same operator as the column FFTs, O(M) per column instead of
+ * two length-M transforms, no spectrum transpose. Used by solves and edited
+ * solves; gfc_backward runs the column transforms.
+ * GFC_COLUMN_FFT: column FFT, multiply by G, inverse column FFT. */
+typedef enum { GFC_COLUMN_RECURSIVE = 0, GFC_COLUMN_FFT = 1 } gfc_column_solver;
+
 typedef struct {
   int H, W;          /* image height and width, each >= 2 */
   int C, batch;      /* channels and batch size, each >= 1 */
@@ -78,6 +93,7 @@ typedef struct {
   void* stream;      /* cudaStream_t to run on; NULL = the legacy default stream */
   int streams;       /* chunks in flight at once (1..4), each on an internal stream
                         forked from and joined back into the plan's stream; 0 = auto */
+  int column_solver; /* gfc_column_solver (register-resident sizes only) */
 } gfc_plan_opts;
 
 /* One item of a ragged batch: C fields of H x W, stored contiguously

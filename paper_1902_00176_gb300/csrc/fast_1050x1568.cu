@@ -14,4 +14,6 @@ cudaError_t fast_run_1050x1568(gfc_plan* P, const Bufs& bf, int mode, const void
 
 size_t fast_zbuf_1050x1568(int H) { return fast_zbuf_elems_for<RowS_1050x1568>(H); }
 
+int fast_items_1050x1568() { return RowS_1050x1568::F; }
+
 }  // namespace gfc

@@ -14,4 +14,6 @@ cudaError_t fast_run_270x270(gfc_plan* P, const Bufs& bf, int mode, const void* 
 
 size_t fast_zbuf_270x270(int H) { return fast_zbuf_elems_for<RowS_270x270>(H); }
 
+int fast_items_270x270() { return RowS_270x270::F; }
+
 }  // namespace gfc

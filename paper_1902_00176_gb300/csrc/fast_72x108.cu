@@ -14,4 +14,6 @@ cudaError_t fast_run_72x108(gfc_plan* P, const Bufs& bf, int mode, const void* i
 
 size_t fast_zbuf_72x108(int H) { return fast_zbuf_elems_for<RowS_72x108>(H); }
 
+int fast_items_72x108() { return RowS_72x108::F; }
+
 }  // namespace gfc

@@ -14,4 +14,6 @@ cudaError_t fast_run_810x1250(gfc_plan* P, const Bufs& bf, int mode, const void*
 
 size_t fast_zbuf_810x1250(int H) { return fast_zbuf_elems_for<RowS_810x1250>(H); }
 
+int fast_items_810x1250() { return RowS_810x1250::F; }
+
 }  // namespace gfc

@@ -66,7 +66,35 @@ struct FastArgs {
   int nf;            // fields in this chunk
   int ldY;           // row stride of the row-major spectrum Y (complex elements)
   int* err;          // the plan's device error word (bounded waits that run out)
+  // recursive column solve (row-major spectrum S, bands of 2F rows from torus row p)
+  int srows;         // rows of S per field (2 zpairs; rows past the support are zero)
+  int G;             // bands per field
+  size_t tri_field;  // complex elements per field of the band scratch
 };
+
+// Band scratch of one field (recursive column solve), complex elements:
+//   carries [G][2][ldY]: row 0 of band g the causal carry into the band, row 1
+//           the anticausal carry from below it (the sweep; read by pass C);
+//   sums    [nkb][G][2][32]: the bands' causal and anticausal sums with zero
+//           carries (pass A), in tiles of 32 columns, so that a tile is one
+//           contiguous copy for the sweep;
+//   col0    srows floats: the real parts of column 0 of S (pass A).
+// The row-major spectrum S holds 2F rows per band; the sweep writes column 0's
+// exact solution into it.
+// (The plan sizes this per field in tri_field.)
+constexpr int kTriCols = 32;
+__device__ __forceinline__ float2* tri_sums(float2* tri, int field, const FastArgs& A) {
+  return tri + (size_t)field * A.tri_field + (size_t)2 * A.G * A.ldY;
+}
+__device__ __forceinline__ float* tri_col0(float2* tri, int field, const FastArgs& A) {
+  const size_t nkb = (size_t)(A.ldY + kTriCols - 1) / kTriCols;
+  return reinterpret_cast<float*>(tri_sums(tri, field, A) + nkb * 2 * A.G * kTriCols);
+}
+// one step of y <- x + a y with a = 1 - delta, as (x + y) - delta y: delta is
+// held to full relative precision, so the pole near DC is not rounded away
+__device__ __forceinline__ float2 tri_step(float2 x, float2 y, float delta) {
+  return make_float2(fmaf(-delta, y.x, x.x + y.x), fmaf(-delta, y.y, x.y + y.y));
+}
 
 __device__ __forceinline__ float f_to_f(float x) { return x; }
 __device__ __forceinline__ float f_to_f(__half x) { return __half2float(x); }
@@ -113,7 +141,10 @@ struct RowShape {
   static_assert(R1 % R2 == 0 || R1 < R2, "row schedule needs R2 | R1 or R1 < R2");
   static constexpr int NO = N + 1;        // stage-2 output buffer stride (natural order)
   static constexpr int WMIN = cx_min_width(N);
+  static constexpr int LDY_ = ((N / 2 + 1) + 3) & ~3;  // row stride of Y and S (complex)
   static constexpr size_t smem_bytes() { return (size_t)(R1 * R2 + F * NP) * sizeof(float2); }
+  static constexpr int CBUF = ((R1 * R2 + F * NP) + 1) & ~1;  // 16-byte aligned offset of the carry rows
+  static constexpr size_t smem_bytes_tri_inv() { return (size_t)(CBUF + 2 * LDY_) * sizeof(float2); }
   static constexpr size_t smem_bytes_fwd() { return (size_t)(R1 * R2 + F * NP + F * NO) * sizeof(float2); }
   // blocks per SM the register allocation must allow: long rows fill shared
   // memory at 2 (3 for the inverse pass); short rows leave room for 4
@@ -122,7 +153,7 @@ struct RowShape {
   // adjoint inverse row pass: twiddles, exchange, the factor table
   // 1 - exp(2 pi i l / N) for l <= N/2, then (16-byte aligned) the F + 1 rows of
   // Y an item needs, LDY complex each
-  static constexpr int LDY = ((N / 2 + 1) + 3) & ~3;
+  static constexpr int LDY = LDY_;
   static constexpr size_t adj_stage_offset() {
     return (((size_t)(R1 * R2 + F * NP + (N / 2 + 1)) * sizeof(float2)) + 15) / 16 * 16;
   }
@@ -384,6 +415,54 @@ __global__ void __launch_bounds__(512) k_fast_div_edit(const T* __restrict__ gx,
 }
 
 // ---------------------------------------------------------------------------
+// Recursive column solve, pass A side: the item's 2F rows of the spectrum, from
+// the F packed transforms in buf2 (two-for-one split), stored row-major
+// (S[row][l], row = image-relative torus row), and per column l the item's
+// band sums with zero carries,
+//   e  = sum_r a^(nb-1-r) X[r]   (causal recursion y = X + a y run down the band)
+//   e' = sum_r a^r X[r]          (anticausal recursion run up the band),
+// over the nb band rows that lie on the torus. Thread t takes columns t, t +
+// blockDim, ...: the row stores and sums are coalesced across threads.
+// ---------------------------------------------------------------------------
+template <class S>
+__device__ __forceinline__ void tri_store_item(const float2* buf2, float2* __restrict__ spec, float2* __restrict__ tri,
+                                               const float* __restrict__ cc, int field, int g, const FastArgs& A) {
+  constexpr int RW = 2 * S::F;
+  float2* Sr = spec + ((size_t)field * A.srows + (size_t)g * RW) * A.ldY;
+  float2* sums = tri_sums(tri, field, A);
+  const int nb = min(RW, A.M - A.p - g * RW);
+  for (int k = threadIdx.x; k < A.Nh; k += blockDim.x) {
+    float2* te = sums + ((size_t)(k / kTriCols) * A.G + g) * 2 * kTriCols + (k % kTriCols);  // tile of column k
+    float2* tp = te + kTriCols;
+    const int km = k == 0 ? 0 : S::N - k;
+    float2 x[RW];
+#pragma unroll
+    for (int q = 0; q < S::F; ++q) {
+      const float2 zk = buf2[q * S::NO + k], zm = buf2[q * S::NO + km];
+      x[2 * q] = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
+      x[2 * q + 1] = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
+    }
+#pragma unroll
+    for (int r = 0; r < RW; ++r) Sr[(size_t)r * A.ldY + k] = x[r];
+    if (k == 0) {
+      float* c0 = tri_col0(tri, field, A) + (size_t)g * RW;
+#pragma unroll
+      for (int r = 0; r < RW; ++r) c0[r] = x[r].x;
+    }
+    const float dl = __ldg(cc + (size_t)k * 8);
+    float2 e = make_float2(0.0f, 0.0f), ep = make_float2(0.0f, 0.0f);
+#pragma unroll
+    for (int r = 0; r < RW; ++r)
+      if (r < nb) e = tri_step(x[r], e, dl);
+#pragma unroll
+    for (int r = RW - 1; r >= 0; --r)
+      if (r < nb) ep = tri_step(x[r], ep, dl);
+    *te = e;
+    *tp = ep;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // pass A: forward row transforms of the packed rows + two-for-one split +
 // transposed store. Persistent over (field, group of F row pairs). The F packed
 // rows of an item are one contiguous bulk copy into the exchange buffer,
@@ -391,10 +470,12 @@ __global__ void __launch_bounds__(512) k_fast_div_edit(const T* __restrict__ gx,
 // this item's stage-2 inputs are read, so it overlaps the stage-2 transforms
 // and the transposed store of the spectrum.
 // ---------------------------------------------------------------------------
-template <class S>
+template <class S, bool TRI>
 __global__ void __launch_bounds__(S::THREADS, S::MINB_FWD) k_fast_rows_fwd(const float2* __restrict__ z,
                                                                  float2* __restrict__ spec,
-                                                                 const float2* __restrict__ twg, FastArgs A) {
+                                                                 const float2* __restrict__ twg, FastArgs A,
+                                                                 float2* __restrict__ tri,
+                                                                 const float* __restrict__ cc) {
   extern __shared__ __align__(16) float2 sm[];
   float2* tw2 = sm;                   // [R1][R2]: w_N^(r j)
   float2* buf = sm + S::R1 * S::R2;   // staged packed rows [F][ldz], then the exchange (m -> m + m / R1)
@@ -467,6 +548,10 @@ __global__ void __launch_bounds__(S::THREADS, S::MINB_FWD) k_fast_rows_fwd(const
       }
     }
     __syncthreads();  // stage-2 results visible
+    if constexpr (TRI) {
+      tri_store_item<S>(buf2, spec, tri, cc, field, g, A);
+      continue;
+    }
     if (g == 0) {
       // rows of every column outside the support [p, p + nrows) are zero, so the
       // column pass loads whole columns without range checks
@@ -522,12 +607,15 @@ __host__ __device__ constexpr size_t fused_exchange_bytes() {
   return (size_t)(S::F * S::NP + S::F * S::NO) * sizeof(float2);
 }
 
-template <class S, typename T, bool ADJ>
+template <class S, typename T, bool ADJ, bool TRI>
 __global__ void __launch_bounds__(S::THREADS, S::MINB_FWD) k_fast_rows_fwd_div(const T* __restrict__ gx,
                                                                      const T* __restrict__ gy,
                                                                      float2* __restrict__ spec,
                                                                      const float2* __restrict__ twg,
-                                                                     float* __restrict__ partial, FastArgs A) {
+                                                                     float* __restrict__ partial, FastArgs A,
+                                                                     float2* __restrict__ tri,
+                                                                     const float* __restrict__ cc) {
+  static_assert(!(ADJ && TRI), "the adjoint runs the column transforms");
   extern __shared__ __align__(16) float2 sm[];
   float2* tw2 = sm;
   float2* buf = sm + S::R1 * S::R2;
@@ -655,6 +743,9 @@ __global__ void __launch_bounds__(S::THREADS, S::MINB_FWD) k_fast_rows_fwd_div(c
       }
     }
     __syncthreads();  // stage-2 results visible
+    if constexpr (TRI) {
+      tri_store_item<S>(buf2, spec, tri, cc, field, g, A);
+    } else {
     if (g == 0) {
       float2* Sz = spec + (size_t)field * A.Nh * A.ldM;
       const int nz = A.M - A.nrows;
@@ -680,6 +771,7 @@ __global__ void __launch_bounds__(S::THREADS, S::MINB_FWD) k_fast_rows_fwd_div(c
           if (two) dst[1] = xb;
         }
       }
+    }
     }
     fence_proxy_async_smem();  // this thread's accesses of the buffers precede the next bulk copies
     __syncthreads();
@@ -708,6 +800,176 @@ static __global__ void __launch_bounds__(32) k_adj_total(double* __restrict__ pa
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
   if (threadIdx.x == 0) pp[kAdjTotal] = a;
+}
+
+// ---------------------------------------------------------------------------
+// Recursive column solve, between the row passes. A block takes 32 columns of
+// one field and stages their band sums (all bands, both directions) in shared
+// memory; warp 0 sweeps the causal sums, warp 1 the anticausal ones, one lane
+// per column l >= 1:
+//   causal:     P_0 = 0, P_{g+1} = e_g + T_g P_g (T_g = a^(rows of band g));
+//               the rows after the last band (tail) and above band 0 (pad) are
+//               zero, so a^tail P_G = (1 - a^M) y[M-1] and the carry into band g
+//               is c_g = P_g + a^(2F g) a^p y[M-1];
+//   anticausal: Q_{G-1} = 0, Q_{g-1} = e'_g + T_g Q_g; a^p Q_{-1} = (1 - a^M) y'[0];
+//               the carry from below band g is Q_g + a^tail (prod_{j>g} T_j) y'[0]
+// (the powers from the plan's FP64 table). The carries replace the sums. Row 0
+// of the solved spectrum (a padding row, X = 0) is U[0][l] = C_l (a y[M-1] +
+// y'[0]); the block's FP64 sum of w_l Re U[0][l] (w = 1 at l = N/2, else 2) is
+// its partial of u[0,0], which the inverse row pass adds in block order.
+// Column 0 (b = 2, singular) is the 1D periodic Poisson problem with its mean
+// removed (the reading G[0,0] = 0): warp 2 of block 0 solves it exactly in
+// FP64 from prefix sums over the torus rows and writes it into S.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_exclusive_scan_d(double v) {
+  const int lane = threadIdx.x & 31;
+  double x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const double y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  return x - v;
+}
+
+constexpr int kTriMaxM = 2112;  // column 0 of the longest register-resident column
+
+// Column 0 of one field (warp-wide, FP64): d[r] = u[r+1] - u[r] has
+// d[r] - d[r-1] = f[r] - mean(f); periodicity fixes d[-1] = -sum_r G[r] / M with
+// G the prefix sums; u[0] = 0 (any constant is removed with u[0,0]: column 0
+// adds w_0 U[0][0] = u[0] / N = 0 to it). The column is read once into shared
+// memory; each lane then walks a contiguous run of torus rows; the solution
+// (1/N folded in) replaces column 0 of S.
+static __device__ __noinline__ void tri_column0(float2* __restrict__ spec, float* fcol, int field,
+                                                const FastArgs& A) {
+  // fcol[p + i] holds column 0 of S row i (bulk copy of pass A's compact copy);
+  // the other torus rows are zero
+  const int lane = threadIdx.x & 31;
+  float2* col = spec + (size_t)field * A.srows * A.ldY;
+  const int nr = min(A.srows, A.M - A.p);  // S rows on the torus
+  for (int r = lane; r < A.M; r += 32)
+    if (r < A.p || r >= A.p + nr) fcol[r] = 0.0f;
+  __syncwarp();
+  const int run = (A.M + 31) / 32;
+  const int r0 = min(lane * run, A.M), r1 = min(r0 + run, A.M);
+  double s0 = 0.0;
+  for (int r = r0; r < r1; ++r) s0 += (double)fcol[r];
+  const double mean = warp_sum_d(s0) / (double)A.M;
+  const double off = warp_exclusive_scan_d(s0 - mean * (double)(r1 - r0));
+  double Gr = off, Gs = 0.0;
+  for (int r = r0; r < r1; ++r) {
+    Gr += (double)fcol[r] - mean;
+    Gs += Gr;
+  }
+  const double D = -warp_sum_d(Gs) / (double)A.M;
+  double u = warp_exclusive_scan_d(D * (double)(r1 - r0) + Gs);
+  const double invN = 1.0 / (double)A.N;
+  Gr = off;
+  for (int r = r0; r < r1; ++r) {
+    const int i = r - A.p;
+    if (i >= 0 && i < nr) col[(size_t)i * A.ldY] = make_float2((float)(u * invN), 0.0f);
+    Gr += (double)fcol[r] - mean;
+    u += D + Gr;
+  }
+}
+
+static __global__ void __launch_bounds__(96) k_tri_carries(float2* __restrict__ spec, float2* __restrict__ tri,
+                                                          const float* __restrict__ cc,
+                                                          const float* __restrict__ powc,
+                                                          double* __restrict__ partial, FastArgs A) {
+  extern __shared__ __align__(16) float2 sm[];  // [G][2][kTriCols] band sums, then [2G][kTriCols] powers
+  float* pws = reinterpret_cast<float*>(sm + (size_t)2 * A.G * kTriCols);
+  __shared__ float2 y0s[kTriCols];
+  __shared__ __align__(16) float fcol[kTriMaxM + 4];  // block 0: column 0 of S (compact copy)
+  __shared__ __align__(8) uint64_t bar;
+  const int kb = blockIdx.x, field = blockIdx.y, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int k = kb * kTriCols + lane;
+  float2* tf = tri + (size_t)field * A.tri_field;
+  // stage this block's tile of band sums [G][2][32] and of powers [2G][32],
+  // and in block 0 the compact column 0, by three bulk copies on one barrier
+  const unsigned seg = (unsigned)(kTriCols * sizeof(float2)), pseg = (unsigned)(kTriCols * sizeof(float));
+  const int nr = min(A.srows, A.M - A.p);  // S rows on the torus
+  const unsigned cbytes = (unsigned)((nr * sizeof(float) + 15) & ~(size_t)15);
+  if (tid == 0) {
+    mbar_init(&bar, 1);
+    mbar_expect_tx(&bar, (seg + pseg) * (unsigned)(2 * A.G) + (kb == 0 ? cbytes : 0u));
+  }
+  __syncthreads();
+  if (tid == 0) {  // the tile of band sums, the tile of powers, block 0: column 0
+    bulk_copy(sm, tri_sums(tri, field, A) + (size_t)kb * 2 * A.G * kTriCols, (unsigned)(2 * A.G) * seg, &bar);
+    bulk_copy(pws, powc + (size_t)kb * 2 * A.G * kTriCols, (unsigned)(2 * A.G) * pseg, &bar);
+    if (kb == 0) bulk_copy(fcol + A.p, tri_col0(tri, field, A), cbytes, &bar);
+  }
+  // per-column constants, loaded while the copies are in flight
+  float4 c03 = make_float4(0.0f, 0.0f, 0.0f, 0.0f), c47 = c03;
+  if (warp < 2 && k >= 1 && k < A.Nh) {
+    c03 = __ldg(reinterpret_cast<const float4*>(cc + (size_t)k * 8));
+    c47 = __ldg(reinterpret_cast<const float4*>(cc + (size_t)k * 8) + 1);
+  }
+  const bool landed = mbar_wait(&bar, 0);
+  if (__syncthreads_or(!landed)) {  // the copies never completed: report, let them drain, stop
+    if (tid == 0) atomicExch(A.err, kErrBulkWait);
+    mbar_wait(&bar, 0);
+    return;
+  }
+  if (warp == 2 && kb == 0) tri_column0(spec, fcol, field, A);
+  const bool col_ok = warp < 2 && k >= 1 && k < A.Nh;
+  float2 yl = make_float2(0.0f, 0.0f);  // warp 0: y[M-1]
+  if (col_ok) {
+    const float Tb = c03.w, Tl = c47.x, Tp = c47.y, inv = c47.z, Tt = c47.w;
+    float2 t = make_float2(0.0f, 0.0f);
+    if (warp == 0) {
+#pragma unroll 8
+      for (int g = 0; g < A.G; ++g) {
+        const float T = (g == A.G - 1) ? Tl : Tb;
+        float2* slot = sm + (size_t)(2 * g) * kTriCols + lane;
+        const float2 e = *slot;
+        *slot = t;
+        t = make_float2(fmaf(T, t.x, e.x), fmaf(T, t.y, e.y));
+      }
+      yl = make_float2(Tt * t.x * inv, Tt * t.y * inv);        // y[M-1], past the tail rows
+      const float2 ci = make_float2(Tp * yl.x, Tp * yl.y);       // y[p-1]
+#pragma unroll 8
+      for (int g = 0; g < A.G; ++g) {
+        const float w = pws[(size_t)g * kTriCols + lane];
+        const float2 P = sm[(size_t)(2 * g) * kTriCols + lane];
+        tf[(size_t)(2 * g) * A.ldY + k] = make_float2(fmaf(w, ci.x, P.x), fmaf(w, ci.y, P.y));
+      }
+    } else {
+#pragma unroll 8
+      for (int g = A.G - 1; g >= 0; --g) {
+        const float T = (g == A.G - 1) ? Tl : Tb;
+        float2* slot = sm + (size_t)(2 * g + 1) * kTriCols + lane;
+        const float2 e = *slot;
+        *slot = t;
+        t = make_float2(fmaf(T, t.x, e.x), fmaf(T, t.y, e.y));
+      }
+      const float2 y0 = make_float2(Tp * t.x * inv, Tp * t.y * inv);  // y'[0]
+#pragma unroll 8
+      for (int g = 0; g < A.G; ++g) {
+        const float w = pws[(size_t)(A.G + g) * kTriCols + lane];
+        const float2 Q = sm[(size_t)(2 * g + 1) * kTriCols + lane];
+        tf[(size_t)(2 * g + 1) * A.ldY + k] = make_float2(fmaf(w, y0.x, Q.x), fmaf(w, y0.y, Q.y));
+      }
+      y0s[lane] = y0;
+    }
+  }
+  __syncthreads();
+  if (warp == 0) {
+    double acc = 0.0;
+    if (col_ok) {
+      const float a = c03.y, C = c03.z;
+      const float2 y0 = y0s[lane];
+      acc = (2 * k == A.N ? 1.0 : 2.0) * (double)(C * fmaf(a, yl.x, y0.x));
+    }
+    acc = warp_sum_d(acc);
+    if (lane == 0) partial[(size_t)field * (kMaxRowBlocks / 2) + kb] = acc;
+  }
 }
 
 template <class S, int MODE>
@@ -845,13 +1107,67 @@ __global__ void __launch_bounds__(S::THREADS, S::MINB) k_fast_cols(const float2*
 // copy for the next item is issued as soon as this item's stage-2 inputs are
 // in registers, so it overlaps the stage-2 transforms and the output stores.
 // ---------------------------------------------------------------------------
-template <class S, typename T>
+// Recursive column solve, pass C side: the 2F staged rows of band g (row-major
+// spectrum S) become rows of the solved spectrum U in place. Per column l >= 1,
+// from the band's two staged carries: the causal recursion down the band and
+// the anticausal one up it, U = C_l (y + y' - X). Column 0 already holds its
+// exact solution. Rows past the torus (band rows >= nb) are left alone: they
+// are below every image row.
+template <class S>
+__device__ __forceinline__ void tri_solve_band(float2* buf, const float2* cbuf, const float* __restrict__ cc, int g,
+                                               const FastArgs& A) {
+  constexpr int RW = 2 * S::F;
+  const int nb = min(RW, A.M - A.p - g * RW);
+  // thread t takes the column pair (2j, 2j + 1), 16-byte shared-memory accesses;
+  // column 0 (already solved) and columns >= Nh pass through unchanged
+  for (int j = threadIdx.x; 2 * j < A.Nh; j += blockDim.x) {
+    const int k0 = 2 * j;
+    const bool v0 = k0 >= 1, v1 = k0 + 1 < A.Nh;
+    // (delta, C) of both columns in one coalesced 16-byte load (the plan's compact table)
+    const float4 dc = __ldg(reinterpret_cast<const float4*>(cc + (size_t)A.Nh * 8) + j);
+    const float dl0 = dc.x, C0 = v0 ? dc.y : 1.0f, dl1 = dc.z, C1 = v1 ? dc.w : 1.0f;
+    const float4 yc4 = reinterpret_cast<const float4*>(cbuf)[j];
+    const float4 ya4 = reinterpret_cast<const float4*>(cbuf + S::LDY)[j];
+    float2 yc0 = make_float2(yc4.x, yc4.y), yc1 = make_float2(yc4.z, yc4.w);
+    float2 ya0 = make_float2(ya4.x, ya4.y), ya1 = make_float2(ya4.z, ya4.w);
+    float4* col = reinterpret_cast<float4*>(buf) + j;
+    float4 x[RW];
+#pragma unroll
+    for (int r = 0; r < RW; ++r) x[r] = col[(size_t)r * (S::LDY / 2)];
+#pragma unroll
+    for (int r = 0; r < RW; ++r)
+      if (r < nb) {
+        yc0 = tri_step(make_float2(x[r].x, x[r].y), yc0, dl0);
+        yc1 = tri_step(make_float2(x[r].z, x[r].w), yc1, dl1);
+        col[(size_t)r * (S::LDY / 2)] = make_float4(yc0.x, yc0.y, yc1.x, yc1.y);
+      }
+#pragma unroll
+    for (int r = RW - 1; r >= 0; --r)
+      if (r < nb) {
+        ya0 = tri_step(make_float2(x[r].x, x[r].y), ya0, dl0);
+        ya1 = tri_step(make_float2(x[r].z, x[r].w), ya1, dl1);
+        const float4 y = col[(size_t)r * (S::LDY / 2)];
+        float4 u = make_float4(C0 * ((y.x + ya0.x) - x[r].x), C0 * ((y.y + ya0.y) - x[r].y),
+                               C1 * ((y.z + ya1.x) - x[r].z), C1 * ((y.w + ya1.y) - x[r].w));
+        if (!v0) {  // column 0 keeps its exact solution
+          u.x = x[r].x;
+          u.y = x[r].y;
+        }
+        col[(size_t)r * (S::LDY / 2)] = u;
+      }
+  }
+}
+
+template <class S, typename T, bool TRI>
 __global__ void __launch_bounds__(S::THREADS, S::MINB_INV) k_fast_rows_inv(const float2* __restrict__ Y,
                                                               const float* __restrict__ partial, T* __restrict__ out,
-                                                              const float2* __restrict__ twg, FastArgs A) {
+                                                              const float2* __restrict__ twg, FastArgs A,
+                                                              const float2* __restrict__ tri,
+                                                              const float* __restrict__ cc) {
   extern __shared__ __align__(16) float2 sm[];
   float2* tw2 = sm;
-  float2* buf = sm + S::R1 * S::R2;  // staged rows of Y [2F][ldY], then the stage-1 exchange
+  float2* buf = sm + S::R1 * S::R2;  // staged rows of Y (TRI: of S) [2F][ldY], then the stage-1 exchange
+  float2* cbuf = sm + S::CBUF;        // TRI: the band's two carries [2][LDY]
   __shared__ float u00s[2];
   __shared__ __align__(8) uint64_t bar;
   constexpr int RW = 2 * S::F;       // rows of Y per item
@@ -868,7 +1184,13 @@ __global__ void __launch_bounds__(S::THREADS, S::MINB_INV) k_fast_rows_inv(const
   auto issue = [&](int w) {  // one thread: stage the rows of item w
     const int field = w / A.ngroups, g = w - field * A.ngroups;
     const int r0 = g * RW, nr = (A.H - r0) < RW ? (A.H - r0) : RW;
-    bulk_load(buf, Y + ((size_t)field * A.H + r0) * A.ldY, (unsigned)(nr * A.ldY * sizeof(float2)), &bar);
+    if constexpr (TRI) {  // the whole band of S (its rows past the image feed the recursions) and its carries
+      const unsigned rb = (unsigned)(RW * A.ldY * sizeof(float2)), cb = (unsigned)(2 * A.ldY * sizeof(float2));
+      mbar_expect_tx(&bar, rb + cb);
+      bulk_copy(buf, Y + ((size_t)field * A.srows + r0) * A.ldY, rb, &bar);
+      bulk_copy(cbuf, tri + (size_t)field * A.tri_field + (size_t)g * 2 * A.ldY, cb, &bar);
+    } else
+      bulk_load(buf, Y + ((size_t)field * A.H + r0) * A.ldY, (unsigned)(nr * A.ldY * sizeof(float2)), &bar);
   };
   // warp 0 loads the u[0,0] partial sums of the next item while this one is
   // transformed (lane-strided, the same order as a plain loop over them)
@@ -910,6 +1232,10 @@ __global__ void __launch_bounds__(S::THREADS, S::MINB_INV) k_fast_rows_inv(const
       if (tid == 0) atomicExch(A.err, kErrBulkWait);
       mbar_wait(&bar, phase);
       return;
+    }
+    if constexpr (TRI) {
+      tri_solve_band<S>(buf, cbuf, cc, g, A);
+      __syncthreads();
     }
     const int ia = g * 2 * S::F + 2 * f, ib = ia + 1;
     const bool va = act && ia < A.H, vb = act && ib < A.H;
@@ -1103,6 +1429,13 @@ size_t fast_zbuf_elems_for(int H) {
   return packed > rows ? packed : rows;
 }
 
+// Bands of the recursive column solve for an H-row image (the gradient's
+// row pairs grouped F at a time: pass A's items).
+template <class RS>
+int fast_tri_groups_for(int H) {
+  return (((H + 2) / 2) + RS::F - 1) / RS::F;
+}
+
 // Set the kernel's shared-memory cap (each kernel here has one fixed size) and
 // return how many blocks of it fit on the device at once.
 template <typename K>
@@ -1118,11 +1451,15 @@ static cudaError_t fast_setup(K kernel, int threads, size_t smem, int* slots) {
 }
 
 // MODE 0: solve from gradient, 1: from Laplacian, 2: adjoint (in0 = grad_out,
-// out0 = grad_gx, out1 = grad_gy).
+// out0 = grad_gx, out1 = grad_gy). Solves (modes 0 and 1) on a plan with the
+// recursive column solve run pass A, the carry sweep and pass C; otherwise
+// pass A, the column transforms (pass B) and pass C.
 template <class RS, class CS, typename T, int MODE>
 static cudaError_t run_fast_mode(gfc_plan* P, const Bufs& bf, const T* in0, const T* in1, T* out0, T* out1, int nf,
                                  cudaStream_t st, const EditArgs* ed = nullptr) {
   static_assert(RS::N <= 2048, "the adjoint packing pass covers a whole row in one block");
+  constexpr bool kTriMode = MODE != 2;
+  const bool tri = kTriMode && P->tri;
   FastArgs A;
   A.H = P->H; A.W = P->W; A.p = P->pad; A.M = P->M; A.N = P->N; A.Nh = P->Nh; A.ldM = P->ldM;
   A.nrows = (MODE == 0) ? P->H + 1 : P->H;
@@ -1130,16 +1467,21 @@ static cudaError_t run_fast_mode(gfc_plan* P, const Bufs& bf, const T* in0, cons
   A.npairs = (A.nrows + 1) / 2;
   A.ldz = (RS::N + 3) & ~3;
   A.ngroups = (A.npairs + RS::F - 1) / RS::F;
+  if (tri) A.ngroups = P->triG;  // the bands of the column solve: every mode uses the gradient's
   A.zpairs = A.ngroups * RS::F;
   A.nparts = (P->Nh + CS::C - 1) / CS::C;
   A.nf = nf;
   A.ldY = (P->Nh + 3) & ~3;
   A.err = P->dev_err;
+  A.srows = 2 * A.zpairs;
+  A.G = P->triG;
+  A.tri_field = P->tri_field;
   // the row passes stage their F packed rows / 2F rows of Y in the exchange buffer
   if ((size_t)2 * RS::F * A.ldY > (size_t)RS::F * RS::NP || A.ldz > RS::NP || A.zpairs > kAdjTotal)
     return cudaErrorInvalidConfiguration;
+  if (tri && (size_t)A.srows * A.ldY > P->spec_field) return cudaErrorInvalidConfiguration;
   static std::mutex mu;
-  static int slots_a = 0, slots_b = 0, slots_c = 0, slots_d = 0;
+  static int slots_a = 0, slots_b = 0, slots_c = 0, slots_d = 0, slots_ta = 0, slots_tc = 0, slots_td = 0;
   cudaError_t e;
   {
     std::lock_guard<std::mutex> lock(mu);
@@ -1151,11 +1493,28 @@ static cudaError_t run_fast_mode(gfc_plan* P, const Bufs& bf, const T* in0, cons
         if ((e = fast_setup(k_fast_rows_adj<RS, T>, RS::THREADS, RS::smem_bytes_adj(), &slots_c)) != cudaSuccess)
           return e;
       } else {
-        if ((e = fast_setup(k_fast_rows_inv<RS, T>, RS::THREADS, RS::smem_bytes(), &slots_c)) != cudaSuccess) return e;
+        if ((e = fast_setup(k_fast_rows_inv<RS, T, false>, RS::THREADS, RS::smem_bytes(), &slots_c)) != cudaSuccess)
+          return e;
+        if ((e = fast_setup(k_fast_rows_inv<RS, T, true>, RS::THREADS, RS::smem_bytes_tri_inv(), &slots_tc)) !=
+            cudaSuccess)
+          return e;
+        // the sweep stages all bands of 32 columns: size it for the most bands any
+        // image on this torus has (H <= M - 2p)
+        int unused_k = 0;
+        constexpr int kGmax = (((CS::M - 2 * kP + 2) / 2) + RS::F - 1) / RS::F;
+        if ((e = fast_setup(k_tri_carries, 96, (size_t)2 * kGmax * kTriCols * (sizeof(float2) + sizeof(float)),
+                            &unused_k)) != cudaSuccess)
+          return e;
+        if ((e = fast_setup(k_fast_rows_fwd<RS, true>, RS::THREADS, RS::smem_bytes_fwd(), &slots_ta)) != cudaSuccess)
+          return e;
       }
-      if ((e = fast_setup(k_fast_rows_fwd<RS>, RS::THREADS, RS::smem_bytes_fwd(), &slots_a)) != cudaSuccess) return e;
-      if (MODE != 1 && (e = fast_setup(k_fast_rows_fwd_div<RS, T, MODE == 2>, RS::THREADS, RS::smem_bytes_fwd(),
-                                       &slots_d)) != cudaSuccess)
+      if ((e = fast_setup(k_fast_rows_fwd<RS, false>, RS::THREADS, RS::smem_bytes_fwd(), &slots_a)) != cudaSuccess)
+        return e;
+      if (MODE != 1 && (e = fast_setup(k_fast_rows_fwd_div<RS, T, MODE == 2, false>, RS::THREADS,
+                                       RS::smem_bytes_fwd(), &slots_d)) != cudaSuccess)
+        return e;
+      if (MODE == 0 && (e = fast_setup(k_fast_rows_fwd_div<RS, T, false, true>, RS::THREADS, RS::smem_bytes_fwd(),
+                                       &slots_td)) != cudaSuccess)
         return e;
     }
   }
@@ -1166,11 +1525,20 @@ static cudaError_t run_fast_mode(gfc_plan* P, const Bufs& bf, const T* in0, cons
   const size_t stage = (MODE == 2) ? (size_t)2 * RS::F * P->W * sizeof(T) : fused_stage_bytes<RS, T>(P->W);
   const bool fused_div = MODE != 1 && !(ed && ed->kind != kEditNone) && (P->W * sizeof(T)) % 16 == 0 &&
                          stage <= fused_exchange_bytes<RS>() && getenv("GFC_UNFUSED_DIV") == nullptr;
+  const long a_items = (long)nf * A.ngroups;
   if (fused_div) {
     prof_begin(P, 0, st);
-    k_fast_rows_fwd_div<RS, T, MODE == 2>
-        <<<grid_for((long)nf * A.ngroups, slots_d), RS::THREADS, RS::smem_bytes_fwd(), st>>>(
-            in0, in1, bf.spec, P->twN, bf.partial, A);
+    if constexpr (MODE == 0) {
+      if (tri)
+        k_fast_rows_fwd_div<RS, T, false, true><<<grid_for(a_items, slots_td), RS::THREADS, RS::smem_bytes_fwd(), st>>>(
+            in0, in1, bf.spec, P->twN, bf.partial, A, bf.tri, P->colcoef);
+      else
+        k_fast_rows_fwd_div<RS, T, false, false><<<grid_for(a_items, slots_d), RS::THREADS, RS::smem_bytes_fwd(), st>>>(
+            in0, in1, bf.spec, P->twN, bf.partial, A, nullptr, nullptr);
+    } else {
+      k_fast_rows_fwd_div<RS, T, MODE == 2, false><<<grid_for(a_items, slots_d), RS::THREADS, RS::smem_bytes_fwd(), st>>>(
+          in0, in1, bf.spec, P->twN, bf.partial, A, nullptr, nullptr);
+    }
     prof_end(P, st);
   }
   if (!fused_div) prof_begin(P, 3, st);
@@ -1193,30 +1561,47 @@ static cudaError_t run_fast_mode(gfc_plan* P, const Bufs& bf, const T* in0, cons
     prof_end(P, st);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     prof_begin(P, 0, st);
-    k_fast_rows_fwd<RS><<<grid_for((long)nf * A.ngroups, slots_a), RS::THREADS, RS::smem_bytes_fwd(), st>>>(
-        bf.zbuf, bf.spec, P->twN, A);
+    if (tri)
+      k_fast_rows_fwd<RS, true><<<grid_for(a_items, slots_ta), RS::THREADS, RS::smem_bytes_fwd(), st>>>(
+          bf.zbuf, bf.spec, P->twN, A, bf.tri, P->colcoef);
+    else
+      k_fast_rows_fwd<RS, false><<<grid_for(a_items, slots_a), RS::THREADS, RS::smem_bytes_fwd(), st>>>(
+          bf.zbuf, bf.spec, P->twN, A, nullptr, nullptr);
     prof_end(P, st);
   }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   prof_begin(P, 1, st);
-  if (MODE == 2) {
-    k_adj_total<<<nf, 32, 0, st>>>(reinterpret_cast<double*>(bf.partial), A.zpairs);
-    P->prof.launches[1] += 1;  // a second launch in this pass
+  const int nkb = (P->Nh + kTriCols - 1) / kTriCols;  // column blocks of the sweep (u[0,0] partials)
+  if (tri) {
+    k_tri_carries<<<dim3(nkb, nf), 96, (size_t)2 * A.G * kTriCols * (sizeof(float2) + sizeof(float)), st>>>(
+        bf.spec, bf.tri, P->colcoef, P->powc, reinterpret_cast<double*>(bf.partial), A);
+  } else {
+    if (MODE == 2) {
+      k_adj_total<<<nf, 32, 0, st>>>(reinterpret_cast<double*>(bf.partial), A.zpairs);
+      P->prof.launches[1] += 1;  // a second launch in this pass
+    }
+    k_fast_cols<CS, MODE><<<grid_for((long)nf * A.nparts, slots_b), CS::THREADS, CS::smem_bytes(), st>>>(
+        bf.spec, bf.zbuf, P->GT, P->twM, bf.partial, A);
   }
-  k_fast_cols<CS, MODE><<<grid_for((long)nf * A.nparts, slots_b), CS::THREADS, CS::smem_bytes(), st>>>(
-      bf.spec, bf.zbuf, P->GT, P->twM, bf.partial, A);
   prof_end(P, st);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   FastArgs C = A;
   prof_begin(P, 2, st);
-  if (MODE == 2) {
+  if constexpr (MODE == 2) {
     C.ngroups = (P->H + RS::F - 1) / RS::F;
     k_fast_rows_adj<RS, T><<<grid_for((long)nf * C.ngroups, slots_c), RS::THREADS, RS::smem_bytes_adj(), st>>>(
         bf.zbuf, out0, out1, P->twN, C);
   } else {
     C.ngroups = ((P->H + 1) / 2 + RS::F - 1) / RS::F;
-    k_fast_rows_inv<RS, T><<<grid_for((long)nf * C.ngroups, slots_c), RS::THREADS, RS::smem_bytes(), st>>>(
-        bf.zbuf, bf.partial, out0, P->twN, C);
+    if (tri) {
+      C.nparts = nkb;
+      k_fast_rows_inv<RS, T, true>
+          <<<grid_for((long)nf * C.ngroups, slots_tc), RS::THREADS, RS::smem_bytes_tri_inv(), st>>>(
+              bf.spec, bf.partial, out0, P->twN, C, bf.tri, P->colcoef);
+    } else {
+      k_fast_rows_inv<RS, T, false><<<grid_for((long)nf * C.ngroups, slots_c), RS::THREADS, RS::smem_bytes(), st>>>(
+          bf.zbuf, bf.partial, out0, P->twN, C, nullptr, nullptr);
+    }
   }
   prof_end(P, st);
   return cudaGetLastError();

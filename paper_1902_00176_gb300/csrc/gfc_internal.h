@@ -15,6 +15,7 @@ struct Bufs {
   float2* spec;    // spectrum
   float2* zbuf;    // packed rows of L / row-major spectrum (fast passes)
   float* partial;  // per-block sums
+  float2* tri;     // band sums and carries of the recursive column solve (fast passes)
 };
 constexpr int kMaxSlots = 4;
 constexpr int kHostBufs = 4;  // most staging buffers of the host-buffer pipeline
@@ -50,6 +51,12 @@ struct gfc_plan {
   int ldS;    // row stride of the row-major spectrum scratch (generic passes), complex elements
   int ldM;    // column stride of the column-major spectrum scratch (fast passes)
   bool fast;  // both transform lengths have register-resident schedules
+  bool tri;   // fast passes with the column direction by recursive filters (gfc_column_solver)
+  int triG;   // bands of the recursive column solve (pass A's items)
+  size_t tri_field;  // complex elements per field of the band scratch
+  float* colcoef;    // [Nh][8] column coefficients of the recursive solve
+  float* powc;       // [2 triG][ldS] carry weights of the bands
+  float2* tri_buf;   // [slots][chunk][tri_field] band scratch
   bool exact; // size policy EXACT: M = H + 2p, N = W + 2p (exact.cu)
   gfc::ExactDim ex_row, ex_col;  // EXACT: the length-N and length-M transforms
   int chunk;  // fields per pipeline chunk
@@ -115,10 +122,14 @@ bool is_7smooth(long n);
 cudaError_t build_twiddles(float2* tw, int n, cudaStream_t s);
 cudaError_t build_green(float* G, int M, int N, int Nh, cudaStream_t s);
 cudaError_t build_green_t(float* GT, int M, int N, int Nh, int ldM, cudaStream_t s);
+// recursive column solve tables: cc [Nh][8], pw [2 G][ldY] (bands of `band` rows from row `pad`)
+cudaError_t build_colcoef(float* cc, float* pw, int M, int N, int Nh, int ldY, int pad, int G, int band,
+                          cudaStream_t s);
 
 // register-resident passes (solve_fast.cu): spectrum laid out [l][r]
 bool fast_supported(int M, int N);
 size_t fast_zbuf_elems(int H, int M, int N);  // per field
+int fast_row_items(int M, int N);             // row pairs per item of the row passes (F)
 // mode 0 gradient, 1 Laplacian, 2 adjoint (out1 = grad_gy)
 // `ed` (mode 0 only, may be null) applies a gradient edit as the gradient is loaded
 cudaError_t run_chunk_fast(gfc_plan* P, const Bufs& B, int mode, const void* in0, const void* in1, void* out0,
@@ -128,6 +139,7 @@ inline Bufs slot_bufs(const gfc_plan* P, int s) {
   b.spec = P->spec + (size_t)s * P->chunk * P->spec_field;
   b.zbuf = P->zbuf ? P->zbuf + (size_t)s * P->chunk * P->zbuf_field : nullptr;
   b.partial = P->partial + (size_t)s * P->chunk * kMaxRowBlocks;
+  b.tri = P->tri_buf ? P->tri_buf + (size_t)s * P->chunk * P->tri_field : nullptr;
   return b;
 }
 

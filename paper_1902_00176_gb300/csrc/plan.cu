@@ -98,6 +98,89 @@ __global__ void k_build_green_t(float* GT, int M, int N, int Nh, int ldM) {
   }
 }
 
+// Coefficients of the recursive column solve, per Hermitian column l (FP64,
+// rounded once to FP32). After the row transforms, column l of Eq. 23's
+// Green multiply is the inverse of the cyclic tridiagonal operator
+// S + S^-1 - b_l along the torus rows (S the row shift, b_l = 4 - 2 cos(2 pi l / N),
+// i.e. lambda(k, l) = 2 cos(2 pi k / M) - b_l). With a_l + 1/a_l = b_l, a_l < 1,
+//   (S + S^-1 - b)^-1 = -a / (1 - a^2) [ (1 - a S)^-1 + (1 - a S^-1)^-1 - 1 ],
+// two first-order recursions (causal and anticausal) on the cyclic rows. The
+// rows are cut into bands of `band` rows from torus row `pad` (the last one
+// `last` rows long), followed by `tail` zero rows and the `pad` zero rows that
+// close the cycle. Row l of the table: delta = 1 - a (formed without
+// cancellation, so the pole stays exact near DC), a, C = -a / ((1 - a^2) N)
+// (1/N: the unnormalised inverse row transform), a^band, a^last, a^pad,
+// 1 / (1 - a^M), a^tail. Column 0 (b = 2, singular) is solved exactly
+// elsewhere; its row is zero.
+// After the [Nh][8] rows, `dc` holds (delta, C) of every column compactly,
+// [ldY][2] (zero past Nh), for the in-band recursions of the inverse row pass.
+__global__ void k_build_colcoef(float* cc, float* dc, int M, int N, int Nh, int ldY, int pad, int band, int last,
+                                int tail) {
+  for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < ldY; l += gridDim.x * blockDim.x) {
+    if (l >= Nh || l == 0) {
+      dc[2 * l] = dc[2 * l + 1] = 0.0f;
+      if (l == 0)
+        for (int i = 0; i < 8; ++i) cc[i] = 0.0f;
+      continue;
+    }
+    float* c = cc + (size_t)l * 8;
+    const double sn = sinpi((double)l / (double)N);
+    const double d = 4.0 * sn * sn;  // b - 2
+    const double r = sqrt(d * (4.0 + d));
+    const double a = 2.0 / (2.0 + d + r), delta = (d + r) / (2.0 + d + r);
+    c[0] = (float)delta;
+    c[1] = (float)a;
+    c[2] = (float)(-a / (delta * (1.0 + a) * (double)N));
+    c[3] = (float)pow(a, (double)band);
+    c[4] = (float)pow(a, (double)last);
+    c[5] = (float)pow(a, (double)pad);
+    c[6] = (float)(1.0 / (1.0 - pow(a, (double)M)));
+    c[7] = (float)pow(a, (double)tail);
+    dc[2 * l] = c[0];
+    dc[2 * l + 1] = c[2];
+  }
+}
+
+// Carry weights of the bands, in tiles of 32 columns [ceil(ldY/32)][2 G][32]:
+// row g holds a^(band g) (the causal carry into band 0 reaching band g), row
+// G + g holds a^(tail + rows of the bands after g) (the anticausal carry at the
+// end of the last band reaching band g).
+__global__ void k_build_powc(float* pw, int N, int Nh, int ldY, int G, int band, int last, int tail) {
+  const int nkb = (ldY + 31) / 32;
+  const long total = (long)nkb * 2 * G * 32;
+  for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
+    const int kb = (int)(idx / (2L * G * 32)), rem = (int)(idx % (2L * G * 32));
+    const int row = rem / 32, l = kb * 32 + rem % 32;
+    if (l == 0 || l >= Nh) {
+      pw[idx] = 0.0f;
+      continue;
+    }
+    const double sn = sinpi((double)l / (double)N);
+    const double d = 4.0 * sn * sn;
+    const double a = 2.0 / (2.0 + d + sqrt(d * (4.0 + d)));
+    double e;
+    if (row < G) {
+      e = (double)band * row;
+    } else {
+      const int g = row - G;
+      e = (double)tail + (g < G - 1 ? (double)band * (G - 2 - g) + last : 0.0);
+    }
+    pw[idx] = (float)pow(a, e);
+  }
+}
+
+cudaError_t build_colcoef(float* cc, float* pw, int M, int N, int Nh, int ldY, int pad, int G, int band,
+                          cudaStream_t s) {
+  const int last = (M - pad - band * (G - 1)) < band ? (M - pad - band * (G - 1)) : band;
+  const int tail = (M - pad - band * G) > 0 ? (M - pad - band * G) : 0;
+  k_build_colcoef<<<(ldY + 255) / 256, 256, 0, s>>>(cc, cc + (size_t)Nh * 8, M, N, Nh, ldY, pad, band, last, tail);
+  const long total = (long)((ldY + 31) / 32) * 2 * G * 32;
+  int blocks = (int)((total + 255) / 256);
+  if (blocks > 4096) blocks = 4096;
+  k_build_powc<<<blocks, 256, 0, s>>>(pw, N, Nh, ldY, G, band, last, tail);
+  return cudaGetLastError();
+}
+
 cudaError_t build_green_t(float* GT, int M, int N, int Nh, int ldM, cudaStream_t s) {
   long total = (long)Nh * ldM;
   int blocks = (int)((total + 255) / 256);
@@ -194,6 +277,20 @@ gfc_status gfc_plan_create_ex(gfc_plan** out, const gfc_plan_opts* o) {
   p->M = M; p->N = N; p->Nh = N / 2 + 1; p->ldS = (p->Nh + 3) & ~3; p->ldM = (M + 3) & ~3;
   p->exact = o->size_policy == GFC_SIZE_EXACT;
   p->fast = !p->exact && fast_supported(M, N) && pad == 4 && getenv("GFC_FORCE_GENERIC") == nullptr;
+  if (o->column_solver != GFC_COLUMN_RECURSIVE && o->column_solver != GFC_COLUMN_FFT) {
+    free(p);
+    return fail(GFC_ERR_INVALID_ARG, "gfc_plan_create: unknown column solver %d", o->column_solver);
+  }
+  p->tri = p->fast && o->column_solver == GFC_COLUMN_RECURSIVE;
+  if (p->tri) {
+    const int F = fast_row_items(M, N);
+    p->triG = (((o->H + 2) / 2) + F - 1) / F;
+    // carries [G][2][ldS], band sums in 32-column tiles, column 0 of the 2 F G rows
+    // of S as floats; even, so every field's scratch stays 16-byte aligned
+    const size_t nkb = (size_t)(p->ldS + 31) / 32;
+    p->tri_field = ((size_t)2 * p->triG * p->ldS + nkb * 2 * p->triG * 32 + (size_t)(2 * F * p->triG + 1) / 2 + 1) &
+                   ~(size_t)1;
+  }
   p->stream = (cudaStream_t)o->stream;
   if (!p->exact && (!make_fft_plan(N, &p->rowplan) || !make_fft_plan(M, &p->colplan))) {
     free(p);
@@ -208,8 +305,12 @@ gfc_status gfc_plan_create_ex(gfc_plan** out, const gfc_plan_opts* o) {
   p->spec_field = per_row_major > per_col_major ? per_row_major : per_col_major;
   if (p->exact) p->spec_field = 2 * (size_t)M * N;  // the complex torus and its transpose
   p->zbuf_field = p->fast ? fast_zbuf_elems(o->H, M, N) : 0;
+  if (p->tri) {  // the row-major spectrum holds 2F rows per band
+    const size_t srows = (size_t)2 * fast_row_items(M, N) * p->triG * p->ldS;
+    if (srows > p->spec_field) p->spec_field = srows;
+  }
   const size_t per_field = p->spec_field * sizeof(float2);
-  const size_t ws = per_field + p->zbuf_field * sizeof(float2);
+  const size_t ws = per_field + (p->zbuf_field + p->tri_field) * sizeof(float2);
   long chunk = o->chunk;
   int nslots = o->streams;
   if (nslots == 0) nslots = 1;
@@ -238,6 +339,11 @@ gfc_status gfc_plan_create_ex(gfc_plan** out, const gfc_plan_opts* o) {
   if (e == cudaSuccess) e = cudaMalloc(&p->spec, per_field * (size_t)chunk * nslots);
   if (e == cudaSuccess) e = cudaMalloc(&p->partial, (size_t)chunk * nslots * kMaxRowBlocks * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc(&p->edit_t2, (size_t)fields * sizeof(float));
+  if (e == cudaSuccess && p->tri) e = cudaMalloc(&p->colcoef, ((size_t)p->Nh * 8 + 2 * (size_t)p->ldS) * sizeof(float));
+  if (e == cudaSuccess && p->tri)
+    e = cudaMalloc(&p->powc, (size_t)((p->ldS + 31) / 32) * 2 * p->triG * 32 * sizeof(float));
+  // (+64 bytes: the sweep's bulk copy of a field's column 0 rounds up to 16 bytes)
+  if (e == cudaSuccess && p->tri) e = cudaMalloc(&p->tri_buf, p->tri_field * chunk * nslots * sizeof(float2) + 64);
   for (int sl = 0; sl < nslots && e == cudaSuccess; ++sl) {
     e = cudaStreamCreateWithFlags(&p->slot_stream[sl], cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->slot_done[sl], cudaEventDisableTiming);
@@ -251,6 +357,8 @@ gfc_status gfc_plan_create_ex(gfc_plan** out, const gfc_plan_opts* o) {
   if (e == cudaSuccess) e = build_twiddles(p->twM, M, bs);
   if (e == cudaSuccess) e = build_green(p->G, M, N, p->Nh, bs);
   if (e == cudaSuccess && p->fast) e = build_green_t(p->GT, M, N, p->Nh, p->ldM, bs);
+  if (e == cudaSuccess && p->tri)
+    e = build_colcoef(p->colcoef, p->powc, M, N, p->Nh, p->ldS, pad, p->triG, 2 * fast_row_items(M, N), bs);
   if (e == cudaSuccess && p->exact) e = exact_setup(p, bs);
   if (e == cudaSuccess) e = cudaStreamSynchronize(bs);
   if (bs) cudaStreamDestroy(bs);
@@ -452,6 +560,9 @@ static void destroy_plan(gfc_plan* p) {
   cudaFree(p->spec);
   cudaFree(p->partial);
   cudaFree(p->edit_t2);
+  cudaFree(p->colcoef);
+  cudaFree(p->powc);
+  cudaFree(p->tri_buf);
   exact_release(p);
   for (int sl = 0; sl < kMaxSlots; ++sl) {
     if (p->slot_stream[sl]) cudaStreamDestroy(p->slot_stream[sl]);

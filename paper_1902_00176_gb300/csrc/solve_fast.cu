@@ -7,7 +7,8 @@ namespace gfc {
 #define GFC_FAST_SHAPE(M, N)                                                                                  \
   cudaError_t fast_run_##M##x##N(gfc_plan*, const Bufs&, int, const void*, const void*, void*, void*, int, \
                                  cudaStream_t, const EditArgs*);                                          \
-  size_t fast_zbuf_##M##x##N(int H);
+  size_t fast_zbuf_##M##x##N(int H);                                                                     \
+  int fast_items_##M##x##N();
 GFC_FAST_SHAPE(810, 1250)
 GFC_FAST_SHAPE(1050, 1568)
 GFC_FAST_SHAPE(270, 270)
@@ -20,12 +21,13 @@ struct FastEntry {
   cudaError_t (*run)(gfc_plan*, const Bufs&, int, const void*, const void*, void*, void*, int, cudaStream_t,
                      const EditArgs*);
   size_t (*zbuf)(int H);
+  int (*items)();
 };
 const FastEntry kFast[] = {
-    {810, 1250, fast_run_810x1250, fast_zbuf_810x1250},
-    {1050, 1568, fast_run_1050x1568, fast_zbuf_1050x1568},
-    {270, 270, fast_run_270x270, fast_zbuf_270x270},
-    {72, 108, fast_run_72x108, fast_zbuf_72x108},
+    {810, 1250, fast_run_810x1250, fast_zbuf_810x1250, fast_items_810x1250},
+    {1050, 1568, fast_run_1050x1568, fast_zbuf_1050x1568, fast_items_1050x1568},
+    {270, 270, fast_run_270x270, fast_zbuf_270x270, fast_items_270x270},
+    {72, 108, fast_run_72x108, fast_zbuf_72x108, fast_items_72x108},
 };
 const FastEntry* find(int M, int N) {
   for (const FastEntry& e : kFast)
@@ -39,6 +41,11 @@ bool fast_supported(int M, int N) { return find(M, N) != nullptr; }
 size_t fast_zbuf_elems(int H, int M, int N) {
   const FastEntry* e = find(M, N);
   return e ? e->zbuf(H) : 0;
+}
+
+int fast_row_items(int M, int N) {
+  const FastEntry* e = find(M, N);
+  return e ? e->items() : 0;
 }
 
 cudaError_t run_chunk_fast(gfc_plan* P, const Bufs& bf, int mode, const void* in0, const void* in1, void* out0,

@@ -37,7 +37,8 @@ class GFCError(RuntimeError):
 class _Opts(ctypes.Structure):
     _fields_ = [("H", ctypes.c_int), ("W", ctypes.c_int), ("C", ctypes.c_int), ("batch", ctypes.c_int),
                 ("dtype", ctypes.c_int), ("pad", ctypes.c_int), ("size_policy", ctypes.c_int),
-                ("chunk", ctypes.c_int), ("stream", ctypes.c_void_p), ("streams", ctypes.c_int)]
+                ("chunk", ctypes.c_int), ("stream", ctypes.c_void_p), ("streams", ctypes.c_int),
+                ("column_solver", ctypes.c_int)]
 
 
 class Item(ctypes.Structure):
@@ -154,15 +155,18 @@ class Plan:
     """A GFC plan: Green spectrum, transform tables and scratch for one problem shape."""
 
     def __init__(self, H: int, W: int, C: int = 1, batch: int = 1, dtype=torch.float32, pad: int = 4,
-                 chunk: int = 0, device=None, streams: int = 0, exact: bool = False):
+                 chunk: int = 0, device=None, streams: int = 0, exact: bool = False, column_fft: bool = False):
         """``exact=True`` solves on Algorithm A's own padded size (H + 2p) x (W + 2p)
-        instead of the next even 7-smooth size."""
+        instead of the next even 7-smooth size. ``column_fft=True`` applies the column
+        direction of the Green multiply by column FFTs instead of the recursive
+        (tridiagonal) column solve (register-resident sizes; same operator)."""
         if dtype not in _DTYPES:
             raise ValueError(f"unsupported dtype {dtype}")
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else
                                    torch.device(device).index or 0)
         self.H, self.W, self.C, self.batch, self.dtype = H, W, C, batch, dtype
-        o = _Opts(H, W, C, batch, _DTYPES[dtype], pad, 1 if exact else 0, chunk, None, streams)
+        o = _Opts(H, W, C, batch, _DTYPES[dtype], pad, 1 if exact else 0, chunk, None, streams,
+                  1 if column_fft else 0)
         h = ctypes.c_void_p()
         with torch.cuda.device(self.device):
             _check(lib().gfc_plan_create_ex(ctypes.byref(h), ctypes.byref(o)))

@@ -1,0 +1,118 @@
+"""The recursive (tridiagonal) column solve against the FP64 oracle and against
+the column-FFT path of the same operator.
+
+After the row transforms, column l of Eq. 23's Green multiply is the inverse of
+the cyclic tridiagonal operator S + S^-1 - b_l along the torus rows; the plan's
+default applies it by causal and anticausal first-order recursions over bands
+of rows, with carries swept around the cycle and column 0 solved exactly. The
+sizes below cover every register-resident torus, bands that end before the
+torus does (tail rows), a band clipped at the torus end, 16-bit storage, the
+Laplacian entry and the edited solves.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle.gfc_oracle as O
+from paper_1902_00176_gb300 import gfc, synth
+
+pytestmark = pytest.mark.gpu
+
+DEV = torch.device("cuda:0")
+REL_F32, MAXABS_F32, REL_16 = 1e-5, 1e-4, 2e-3
+
+
+@pytest.fixture(autouse=True)
+def _lib(gfc_lib):
+    yield
+
+
+def _rel(got, ref):
+    return float(np.linalg.norm(got - ref) / max(np.linalg.norm(ref), 1e-300))
+
+
+def _np(t):
+    return t.double().cpu().numpy()
+
+
+def _dev(a, dtype=torch.float32):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV).to(dtype)
+
+
+# (H, W): 801x1200 (bands reach the torus end), 795x1199 (6 tail rows after the
+# last band), 1024x1536, 256x256, 64x96, 60x100 (72x108 torus, a clipped band)
+SIZES = [(801, 1200), (795, 1199), (1024, 1536), (256, 256), (64, 96), (60, 100), (802, 1242)]
+
+
+@pytest.mark.parametrize("H,W", SIZES)
+def test_recursive_column_solve_matches_oracle_and_column_fft(H, W):
+    B = 2
+    gx, gy = synth.perturbed_gradient_batch(batch=B, H=H, W=W, seed=7100 + H)
+    tx, ty = _dev(gx), _dev(gy)
+    rec = gfc.Plan(H, W, 1, B, device=DEV)
+    fft = gfc.Plan(H, W, 1, B, device=DEV, column_fft=True)
+    assert (rec.M, rec.N) == (fft.M, fft.N)
+    a = _np(rec.solve_from_gradient(tx, ty))
+    b = _np(fft.solve_from_gradient(tx, ty))
+    for f in range(B):
+        ref = O.solve_from_gradient(gx[f, 0].astype(np.float64), gy[f, 0].astype(np.float64), rec.M, rec.N,
+                                    rec.pad)
+        assert _rel(a[f, 0], ref) <= REL_F32, (f, _rel(a[f, 0], ref))
+        assert np.abs(a[f, 0] - ref).max() <= MAXABS_F32, f
+    assert _rel(a, b) <= 2e-6, _rel(a, b)
+    a2 = _np(rec.solve_from_gradient(tx, ty))
+    assert np.array_equal(a, a2)  # deterministic
+    rec.close()
+    fft.close()
+
+
+@pytest.mark.parametrize("H,W", [(801, 1200), (256, 256), (64, 96), (795, 1199)])
+def test_recursive_column_solve_laplacian_entry(H, W):
+    rng = np.random.default_rng(H * 11 + W)
+    lap = (rng.standard_normal((2, 1, H, W)) * 0.01).astype(np.float32)
+    p = gfc.Plan(H, W, 1, 2, device=DEV)
+    out = _np(p.solve_from_laplacian(_dev(lap)))
+    for f in range(2):
+        ref = O.solve_from_laplacian(lap[f, 0].astype(np.float64), p.M, p.N, p.pad)
+        # white-noise Laplacian: the FP32 conditioning limit of white inputs (|G| ~ (M/2pi)^2
+        # amplifies round-off in the lowest bins); the column-FFT path is the same-math bar
+        q = gfc.Plan(H, W, 1, 2, device=DEV, column_fft=True)
+        alt = _np(q.solve_from_laplacian(_dev(lap)))[f, 0]
+        q.close()
+        assert _rel(out[f, 0], ref) <= max(REL_F32, 3.0 * _rel(alt, ref)), (_rel(out[f, 0], ref), _rel(alt, ref))
+    p.close()
+
+
+@pytest.mark.parametrize("dtype", [torch.float16, torch.bfloat16])
+@pytest.mark.parametrize("H,W", [(801, 1200), (256, 256)])
+def test_recursive_column_solve_16bit_storage(dtype, H, W):
+    gx, gy = synth.perturbed_gradient_batch(batch=1, H=H, W=W, seed=7300)
+    tx, ty = _dev(gx, dtype), _dev(gy, dtype)
+    p = gfc.Plan(H, W, 1, 1, dtype, device=DEV)
+    out = _np(p.solve_from_gradient(tx, ty))[0, 0]
+    ref = O.solve_from_gradient(_np(tx)[0, 0], _np(ty)[0, 0], p.M, p.N, p.pad)
+    assert _rel(out, ref) <= REL_16
+    p.close()
+
+
+@pytest.mark.parametrize("edit", ["threshold", "merge"])
+def test_recursive_column_solve_edited(edit):
+    H, W, B = 801, 1200, 2
+    img, gx, gy, edges = synth.edit_batch(B, 1, H, W, seed=7400)
+    tx, ty, te = _dev(gx), _dev(gy), _dev(edges)
+    rec = gfc.Plan(H, W, 1, B, device=DEV)
+    fft = gfc.Plan(H, W, 1, B, device=DEV, column_fft=True)
+    kw = dict(frac=0.1) if edit == "threshold" else dict(alpha=0.5, edges=te)
+    a = _np(rec.solve_edited(tx, ty, edit, **kw))
+    b = _np(fft.solve_edited(tx, ty, edit, **kw))
+    assert _rel(a, b) <= 2e-6
+    rec.close()
+    fft.close()
+
+
+def test_unknown_column_solver_is_rejected():
+    import ctypes
+
+    o = gfc._Opts(64, 96, 1, 1, 0, 4, 0, 0, None, 0, 7)
+    h = ctypes.c_void_p()
+    assert gfc.lib().gfc_plan_create_ex(ctypes.byref(h), ctypes.byref(o)) == 1
