@@ -746,8 +746,7 @@ def _edit_workload(dev, samples):
     res["threshold_solve_correct"] = {"ms": ms, "solves_per_s": B * 1000.0 / ms}
 
     def fused():
-        p.solve_edited(tx, ty, "threshold", frac=0.1, out=out)
-        p.color_correct(out, mean, std)
+        p.solve_corrected(tx, ty, mean, std, edit="threshold", frac=0.1, out=out)
 
     ms = _time_ms(fused, dev, 5)
     res["threshold_solve_correct_fused"] = {"ms": ms, "solves_per_s": B * 1000.0 / ms}
@@ -757,6 +756,13 @@ def _edit_workload(dev, samples):
     res["solve_threshold_fused"] = {"ms": ms, "solves_per_s": B * 1000.0 / ms}
     _sample(samples, "edit_100x801x1200_fp32", "threshold", _h(out[2, 0]), p.M, p.N, gx=_h(tx[2, 0]),
             gy=_h(ty[2, 0]), frac=0.1)
+    ms = _time_ms(lambda: p.solve_edited(tx, ty, "threshold", frac=0.1, ref=1.0, out=out), dev, 5)
+    res["solve_threshold_ref_fused"] = {"ms": ms, "solves_per_s": B * 1000.0 / ms,
+                                        "note": "threshold against a given reference magnitude: no max pre-pass"}
+    ms = _time_ms(lambda: p.solve_from_gradient(tx, ty, out), dev, 5)
+    res["solve_plain_same_inputs"] = {"ms": ms, "solves_per_s": B * 1000.0 / ms}
+    ms = _time_ms(lambda: p.solve_corrected(tx, ty, mean, std, out=out), dev, 5)
+    res["solve_correct_fused"] = {"ms": ms, "solves_per_s": B * 1000.0 / ms}
     ms = _time_ms(lambda: p.solve_edited(tx, ty, "merge", alpha=0.5, edges=te, out=out), dev, 5)
     res["solve_merge_fused"] = {"ms": ms, "solves_per_s": B * 1000.0 / ms}
     _sample(samples, "edit_100x801x1200_fp32", "merge", _h(out[3, 0]), p.M, p.N, gx=_h(tx[3, 0]), gy=_h(ty[3, 0]),

@@ -290,6 +290,22 @@ typedef struct {
  * during the call. */
 gfc_status gfc_solve_edited(gfc_plan* plan, const void* gx, const void* gy, const gfc_edit* edit, void* out);
 
+/* The gradient-domain editing flow of Sec. 3.1.1 (Fig. 1) in one call: edit
+ * (optional), solve (Eq. 23), colour-correct (Eq. 25, Sec. 3.2.2):
+ * out = (I_c - mean(I_c)) * ref_std / std(I_c) + ref_mean per field, I_c the
+ * solved field, ref_mean / ref_std the original image's statistics (device
+ * arrays of batch * C floats, e.g. from gfc_field_stats); a field with
+ * std(I_c) = 0 becomes ref_mean. `edit` may be NULL (no edit) or as for
+ * gfc_solve_edited. On plans with the recursive column solve the statistics of
+ * I_c are taken while the last pass stores it (per-item FP64 partials, reduced
+ * in a fixed order), and one more pass applies the correction in place: out is
+ * written once by the solve and read and written once more. Other plans run the
+ * solve and then gfc_color_correct. The result matches those two calls to FP32
+ * rounding of the statistics. Layout and errors as gfc_solve_edited; ragged
+ * plans return GFC_ERR_UNSUPPORTED. */
+gfc_status gfc_solve_corrected(gfc_plan* plan, const void* gx, const void* gy, const gfc_edit* edit,
+                               const float* ref_mean, const float* ref_std, void* out);
+
 /* Boundary-preserving offset (Sec. 2.3.2): for fields solved from an image
  * that was padded by `ring` pixels on every side, subtract the mean of the
  * solution over that ring (the least-squares constant that makes the padded

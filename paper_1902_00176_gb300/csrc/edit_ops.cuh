@@ -18,6 +18,10 @@ struct EditArgs {
   float alpha;        // merge weight (Eq. 26)
   const void* edges;  // merge: edge map at the chunk's first field (plan dtype)
   const float* t2;    // threshold: squared threshold of each field of the chunk
+  // colour correction (Eq. 25) fused after the solve: the statistics of the
+  // solved field are taken as pass C stores it; null = none
+  const float* ref_mean;  // reference mean of each field of the chunk
+  const float* ref_std;   // reference standard deviation of each field of the chunk
 };
 
 // |E|^2 with both products and the sum rounded to FP32 (no contraction)

@@ -337,7 +337,7 @@ cudaError_t run_exact(gfc_plan* P, const Bufs& bf, const T* in0, const T* in1, T
   const int np = (nf + 1) / 2;  // complex tori: two fields each
   float2* X = bf.spec;
   float2* XT = bf.spec + (size_t)np * M * N;
-  const EditArgs none{kEditNone, 0.0f, nullptr, nullptr};
+  const EditArgs none{kEditNone, 0.0f, nullptr, nullptr, nullptr, nullptr};
   const EditArgs& E = ed ? *ed : none;
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);

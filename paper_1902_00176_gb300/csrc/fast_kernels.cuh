@@ -607,15 +607,22 @@ __host__ __device__ constexpr size_t fused_exchange_bytes() {
   return (size_t)(S::F * S::NP + S::F * S::NO) * sizeof(float2);
 }
 
-template <class S, typename T, bool ADJ, bool TRI>
+// EDIT = kEditThreshold (Sec. 3.2.3) zeroes, in the staged rows, every pixel whose
+// gradient magnitude is below the field's threshold (t2s: squared thresholds of
+// the chunk's fields), with the keep/drop decision of the standalone threshold
+// kernel, before the divergence is formed; the gy row above the item takes its
+// decision from gx of that row, read from global memory ahead of the staging.
+template <class S, typename T, bool ADJ, bool TRI, int EDIT = kEditNone>
 __global__ void __launch_bounds__(S::THREADS, S::MINB_FWD) k_fast_rows_fwd_div(const T* __restrict__ gx,
                                                                      const T* __restrict__ gy,
                                                                      float2* __restrict__ spec,
                                                                      const float2* __restrict__ twg,
                                                                      float* __restrict__ partial, FastArgs A,
                                                                      float2* __restrict__ tri,
-                                                                     const float* __restrict__ cc) {
+                                                                     const float* __restrict__ cc,
+                                                                     const float* __restrict__ t2s = nullptr) {
   static_assert(!(ADJ && TRI), "the adjoint runs the column transforms");
+  static_assert(EDIT == kEditNone || (EDIT == kEditThreshold && !ADJ), "only the threshold edit is staged");
   extern __shared__ __align__(16) float2 sm[];
   float2* tw2 = sm;
   float2* buf = sm + S::R1 * S::R2;
@@ -657,14 +664,62 @@ __global__ void __launch_bounds__(S::THREADS, S::MINB_FWD) k_fast_rows_fwd_div(c
   __syncthreads();
   if (tid == 0 && (int)blockIdx.x < items) issue(blockIdx.x);
   unsigned phase = 0;
+  constexpr int kEdW = (S::N + S::THREADS - 1) / S::THREADS;  // gx values of the row above, per thread
 #pragma unroll 1
   for (int w = blockIdx.x; w < items; w += gridDim.x, phase ^= 1u) {
     const int field = w / A.ngroups, g = w - field * A.ngroups;
+    float gxa[EDIT == kEditThreshold ? kEdW : 1];
+    if constexpr (EDIT == kEditThreshold) {
+      const int r0 = g * RW;
+      const T* src = gx + field * fe + (size_t)(r0 > 0 ? r0 - 1 : 0) * A.W;
+#pragma unroll
+      for (int q = 0; q < kEdW; ++q) {
+        const int j = tid + q * S::THREADS;
+        gxa[q] = (r0 > 0 && j < A.W) ? f_to_f(src[j]) : 0.0f;
+      }
+    }
     const bool landed = mbar_wait(&bar, phase);
     if (__syncthreads_or(!landed)) {  // the copies never completed: report, let them drain, stop
       if (tid == 0) atomicExch(A.err, kErrBulkWait);
       mbar_wait(&bar, phase);
       return;
+    }
+    if constexpr (EDIT == kEditThreshold) {
+      const float t2 = t2s[field];
+      const int r0 = g * RW, nx = (A.H - r0) < RW ? (A.H - r0) : RW;
+      const T zero = f_from_f<T>(0.0f);
+      // staged pixels (r0 + i, j): gx in sgx row i, gy in sgy row i + 1; rows are
+      // 16-byte multiples, so 16 bytes (VE pixels) at a time
+      constexpr int VE = 16 / (int)sizeof(T);
+      const int wv = A.W / VE;
+      for (int idx = tid; idx < nx * wv; idx += S::THREADS) {
+        const int i = idx / wv, jv = idx - i * wv;
+        uint4* xp = reinterpret_cast<uint4*>(sgx + (size_t)i * A.W) + jv;
+        uint4* yp = reinterpret_cast<uint4*>(sgy + (size_t)(i + 1) * A.W) + jv;
+        uint4 xv = *xp, yv = *yp;
+        T* xe = reinterpret_cast<T*>(&xv);
+        T* ye = reinterpret_cast<T*>(&yv);
+        bool any = false;
+#pragma unroll
+        for (int e2 = 0; e2 < VE; ++e2)
+          if (edit_mag2(f_to_f(xe[e2]), f_to_f(ye[e2])) < t2) {
+            xe[e2] = zero;
+            ye[e2] = zero;
+            any = true;
+          }
+        if (any) {
+          *xp = xv;
+          *yp = yv;
+        }
+      }
+      if (r0 > 0) {  // gy of the row above (sgy row 0)
+#pragma unroll
+        for (int q = 0; q < kEdW; ++q) {
+          const int j = tid + q * S::THREADS;
+          if (j < A.W && edit_mag2(gxa[q], f_to_f(sgy[j])) < t2) sgy[j] = zero;
+        }
+      }
+      __syncthreads();
     }
     float2 v[S::R1];
     if (ADJ && act) {
@@ -1158,9 +1213,14 @@ __device__ __forceinline__ void tri_solve_band(float2* buf, const float2* cbuf, 
   }
 }
 
-template <class S, typename T, bool TRI>
+// Per-field statistics of the stored output (colour correction, Eq. 25): item
+// g of a field writes (sum x, sum x^2) of its stored values in FP64 at
+// partial (as doubles) + field * kMaxRowBlocks / 2 + kStatsOff + 2 g.
+constexpr int kStatsOff = 160;
+
+template <class S, typename T, bool TRI, bool STATS>
 __global__ void __launch_bounds__(S::THREADS, S::MINB_INV) k_fast_rows_inv(const float2* __restrict__ Y,
-                                                              const float* __restrict__ partial, T* __restrict__ out,
+                                                              float* __restrict__ partial, T* __restrict__ out,
                                                               const float2* __restrict__ twg, FastArgs A,
                                                               const float2* __restrict__ tri,
                                                               const float* __restrict__ cc) {
@@ -1271,6 +1331,16 @@ __global__ void __launch_bounds__(S::THREADS, S::MINB_INV) k_fast_rows_inv(const
     const bool act2 = act && t < S::JSPAN;
     const float u00 = u00s[parity];
     T* o = out + (size_t)field * A.H * A.W;
+    // STATS: this thread's stored values as float sums about its first value
+    float st_sh = 0.0f, st_s = 0.0f, st_q = 0.0f;
+    int st_n = 0;
+    auto st_add = [&](float x) {
+      if (st_n == 0) st_sh = x;
+      const float d = x - st_sh;
+      st_s += d;
+      st_q = fmaf(d, d, st_q);
+      ++st_n;
+    };
 #pragma unroll
     for (int jj = 0; jj < S::J2; ++jj) {
       const int j = t + S::R2 * jj;
@@ -1294,15 +1364,120 @@ __global__ void __launch_bounds__(S::THREADS, S::MINB_INV) k_fast_rows_inv(const
           // columns of this stage inside [0, WMIN) for every t need no crop test
           const bool sure = (S::R2 * jj + S::R1 * s2 >= kP) && (S::R2 * jj + S::JSPAN - 1 + S::R1 * s2 - kP < S::WMIN);
           if (sure || (jc >= 0 && jc < A.W)) {
-            if (va) o[(size_t)ia * A.W + jc] = f_from_f<T>(u[s2].x - u00);
-            if (vb) o[(size_t)ib * A.W + jc] = f_from_f<T>(u[s2].y - u00);
+            const T qa = f_from_f<T>(u[s2].x - u00), qb = f_from_f<T>(u[s2].y - u00);
+            if (va) o[(size_t)ia * A.W + jc] = qa;
+            if (vb) o[(size_t)ib * A.W + jc] = qb;
+            if constexpr (STATS) {
+              if (va) st_add(f_to_f(qa));
+              if (vb) st_add(f_to_f(qb));
+            }
           }
         }
       }
     }
+    if constexpr (STATS) {
+      // (count, mean, M2) of the thread, combined pairwise (Chan et al.'s update,
+      // stable in FP32) down a shuffle tree and across the warps in order; the
+      // item's (count, mean, M2) go out in FP64
+      float cn = (float)st_n, cm = st_n ? st_sh + st_s / cn : 0.0f, c2 = st_n ? st_q - st_s * (st_s / cn) : 0.0f;
+      auto chan = [](float& n, float& m, float& m2, float nb, float mb, float m2b) {
+        const float nt = n + nb;
+        if (nt > 0.0f) {
+          const float d = mb - m, fb = nb / nt;
+          m = fmaf(d, fb, m);
+          m2 = m2 + m2b + d * d * n * fb;
+        }
+        n = nt;
+      };
+#pragma unroll
+      for (int o2 = 16; o2 > 0; o2 >>= 1) {
+        const float nb = __shfl_xor_sync(0xffffffffu, cn, o2), mb = __shfl_xor_sync(0xffffffffu, cm, o2),
+                    m2b = __shfl_xor_sync(0xffffffffu, c2, o2);
+        chan(cn, cm, c2, nb, mb, m2b);
+      }
+      __shared__ float st_red[3 * (S::THREADS / 32)];
+      if ((tid & 31) == 0) {
+        st_red[3 * (tid >> 5)] = cn;
+        st_red[3 * (tid >> 5) + 1] = cm;
+        st_red[3 * (tid >> 5) + 2] = c2;
+      }
+      __syncthreads();
+      if (tid == 0) {
+        float n = 0.0f, m = 0.0f, m2 = 0.0f;
+        for (int k = 0; k < S::THREADS / 32; ++k) chan(n, m, m2, st_red[3 * k], st_red[3 * k + 1], st_red[3 * k + 2]);
+        double* dst = reinterpret_cast<double*>(partial) + (size_t)field * (kMaxRowBlocks / 2) + kStatsOff + 3 * g;
+        dst[0] = (double)n;
+        dst[1] = (double)m;
+        dst[2] = (double)m2;
+      }
+      // st_red is rewritten only after the next item's barriers
+    }
   }
 }
 
+// Colour correction of Eq. 25 for fields whose statistics the inverse row pass
+// took as it stored them. k_fast_color_finish: one warp per field combines the
+// items' (count, mean, M2) in FP64 in a fixed order (lane-strided, then a
+// shuffle tree) into the field's mean and population standard deviation and
+// writes (mean, gain = ref_std / std or 0 when std = 0, ref_mean) at
+// kColorCoef of the field's scratch. k_fast_color_apply maps
+// x <- (x - mean) gain + ref_mean, 16 bytes per access where the field allows.
+constexpr int kColorCoef = 1200;  // float offset (past the item statistics, 3 doubles per item)
+
+__device__ __forceinline__ void chan_d(double& n, double& m, double& m2, double nb, double mb, double m2b) {
+  const double nt = n + nb;
+  if (nt > 0.0) {
+    const double d = mb - m, fb = nb / nt;
+    m += d * fb;
+    m2 += m2b + d * d * n * fb;
+  }
+  n = nt;
+}
+
+static __global__ void __launch_bounds__(256) k_fast_color_finish(float* __restrict__ partial, int nitems, int nf,
+                                                                  const float* __restrict__ ref_mean,
+                                                                  const float* __restrict__ ref_std) {
+  const int field = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (field >= nf) return;
+  const double* pp = reinterpret_cast<const double*>(partial) + (size_t)field * (kMaxRowBlocks / 2) + kStatsOff;
+  double n = 0.0, m = 0.0, m2 = 0.0;
+  for (int i = lane; i < nitems; i += 32) chan_d(n, m, m2, pp[3 * i], pp[3 * i + 1], pp[3 * i + 2]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double nb = __shfl_down_sync(0xffffffffu, n, o), mb = __shfl_down_sync(0xffffffffu, m, o),
+                 m2b = __shfl_down_sync(0xffffffffu, m2, o);
+    chan_d(n, m, m2, nb, mb, m2b);
+  }
+  if (lane == 0) {
+    const double sd = n > 0.0 ? sqrt(fmax(m2 / n, 0.0)) : 0.0;
+    float* c = partial + (size_t)field * kMaxRowBlocks + kColorCoef;
+    c[0] = (float)m;
+    c[1] = sd > 0.0 ? (float)((double)ref_std[field] / sd) : 0.0f;
+    c[2] = ref_mean[field];
+  }
+}
+
+template <typename T, int V>
+__global__ void __launch_bounds__(256) k_fast_color_apply(T* __restrict__ out, const float* __restrict__ partial,
+                                                          long long n) {
+  const int field = blockIdx.y;
+  const float* c = partial + (size_t)field * kMaxRowBlocks + kColorCoef;
+  const float mc = c[0], gsc = c[1], mi = c[2];
+  T* x = out + (long long)field * n;
+  const long long nv = n / V;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += (long long)gridDim.x * blockDim.x) {
+    if constexpr (V == 4) {
+      float4 v = reinterpret_cast<float4*>(x)[i];
+      v.x = fmaf(v.x - mc, gsc, mi);
+      v.y = fmaf(v.y - mc, gsc, mi);
+      v.z = fmaf(v.z - mc, gsc, mi);
+      v.w = fmaf(v.w - mc, gsc, mi);
+      reinterpret_cast<float4*>(x)[i] = v;
+    } else {
+      x[i] = f_from_f<T>(fmaf(f_to_f(x[i]) - mc, gsc, mi));
+    }
+  }
+}
 
 // ---------------------------------------------------------------------------
 // adjoint pass C: w = inverse transform of the row-major spectrum Y (rows
@@ -1481,7 +1656,8 @@ static cudaError_t run_fast_mode(gfc_plan* P, const Bufs& bf, const T* in0, cons
     return cudaErrorInvalidConfiguration;
   if (tri && (size_t)A.srows * A.ldY > P->spec_field) return cudaErrorInvalidConfiguration;
   static std::mutex mu;
-  static int slots_a = 0, slots_b = 0, slots_c = 0, slots_d = 0, slots_ta = 0, slots_tc = 0, slots_td = 0;
+  static int slots_a = 0, slots_b = 0, slots_c = 0, slots_d = 0, slots_ta = 0, slots_tc = 0, slots_td = 0,
+             slots_ts = 0, slots_tde = 0;
   cudaError_t e;
   {
     std::lock_guard<std::mutex> lock(mu);
@@ -1493,10 +1669,14 @@ static cudaError_t run_fast_mode(gfc_plan* P, const Bufs& bf, const T* in0, cons
         if ((e = fast_setup(k_fast_rows_adj<RS, T>, RS::THREADS, RS::smem_bytes_adj(), &slots_c)) != cudaSuccess)
           return e;
       } else {
-        if ((e = fast_setup(k_fast_rows_inv<RS, T, false>, RS::THREADS, RS::smem_bytes(), &slots_c)) != cudaSuccess)
-          return e;
-        if ((e = fast_setup(k_fast_rows_inv<RS, T, true>, RS::THREADS, RS::smem_bytes_tri_inv(), &slots_tc)) !=
+        if ((e = fast_setup(k_fast_rows_inv<RS, T, false, false>, RS::THREADS, RS::smem_bytes(), &slots_c)) !=
             cudaSuccess)
+          return e;
+        if ((e = fast_setup(k_fast_rows_inv<RS, T, true, false>, RS::THREADS, RS::smem_bytes_tri_inv(), &slots_tc)) !=
+            cudaSuccess)
+          return e;
+        if (MODE == 0 && (e = fast_setup(k_fast_rows_inv<RS, T, true, true>, RS::THREADS, RS::smem_bytes_tri_inv(),
+                                         &slots_ts)) != cudaSuccess)
           return e;
         // the sweep stages all bands of 32 columns: size it for the most bands any
         // image on this torus has (H <= M - 2p)
@@ -1516,6 +1696,9 @@ static cudaError_t run_fast_mode(gfc_plan* P, const Bufs& bf, const T* in0, cons
       if (MODE == 0 && (e = fast_setup(k_fast_rows_fwd_div<RS, T, false, true>, RS::THREADS, RS::smem_bytes_fwd(),
                                        &slots_td)) != cudaSuccess)
         return e;
+      if (MODE == 0 && (e = fast_setup(k_fast_rows_fwd_div<RS, T, false, true, kEditThreshold>, RS::THREADS,
+                                       RS::smem_bytes_fwd(), &slots_tde)) != cudaSuccess)
+        return e;
     }
   }
   auto grid_for = [](long items, int slots) { return (int)(items < slots ? items : slots); };
@@ -1523,13 +1706,20 @@ static cudaError_t run_fast_mode(gfc_plan* P, const Bufs& bf, const T* in0, cons
   // its packing of grad_out (with the row-pair sums) into it, when the rows can
   // be bulk-copied and their staging fits the exchange buffers.
   const size_t stage = (MODE == 2) ? (size_t)2 * RS::F * P->W * sizeof(T) : fused_stage_bytes<RS, T>(P->W);
-  const bool fused_div = MODE != 1 && !(ed && ed->kind != kEditNone) && (P->W * sizeof(T)) % 16 == 0 &&
+  const int edit_kind = (MODE == 0 && ed) ? ed->kind : kEditNone;
+  // the threshold edit is staged with the gradient (recursive column solve plans)
+  const bool fused_edit = edit_kind == kEditThreshold && tri;
+  const bool fused_div = MODE != 1 && (edit_kind == kEditNone || fused_edit) && (P->W * sizeof(T)) % 16 == 0 &&
                          stage <= fused_exchange_bytes<RS>() && getenv("GFC_UNFUSED_DIV") == nullptr;
   const long a_items = (long)nf * A.ngroups;
   if (fused_div) {
     prof_begin(P, 0, st);
     if constexpr (MODE == 0) {
-      if (tri)
+      if (fused_edit)
+        k_fast_rows_fwd_div<RS, T, false, true, kEditThreshold>
+            <<<grid_for(a_items, slots_tde), RS::THREADS, RS::smem_bytes_fwd(), st>>>(
+                in0, in1, bf.spec, P->twN, bf.partial, A, bf.tri, P->colcoef, ed->t2);
+      else if (tri)
         k_fast_rows_fwd_div<RS, T, false, true><<<grid_for(a_items, slots_td), RS::THREADS, RS::smem_bytes_fwd(), st>>>(
             in0, in1, bf.spec, P->twN, bf.partial, A, bf.tri, P->colcoef);
       else
@@ -1546,7 +1736,7 @@ static cudaError_t run_fast_mode(gfc_plan* P, const Bufs& bf, const T* in0, cons
     const int nq = A.ldz / 4;
     const int bx = (MODE == 2) ? ((nq + 31) / 32) * 32 : (nq >= 256 ? 256 : ((nq + 31) / 32) * 32);
     const dim3 grid((nq + bx - 1) / bx, A.zpairs, nf);
-    const int kind = (MODE == 0 && ed) ? ed->kind : kEditNone;
+    const int kind = fused_div ? kEditNone : edit_kind;  // a fused edit needs no pass L
     const int ex = ((nq + 31) / 32) * 32 <= 512 ? ((nq + 31) / 32) * 32 : 256;  // whole warps
     const dim3 egrid((nq + ex - 1) / ex, (A.zpairs + kEditPairs - 1) / kEditPairs, nf);
     if (kind == kEditThreshold)
@@ -1593,14 +1783,37 @@ static cudaError_t run_fast_mode(gfc_plan* P, const Bufs& bf, const T* in0, cons
         bf.zbuf, out0, out1, P->twN, C);
   } else {
     C.ngroups = ((P->H + 1) / 2 + RS::F - 1) / RS::F;
-    if (tri) {
+    const bool stats = MODE == 0 && tri && ed && ed->ref_mean;
+    if (stats && (kStatsOff + 3 * C.ngroups > kColorCoef / 2 || nkb > kStatsOff)) return cudaErrorInvalidConfiguration;
+    if (stats) {
       C.nparts = nkb;
-      k_fast_rows_inv<RS, T, true>
+      k_fast_rows_inv<RS, T, true, true>
+          <<<grid_for((long)nf * C.ngroups, slots_ts), RS::THREADS, RS::smem_bytes_tri_inv(), st>>>(
+              bf.spec, bf.partial, out0, P->twN, C, bf.tri, P->colcoef);
+    } else if (tri) {
+      C.nparts = nkb;
+      k_fast_rows_inv<RS, T, true, false>
           <<<grid_for((long)nf * C.ngroups, slots_tc), RS::THREADS, RS::smem_bytes_tri_inv(), st>>>(
               bf.spec, bf.partial, out0, P->twN, C, bf.tri, P->colcoef);
     } else {
-      k_fast_rows_inv<RS, T, false><<<grid_for((long)nf * C.ngroups, slots_c), RS::THREADS, RS::smem_bytes(), st>>>(
-          bf.zbuf, bf.partial, out0, P->twN, C, nullptr, nullptr);
+      k_fast_rows_inv<RS, T, false, false>
+          <<<grid_for((long)nf * C.ngroups, slots_c), RS::THREADS, RS::smem_bytes(), st>>>(
+              bf.zbuf, bf.partial, out0, P->twN, C, nullptr, nullptr);
+    }
+    if (stats) {
+      prof_end(P, st);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      prof_begin(P, 3, st);  // counted with the other non-transform pass
+      const long long n = (long long)P->H * P->W;
+      k_fast_color_finish<<<(nf + 7) / 8, 256, 0, st>>>(bf.partial, C.ngroups, nf, ed->ref_mean, ed->ref_std);
+      const bool v4 = sizeof(T) == 4 && n % 4 == 0 && (reinterpret_cast<uintptr_t>(out0) & 15) == 0;
+      const long long per = v4 ? n / 4 : n;
+      int nblk = (int)((per + 256 * 8 - 1) / (256 * 8));
+      if (nblk < 1) nblk = 1;
+      if (v4)
+        k_fast_color_apply<T, 4><<<dim3(nblk, nf), 256, 0, st>>>(out0, bf.partial, n);
+      else
+        k_fast_color_apply<T, 1><<<dim3(nblk, nf), 256, 0, st>>>(out0, bf.partial, n);
     }
   }
   prof_end(P, st);

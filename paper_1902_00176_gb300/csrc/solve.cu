@@ -476,7 +476,7 @@ static cudaError_t run_chunk(gfc_plan* P, const Bufs& bf, const T* in0, const T*
                              cudaStream_t st, const EditArgs* ed = nullptr) {
   if (P->exact) return run_chunk_exact(P, bf, MODE, in0, in1, out0, out1, nf, st, ed);
   if (P->fast) return run_chunk_fast(P, bf, MODE, in0, in1, out0, out1, nf, st, ed);
-  const EditArgs none{kEditNone, 0.0f, nullptr, nullptr};
+  const EditArgs none{kEditNone, 0.0f, nullptr, nullptr, nullptr, nullptr};
   const EditArgs& E = ed ? *ed : none;
   // pass A
   PassArgs A = base_args(P);
@@ -547,11 +547,15 @@ static gfc_status run_all(gfc_plan* P, const void* a, const void* b, void* o0, v
     T* out0 = static_cast<T*>(o0) + f0 * fe;
     T* out1 = o1 ? static_cast<T*>(o1) + f0 * fe : nullptr;
     const int s = fork ? (int)(c % P->nslots) : 0;
-    EditArgs ec{kEditNone, 0.0f, nullptr, nullptr};
+    EditArgs ec{kEditNone, 0.0f, nullptr, nullptr, nullptr, nullptr};
     if (ed) {  // the edit's per-field data, at this chunk's first field
       ec = *ed;
       if (ec.edges) ec.edges = static_cast<const T*>(ec.edges) + f0 * fe;
       if (ec.t2) ec.t2 += f0;
+      if (ec.ref_mean) {
+        ec.ref_mean += f0;
+        ec.ref_std += f0;
+      }
     }
     cudaError_t e = run_chunk<T, MODE>(P, slot_bufs(P, s), in0, in1, out0, out1, nf,
                                        fork ? P->slot_stream[s] : P->stream, ed ? &ec : nullptr);
@@ -594,7 +598,7 @@ static gfc_status run_ragged(gfc_plan* P, const void* a, const void* b, void* o0
       prof_begin(P, 0, st);
       k<<<dim3(ceil_div(pairs_max, ppb), nf), 256, smem, st>>>(static_cast<const T*>(a), static_cast<const T*>(b),
                                                                  P->spec, P->partial, P->twN, A,
-                                                                 EditArgs{kEditNone, 0.0f, nullptr, nullptr});
+                                                                 EditArgs{kEditNone, 0.0f, nullptr, nullptr, nullptr, nullptr});
       prof_end(P, st);
       if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "gfc ragged pass A");
     }
@@ -780,6 +784,35 @@ gfc_status gfc_solve_from_gradient(gfc_plan* plan, const void* gx, const void* g
   return dispatch<kGrad>(plan, gx, gy, out, nullptr);
 }
 
+}  // extern "C"
+
+// Validate `edit` and turn it into the passes' EditArgs (the threshold's per-field
+// squared thresholds prepared in the plan's scratch).
+static gfc_status prepare_edit(gfc_plan* plan, const void* gx, const void* gy, const gfc_edit* edit, EditArgs* ed,
+                               const char* who) {
+  *ed = EditArgs{kEditNone, 0.0f, nullptr, nullptr, nullptr, nullptr};
+  if (!edit || edit->kind == GFC_EDIT_NONE) return GFC_OK;
+  if (plan->ragged) return fail(GFC_ERR_UNSUPPORTED, "%s: ragged plans are not supported", who);
+  if (edit->kind == GFC_EDIT_THRESHOLD) {
+    if (!(edit->frac >= 0.0f) || !(edit->ref == edit->ref))
+      return fail(GFC_ERR_INVALID_ARG, "%s: frac must be >= 0 and ref a number", who);
+    if (gfc_status s = edit_prepare_threshold(plan, gx, gy, edit->frac, edit->ref)) return s;
+    ed->kind = kEditThreshold;
+    ed->t2 = plan->edit_t2;
+  } else if (edit->kind == GFC_EDIT_MERGE) {
+    if (!edit->edges) return fail(GFC_ERR_INVALID_ARG, "%s: merge needs an edge map", who);
+    if (!(edit->alpha >= 0.0f && edit->alpha <= 1.0f)) return fail(GFC_ERR_INVALID_ARG, "%s: alpha outside [0, 1]", who);
+    ed->kind = kEditMerge;
+    ed->alpha = edit->alpha;
+    ed->edges = edit->edges;
+  } else {
+    return fail(GFC_ERR_INVALID_ARG, "%s: unknown edit kind %d", who, edit->kind);
+  }
+  return GFC_OK;
+}
+
+extern "C" {
+
 gfc_status gfc_solve_edited(gfc_plan* plan, const void* gx, const void* gy, const gfc_edit* edit, void* out) {
   clear_error();
   if (!plan || !gx || !gy || !edit || !out) return fail(GFC_ERR_INVALID_ARG, "gfc_solve_edited: null argument");
@@ -788,25 +821,33 @@ gfc_status gfc_solve_edited(gfc_plan* plan, const void* gx, const void* gy, cons
   if (out == gx || out == gy || out == edit->edges)
     return fail(GFC_ERR_INVALID_ARG, "gfc_solve_edited: out aliases an input");
   if (edit->kind == GFC_EDIT_NONE) return dispatch<kGrad>(plan, gx, gy, out, nullptr);
-  if (plan->ragged) return fail(GFC_ERR_UNSUPPORTED, "gfc_solve_edited: ragged plans are not supported");
-  EditArgs ed{kEditNone, 0.0f, nullptr, nullptr};
-  if (edit->kind == GFC_EDIT_THRESHOLD) {
-    if (!(edit->frac >= 0.0f) || !(edit->ref == edit->ref))
-      return fail(GFC_ERR_INVALID_ARG, "gfc_solve_edited: frac must be >= 0 and ref a number");
-    if (gfc_status s = edit_prepare_threshold(plan, gx, gy, edit->frac, edit->ref)) return s;
-    ed.kind = kEditThreshold;
-    ed.t2 = plan->edit_t2;
-  } else if (edit->kind == GFC_EDIT_MERGE) {
-    if (!edit->edges) return fail(GFC_ERR_INVALID_ARG, "gfc_solve_edited: merge needs an edge map");
-    if (!(edit->alpha >= 0.0f && edit->alpha <= 1.0f))
-      return fail(GFC_ERR_INVALID_ARG, "gfc_solve_edited: alpha outside [0, 1]");
-    ed.kind = kEditMerge;
-    ed.alpha = edit->alpha;
-    ed.edges = edit->edges;
-  } else {
-    return fail(GFC_ERR_INVALID_ARG, "gfc_solve_edited: unknown edit kind %d", edit->kind);
-  }
+  EditArgs ed;
+  if (gfc_status s = prepare_edit(plan, gx, gy, edit, &ed, "gfc_solve_edited")) return s;
   return dispatch<kGrad>(plan, gx, gy, out, nullptr, &ed);
+}
+
+gfc_status gfc_solve_corrected(gfc_plan* plan, const void* gx, const void* gy, const gfc_edit* edit,
+                               const float* ref_mean, const float* ref_std, void* out) {
+  clear_error();
+  if (!plan || !gx || !gy || !ref_mean || !ref_std || !out)
+    return fail(GFC_ERR_INVALID_ARG, "gfc_solve_corrected: null argument");
+  if (misaligned(gx) || misaligned(gy) || misaligned(out))
+    return fail(GFC_ERR_INVALID_ARG, "gfc_solve_corrected: pointers must be 16-byte aligned");
+  if (out == gx || out == gy || (edit && out == edit->edges))
+    return fail(GFC_ERR_INVALID_ARG, "gfc_solve_corrected: out aliases an input");
+  if (plan->ragged) return fail(GFC_ERR_UNSUPPORTED, "gfc_solve_corrected: ragged plans are not supported");
+  if (plan->fast && plan->tri && !plan->exact) {
+    EditArgs ed;
+    if (gfc_status s = prepare_edit(plan, gx, gy, edit, &ed, "gfc_solve_corrected")) return s;
+    ed.ref_mean = ref_mean;
+    ed.ref_std = ref_std;
+    return dispatch<kGrad>(plan, gx, gy, out, nullptr, &ed);
+  }
+  // other plans: the solve, then the separate statistics and correction passes
+  gfc_status s = (edit && edit->kind != GFC_EDIT_NONE) ? gfc_solve_edited(plan, gx, gy, edit, out)
+                                                       : gfc_solve_from_gradient(plan, gx, gy, out);
+  if (s != GFC_OK) return s;
+  return gfc_color_correct(plan, out, ref_mean, ref_std);
 }
 
 gfc_status gfc_solve_from_laplacian(gfc_plan* plan, const void* lap, void* out) {

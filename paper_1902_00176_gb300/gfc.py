@@ -81,6 +81,8 @@ _SIGNATURES = {
     "gfc_plan_copy_green": [ctypes.c_void_p, ctypes.c_void_p],
     "gfc_solve_from_gradient": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
     "gfc_solve_edited": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(_Edit), ctypes.c_void_p],
+    "gfc_solve_corrected": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(_Edit),
+                            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
     "gfc_solve_from_laplacian": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
     "gfc_backward": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
     "gfc_fft_c2c": [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
@@ -233,6 +235,28 @@ class Plan:
         e = _Edit(EDIT_KINDS[edit], float(frac), float(ref), float(alpha), eptr)
         self._bind_stream()
         _check(lib().gfc_solve_edited(self._h, gx.data_ptr(), gy.data_ptr(), ctypes.byref(e), out.data_ptr()))
+        return out
+
+    def solve_corrected(self, gx, gy, ref_mean, ref_std, edit="none", frac=0.1, ref=0.0, alpha=0.5, edges=None,
+                        out=None):
+        """Edit (optional), solve and colour-correct (Eq. 25) in one call: each field is
+        rescaled to ``ref_mean`` / ``ref_std`` ([batch, C] float32, e.g. from field_stats
+        of the original image)."""
+        gx, gy = self._check_field(gx, "gx"), self._check_field(gy, "gy")
+        ref_mean, ref_std = self._stats_tensor(ref_mean, "ref_mean"), self._stats_tensor(ref_std, "ref_std")
+        if edit not in EDIT_KINDS:
+            raise ValueError(f"unknown edit {edit!r}")
+        eptr = None
+        if edit == "merge":
+            if edges is None:
+                raise ValueError("merge needs an edge map")
+            edges = self._check_field(edges, "edges")
+            eptr = edges.data_ptr()
+        out = self._empty() if out is None else self._check_field(out, "out")
+        e = _Edit(EDIT_KINDS[edit], float(frac), float(ref), float(alpha), eptr)
+        self._bind_stream()
+        _check(lib().gfc_solve_corrected(self._h, gx.data_ptr(), gy.data_ptr(), ctypes.byref(e), ref_mean.data_ptr(),
+                                         ref_std.data_ptr(), out.data_ptr()))
         return out
 
     def solve_from_laplacian(self, lap, out=None):

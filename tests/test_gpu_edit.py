@@ -275,3 +275,78 @@ def test_solve_edited_rejects_bad_edits():
     st = gfc.lib().gfc_solve_edited(p._h, x.data_ptr(), x.data_ptr(), gfc.ctypes.byref(e), out.data_ptr())
     assert st == 1
     p.close()
+
+
+# ---- the editing flow in one call: edit, solve, colour-correct (Eq. 25 fused) ---------
+
+@pytest.mark.parametrize("edit", ["none", "threshold", "merge"])
+@pytest.mark.parametrize("H,W,C,B,dt", [(801, 1200, 1, 3, "f32"), (64, 96, 3, 2, "f32"), (256, 256, 2, 2, "bf16")])
+def test_solve_corrected_matches_two_step_and_oracle(H, W, C, B, dt, edit):
+    """gfc_solve_corrected (statistics taken as the last pass stores the field) against
+    the solve followed by gfc_color_correct, and against the oracle's flow."""
+    img, gx, gy, edges = synth.edit_batch(B, C, H, W, seed=6300)
+    p = gfc.Plan(H, W, C=C, batch=B, dtype=DT[dt], device=DEV)
+    dx, dy, de = _dev(gx, DT[dt]), _dev(gy, DT[dt]), _dev(edges, DT[dt])
+    m, s = p.field_stats(_dev(img, DT[dt]))
+    kw = {"none": {}, "threshold": dict(frac=0.1), "merge": dict(alpha=0.5, edges=de)}[edit]
+    one = p.solve_corrected(dx, dy, m, s, edit=edit, **kw)
+    two = p.solve_edited(dx, dy, edit, **kw)
+    p.color_correct(two, m, s)
+    tol = REL_F32 if dt == "f32" else REL_16
+    assert _rel(_np(one), _np(two)) <= (1e-6 if dt == "f32" else tol)
+    again = p.solve_corrected(dx, dy, m, s, edit=edit, **kw)
+    assert torch.equal(one, again)  # fixed reduction order
+    if dt != "f32" and edit == "merge":
+        p.close()  # 16-bit merge rounds the merged gradient to storage first: two-step parity only
+        return
+    mm, ss = _np(m), _np(s)
+    X, Y, E = _np(dx), _np(dy), _np(de)
+    for b in range(B):
+        for c in range(C):
+            ex, ey = X[b, c], Y[b, c]
+            if edit == "threshold":
+                ex, ey, _ = oracle.gradient_threshold(ex.astype(np.float32), ey.astype(np.float32), 0.1)
+            elif edit == "merge":
+                ex, ey = oracle.gradient_merge(ex, ey, E[b, c], 0.5)
+            ic = oracle.solve_from_gradient(np.asarray(ex, np.float64), np.asarray(ey, np.float64), p.M, p.N, p.pad)
+            ref = oracle.color_correct_with(ic, mm.reshape(B, C)[b, c], ss.reshape(B, C)[b, c])
+            got = _np(one)[b, c]
+            if dt == "f32":
+                assert _rel(got, ref) <= REL_F32 and np.abs(got - ref).max() <= 1e-4, (b, c, _rel(got, ref))
+            else:
+                # rounded to 16 bits twice, by the solve's store and after the correction's
+                # gain g = ref_std / std(I_c): the first rounding reaches the result
+                # scaled by g (the bound used for every twice-rounded 16-bit result)
+                g = ss.reshape(B, C)[b, c] / max(float(np.std(ic)), 1e-300)
+                tol = REL_16 * (1.0 + g * np.linalg.norm(ic - ic.mean()) / np.linalg.norm(ref))
+                assert _rel(got, ref) <= tol, (b, c, _rel(got, ref), tol)
+    p.close()
+
+
+@pytest.mark.parametrize("kw", [dict(H=40, W=56), dict(H=801, W=1200, column_fft=True)])
+def test_solve_corrected_on_other_plans_is_the_two_step_flow(kw):
+    """Plans without the recursive column solve (generic sizes, column-FFT plans) run
+    the solve and then gfc_color_correct: the same bits as the two calls."""
+    B, C = 2, 1
+    img, gx, gy, _ = synth.edit_batch(B, C, kw["H"], kw["W"], seed=6400)
+    p = gfc.Plan(C=C, batch=B, device=DEV, **kw)
+    dx, dy = _dev(gx), _dev(gy)
+    m, s = p.field_stats(_dev(img))
+    one = p.solve_corrected(dx, dy, m, s, edit="threshold", frac=0.2)
+    two = p.solve_edited(dx, dy, "threshold", frac=0.2)
+    p.color_correct(two, m, s)
+    assert torch.equal(one, two)
+    p.close()
+
+
+def test_solve_corrected_rejects_bad_arguments():
+    p = gfc.Plan(32, 48, device=DEV)
+    x = torch.zeros((1, 1, 32, 48), device=DEV)
+    m = torch.zeros((1, 1), device=DEV)
+    e = gfc._Edit(0, 0.0, 0.0, 0.5, None)
+    st = gfc.lib().gfc_solve_corrected(p._h, x.data_ptr(), x.data_ptr(), gfc.ctypes.byref(e), None, m.data_ptr(),
+                                       torch.empty_like(x).data_ptr())
+    assert st == 1
+    with pytest.raises(gfc.GFCError):
+        p.solve_corrected(x, x.clone(), m, m, edit="merge", alpha=2.0, edges=x.clone())
+    p.close()
