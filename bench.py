@@ -54,10 +54,22 @@ def smooth_even_at_least(n: int) -> int:
         n += 2
 
 
+# Row lengths with register-resident row passes (the library's gfc_row_lengths;
+# a CPU test checks that the two agree).
+ROW_LENGTHS = (108, 140, 160, 180, 200, 224, 252, 270, 294, 320, 360, 400, 448, 500, 560, 630, 700, 784, 882, 980,
+               1080, 1120, 1200, 1250, 1372, 1400, 1536, 1568, 1750, 1960, 2058)
+
+
 def padded_size(H: int, W: int, pad: int = 4):
     """(M, N) of the SMOOTH padded torus, computed here so that the oracle legs never
-    load the product library (a CPU test checks it against the library's rule)."""
-    return smooth_even_at_least(H + 2 * pad), smooth_even_at_least(W + 2 * pad)
+    load the product library (a CPU test checks it against the library's rule): M the
+    smallest even 7-smooth size >= H + 2p, N the smallest compiled row length >= W + 2p
+    when W + 2p lies in (136, 2058], else as M."""
+    n = W + 2 * pad
+    N = smooth_even_at_least(n)
+    if 136 < n <= ROW_LENGTHS[-1]:
+        N = min(r for r in ROW_LENGTHS if r >= n)
+    return smooth_even_at_least(H + 2 * pad), N
 
 
 def torchrun_command(gpus: int, argv, env, python=None):

@@ -61,8 +61,12 @@ typedef enum {
   GFC_ERR_TIMEOUT = 5      /* a bounded device-side wait ran out */
 } gfc_status;
 
-/* GFC_SIZE_SMOOTH: M, N = smallest even 7-smooth sizes >= H + 2p, W + 2p (the
- * register-resident transforms). GFC_SIZE_EXACT: Algorithm A's own size,
+/* GFC_SIZE_SMOOTH: M = the smallest even 7-smooth size >= H + 2p; N = the
+ * smallest row length >= W + 2p that has register-resident row passes
+ * (gfc_row_lengths) when W + 2p lies in (136, 2058], else the smallest even
+ * 7-smooth size >= W + 2p. Either way the torus is at least Algorithm A's
+ * padded size and the extra zero rows and columns go to the bottom and right:
+ * the same least-squares problem on a slightly larger torus. GFC_SIZE_EXACT: Algorithm A's own size,
  * M = H + 2p, N = W + 2p, whatever their prime factors (Bluestein's chirp-z
  * for lengths that are not 7-smooth); H + 2p and W + 2p <= 2048, uniform plans;
  * solves, edited solves and the adjoint (gfc_backward) on that torus. */
@@ -108,6 +112,11 @@ typedef struct {
  * Writes M, N; returns GFC_ERR_INVALID_ARG for H or W < 2 or null outputs,
  * GFC_ERR_UNSUPPORTED when M or N would exceed the largest supported length. */
 gfc_status gfc_padded_size(int H, int W, int pad, int size_policy, int* M, int* N);
+
+/* The row lengths N with register-resident row passes, ascending. Writes up to
+ * `capacity` of them to `lengths` (may be NULL when capacity is 0) and returns
+ * how many there are. Host-only. */
+int gfc_row_lengths(int* lengths, int capacity);
 
 /* Create a plan for batch x C fields of H x W in `dtype` on the current CUDA
  * device (Algorithm A: the Green spectrum is built once per size, in FP64 on

@@ -33,6 +33,7 @@
 #include <cuda_runtime.h>
 
 #include <mutex>
+#include <type_traits>
 
 #include "fft_reg.cuh"
 #include "gfc_internal.h"
@@ -43,18 +44,19 @@ namespace gfc {
 // The register-resident schedules assume Algorithm A's pad of 4.
 constexpr int kP = 4;
 
-constexpr bool cx_smooth7(int n) {
-  if (n < 1) return false;
-  for (int f : {2, 3, 5, 7})
-    while (n % f == 0) n /= f;
-  return n == 1;
-}
-// smallest image width that pads to N under the SMOOTH policy (pad kP)
+// smallest image width that pads to row length N under the SMOOTH policy (pad
+// kP): the row kernels skip the crop test for columns below it
 constexpr int cx_min_width(int N) {
-  int prev = N - 2;
-  while (prev > 0 && !cx_smooth7(prev)) prev -= 2;
-  return prev - 2 * kP + 1;
+  int lo = N;
+  for (int n = N; n > 2 * kP && cx_row_policy(n) >= N; --n)
+    if (cx_row_policy(n) == N) lo = n;
+  return lo - 2 * kP;
 }
+
+// Column schedule placeholder of a shape compiled for its row length only.
+struct NoCols {
+  static constexpr int C = 1;
+};
 
 struct FastArgs {
   int H, W, p, M, N, Nh, ldM;
@@ -858,24 +860,31 @@ static __global__ void __launch_bounds__(32) k_adj_total(double* __restrict__ pa
 }
 
 // ---------------------------------------------------------------------------
-// Recursive column solve, between the row passes. A block takes 32 columns of
-// one field and stages their band sums (all bands, both directions) in shared
-// memory; warp 0 sweeps the causal sums, warp 1 the anticausal ones, one lane
-// per column l >= 1:
-//   causal:     P_0 = 0, P_{g+1} = e_g + T_g P_g (T_g = a^(rows of band g));
-//               the rows after the last band (tail) and above band 0 (pad) are
-//               zero, so a^tail P_G = (1 - a^M) y[M-1] and the carry into band g
-//               is c_g = P_g + a^(2F g) a^p y[M-1];
-//   anticausal: Q_{G-1} = 0, Q_{g-1} = e'_g + T_g Q_g; a^p Q_{-1} = (1 - a^M) y'[0];
-//               the carry from below band g is Q_g + a^tail (prod_{j>g} T_j) y'[0]
-// (the powers from the plan's FP64 table). The carries replace the sums. Row 0
-// of the solved spectrum (a padding row, X = 0) is U[0][l] = C_l (a y[M-1] +
-// y'[0]); the block's FP64 sum of w_l Re U[0][l] (w = 1 at l = N/2, else 2) is
-// its partial of u[0,0], which the inverse row pass adds in block order.
-// Column 0 (b = 2, singular) is the 1D periodic Poisson problem with its mean
-// removed (the reading G[0,0] = 0): warp 2 of block 0 solves it exactly in
-// FP64 from prefix sums over the torus rows and writes it into S.
+// Recursive column solve, between the row passes: the carry sweep. A block
+// takes 32 columns (one per lane) of one field; its kTriSeg warps cut the G
+// bands into segments. With T_g = a^(rows of band g):
+//   causal:     the carry into band g is c_g, c_{g+1} = e_g + T_g c_g around the
+//               cycle, where the rows after the last band (tail) and above band 0
+//               (pad) are zero: a^tail (c_G - prod T c_0) = (1 - a^M) y[M-1] -
+//               ..., i.e. with P the sweep of the e_g from a zero carry,
+//               y[M-1] = a^tail P_G / (1 - a^M) and c_0 = a^p y[M-1];
+//   anticausal: the carry from below band g is q_g, q_{g-1} = e'_g + T_g q_g,
+//               q_{G-1} = a^tail y'[0], y'[0] = a^p Q_{-1} / (1 - a^M) with Q the
+//               sweep from a zero carry.
+// Each warp sweeps its segment from zero carries (both directions); warps 0
+// and 1 then sweep the segment totals (segment transfers a^(2F n) from the
+// plan's FP64 power table) and close the cycle; every warp re-sweeps its
+// segment from its true carries and writes c_g, q_g (the band sums are read
+// twice, the second time from cache). Row 0 of the solved spectrum (a padding
+// row, X = 0) is U[0][l] = C_l (a y[M-1] + y'[0]): the block's FP64 sum of
+// w_l Re U[0][l] (w = 1 at l = N/2, else 2) is its partial of u[0,0], added in
+// block order by the inverse row pass. Column 0 (b = 2, singular) is the 1D
+// periodic Poisson problem with its mean removed (the reading G[0,0] = 0): the
+// extra warp of block 0 solves it exactly in FP64 and writes it into S.
 // ---------------------------------------------------------------------------
+constexpr int kTriMaxM = 2112;  // column 0 of the longest supported column
+constexpr int kTriSeg = kTriSegments;  // band segments (warps) per sweep block
+
 __device__ __forceinline__ double warp_sum_d(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -892,18 +901,14 @@ __device__ __forceinline__ double warp_exclusive_scan_d(double v) {
   return x - v;
 }
 
-constexpr int kTriMaxM = 2112;  // column 0 of the longest register-resident column
-
 // Column 0 of one field (warp-wide, FP64): d[r] = u[r+1] - u[r] has
 // d[r] - d[r-1] = f[r] - mean(f); periodicity fixes d[-1] = -sum_r G[r] / M with
 // G the prefix sums; u[0] = 0 (any constant is removed with u[0,0]: column 0
-// adds w_0 U[0][0] = u[0] / N = 0 to it). The column is read once into shared
-// memory; each lane then walks a contiguous run of torus rows; the solution
-// (1/N folded in) replaces column 0 of S.
+// adds w_0 U[0][0] = u[0] / N = 0 to it). fcol[p + i] holds column 0 of S row
+// i (bulk copy of pass A's compact copy); each lane walks a contiguous run of
+// torus rows; the solution (1/N folded in) replaces column 0 of S.
 static __device__ __noinline__ void tri_column0(float2* __restrict__ spec, float* fcol, int field,
                                                 const FastArgs& A) {
-  // fcol[p + i] holds column 0 of S row i (bulk copy of pass A's compact copy);
-  // the other torus rows are zero
   const int lane = threadIdx.x & 31;
   float2* col = spec + (size_t)field * A.srows * A.ldY;
   const int nr = min(A.srows, A.M - A.p);  // S rows on the torus
@@ -933,97 +938,141 @@ static __device__ __noinline__ void tri_column0(float2* __restrict__ spec, float
   }
 }
 
-static __global__ void __launch_bounds__(96) k_tri_carries(float2* __restrict__ spec, float2* __restrict__ tri,
-                                                          const float* __restrict__ cc,
-                                                          const float* __restrict__ powc,
-                                                          double* __restrict__ partial, FastArgs A) {
-  extern __shared__ __align__(16) float2 sm[];  // [G][2][kTriCols] band sums, then [2G][kTriCols] powers
-  float* pws = reinterpret_cast<float*>(sm + (size_t)2 * A.G * kTriCols);
+static __global__ void __launch_bounds__(32 * (kTriSeg + 1)) k_tri_carries(float2* __restrict__ spec,
+                                                                          float2* __restrict__ tri,
+                                                                          const float* __restrict__ cc,
+                                                                          const float* __restrict__ powc,
+                                                                          double* __restrict__ partial, FastArgs A) {
+  __shared__ float2 seg_e[kTriSeg][kTriCols], seg_q[kTriSeg][kTriCols];  // segment totals, then carries
   __shared__ float2 y0s[kTriCols];
+  __shared__ float yls[2 * kTriCols];
   __shared__ __align__(16) float fcol[kTriMaxM + 4];  // block 0: column 0 of S (compact copy)
   __shared__ __align__(8) uint64_t bar;
   const int kb = blockIdx.x, field = blockIdx.y, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int k = kb * kTriCols + lane;
-  float2* tf = tri + (size_t)field * A.tri_field;
-  // stage this block's tile of band sums [G][2][32] and of powers [2G][32],
-  // and in block 0 the compact column 0, by three bulk copies on one barrier
-  const unsigned seg = (unsigned)(kTriCols * sizeof(float2)), pseg = (unsigned)(kTriCols * sizeof(float));
-  const int nr = min(A.srows, A.M - A.p);  // S rows on the torus
+  const bool col_ok = k >= 1 && k < A.Nh;
+  const float2* sums = tri_sums(tri, field, A) + (size_t)kb * 2 * A.G * kTriCols + lane;  // [g][2][32]
+  float2* carry = tri + (size_t)field * A.tri_field + k;                                 // [g][2][ldY]
+  // column 0's compact copy for block 0's extra warp, in flight during the sweeps
+  const int nr = min(A.srows, A.M - A.p);
   const unsigned cbytes = (unsigned)((nr * sizeof(float) + 15) & ~(size_t)15);
-  if (tid == 0) {
+  if (kb == 0 && tid == 32 * kTriSeg) {
     mbar_init(&bar, 1);
-    mbar_expect_tx(&bar, (seg + pseg) * (unsigned)(2 * A.G) + (kb == 0 ? cbytes : 0u));
+    mbar_expect_tx(&bar, cbytes);
+    bulk_copy(fcol + A.p, tri_col0(tri, field, A), cbytes, &bar);
   }
-  __syncthreads();
-  if (tid == 0) {  // the tile of band sums, the tile of powers, block 0: column 0
-    bulk_copy(sm, tri_sums(tri, field, A) + (size_t)kb * 2 * A.G * kTriCols, (unsigned)(2 * A.G) * seg, &bar);
-    bulk_copy(pws, powc + (size_t)kb * 2 * A.G * kTriCols, (unsigned)(2 * A.G) * pseg, &bar);
-    if (kb == 0) bulk_copy(fcol + A.p, tri_col0(tri, field, A), cbytes, &bar);
-  }
-  // per-column constants, loaded while the copies are in flight
   float4 c03 = make_float4(0.0f, 0.0f, 0.0f, 0.0f), c47 = c03;
-  if (warp < 2 && k >= 1 && k < A.Nh) {
+  if (col_ok) {
     c03 = __ldg(reinterpret_cast<const float4*>(cc + (size_t)k * 8));
     c47 = __ldg(reinterpret_cast<const float4*>(cc + (size_t)k * 8) + 1);
   }
-  const bool landed = mbar_wait(&bar, 0);
-  if (__syncthreads_or(!landed)) {  // the copies never completed: report, let them drain, stop
-    if (tid == 0) atomicExch(A.err, kErrBulkWait);
-    mbar_wait(&bar, 0);
-    return;
+  const float a = c03.y, C = c03.z, Tb = c03.w, Tl = c47.x, Tp = c47.y, inv = c47.z, Tt = c47.w;
+  const int per = (A.G + kTriSeg - 1) / kTriSeg;
+  const int g0 = min(warp * per, A.G), g1 = min(g0 + per, A.G);
+  // phase 1: each segment from zero carries
+  if (warp < kTriSeg) {
+    float2 t = make_float2(0.0f, 0.0f), q = t;
+    if (col_ok) {
+#pragma unroll 4
+      for (int g = g0; g < g1; ++g) {
+        const float T = (g == A.G - 1) ? Tl : Tb;
+        const float2 e = sums[(size_t)g * 2 * kTriCols];
+        t = make_float2(fmaf(T, t.x, e.x), fmaf(T, t.y, e.y));
+      }
+#pragma unroll 4
+      for (int g = g1 - 1; g >= g0; --g) {
+        const float T = (g == A.G - 1) ? Tl : Tb;
+        const float2 e = sums[(size_t)g * 2 * kTriCols + kTriCols];
+        q = make_float2(fmaf(T, q.x, e.x), fmaf(T, q.y, e.y));
+      }
+    }
+    seg_e[warp][lane] = t;
+    seg_q[warp][lane] = q;
   }
-  if (warp == 2 && kb == 0) tri_column0(spec, fcol, field, A);
-  const bool col_ok = warp < 2 && k >= 1 && k < A.Nh;
-  float2 yl = make_float2(0.0f, 0.0f);  // warp 0: y[M-1]
-  if (col_ok) {
-    const float Tb = c03.w, Tl = c47.x, Tp = c47.y, inv = c47.z, Tt = c47.w;
-    float2 t = make_float2(0.0f, 0.0f);
+  __syncthreads();
+  // phase 2: the segment totals around the cycle (warp 0 causal, warp 1 anticausal)
+  if (warp < 2 && col_ok) {
+    float Ts[kTriSeg];  // transfer of segment s: a^(rows of its bands), all loaded at once
+#pragma unroll
+    for (int s2 = 0; s2 < kTriSeg; ++s2) {
+      const int b0 = min(s2 * per, A.G), b1 = min(b0 + per, A.G);
+      Ts[s2] = (b1 <= b0) ? 1.0f
+                          : (b1 < A.G ? __ldg(powc + (size_t)(b1 - b0) * A.ldY + k)
+                                      : __ldg(powc + (size_t)(b1 - b0 - 1) * A.ldY + k) * Tl);
+    }
+    auto seg_T = [&](int s2) { return Ts[s2]; };
     if (warp == 0) {
-#pragma unroll 8
-      for (int g = 0; g < A.G; ++g) {
-        const float T = (g == A.G - 1) ? Tl : Tb;
-        float2* slot = sm + (size_t)(2 * g) * kTriCols + lane;
-        const float2 e = *slot;
-        *slot = t;
+      float2 t = make_float2(0.0f, 0.0f);
+#pragma unroll
+      for (int s = 0; s < kTriSeg; ++s) {
+        const float T = seg_T(s);
+        const float2 e = seg_e[s][lane];
         t = make_float2(fmaf(T, t.x, e.x), fmaf(T, t.y, e.y));
       }
-      yl = make_float2(Tt * t.x * inv, Tt * t.y * inv);        // y[M-1], past the tail rows
-      const float2 ci = make_float2(Tp * yl.x, Tp * yl.y);       // y[p-1]
-#pragma unroll 8
-      for (int g = 0; g < A.G; ++g) {
-        const float w = pws[(size_t)g * kTriCols + lane];
-        const float2 P = sm[(size_t)(2 * g) * kTriCols + lane];
-        tf[(size_t)(2 * g) * A.ldY + k] = make_float2(fmaf(w, ci.x, P.x), fmaf(w, ci.y, P.y));
+      const float2 yl = make_float2(Tt * t.x * inv, Tt * t.y * inv);  // y[M-1]
+      float2 c = make_float2(Tp * yl.x, Tp * yl.y);                   // y[p-1]: carry into band 0
+#pragma unroll
+      for (int s = 0; s < kTriSeg; ++s) {
+        const float T = seg_T(s);
+        const float2 e = seg_e[s][lane];
+        seg_e[s][lane] = c;
+        c = make_float2(fmaf(T, c.x, e.x), fmaf(T, c.y, e.y));
       }
+      yls[lane] = yl.x;
     } else {
-#pragma unroll 8
-      for (int g = A.G - 1; g >= 0; --g) {
-        const float T = (g == A.G - 1) ? Tl : Tb;
-        float2* slot = sm + (size_t)(2 * g + 1) * kTriCols + lane;
-        const float2 e = *slot;
-        *slot = t;
-        t = make_float2(fmaf(T, t.x, e.x), fmaf(T, t.y, e.y));
+      float2 q = make_float2(0.0f, 0.0f);
+#pragma unroll
+      for (int s = kTriSeg - 1; s >= 0; --s) {
+        const float T = seg_T(s);
+        const float2 e = seg_q[s][lane];
+        q = make_float2(fmaf(T, q.x, e.x), fmaf(T, q.y, e.y));
       }
-      const float2 y0 = make_float2(Tp * t.x * inv, Tp * t.y * inv);  // y'[0]
-#pragma unroll 8
-      for (int g = 0; g < A.G; ++g) {
-        const float w = pws[(size_t)(A.G + g) * kTriCols + lane];
-        const float2 Q = sm[(size_t)(2 * g + 1) * kTriCols + lane];
-        tf[(size_t)(2 * g + 1) * A.ldY + k] = make_float2(fmaf(w, y0.x, Q.x), fmaf(w, y0.y, Q.y));
+      const float2 y0 = make_float2(Tp * q.x * inv, Tp * q.y * inv);  // y'[0]
+      float2 c = make_float2(Tt * y0.x, Tt * y0.y);                   // carry from below the last band
+#pragma unroll
+      for (int s = kTriSeg - 1; s >= 0; --s) {
+        const float T = seg_T(s);
+        const float2 e = seg_q[s][lane];
+        seg_q[s][lane] = c;
+        c = make_float2(fmaf(T, c.x, e.x), fmaf(T, c.y, e.y));
       }
       y0s[lane] = y0;
     }
   }
   __syncthreads();
+  // phase 3: each segment again from its true carries; the carries go out
+  if (warp < kTriSeg && col_ok) {
+    float2 c = seg_e[warp][lane];
+#pragma unroll 4
+    for (int g = g0; g < g1; ++g) {
+      const float T = (g == A.G - 1) ? Tl : Tb;
+      const float2 e = sums[(size_t)g * 2 * kTriCols];
+      carry[(size_t)(2 * g) * A.ldY] = c;
+      c = make_float2(fmaf(T, c.x, e.x), fmaf(T, c.y, e.y));
+    }
+    float2 q = seg_q[warp][lane];
+#pragma unroll 4
+    for (int g = g1 - 1; g >= g0; --g) {
+      const float T = (g == A.G - 1) ? Tl : Tb;
+      const float2 e = sums[(size_t)g * 2 * kTriCols + kTriCols];
+      carry[(size_t)(2 * g + 1) * A.ldY] = q;
+      q = make_float2(fmaf(T, q.x, e.x), fmaf(T, q.y, e.y));
+    }
+  }
   if (warp == 0) {
     double acc = 0.0;
-    if (col_ok) {
-      const float a = c03.y, C = c03.z;
-      const float2 y0 = y0s[lane];
-      acc = (2 * k == A.N ? 1.0 : 2.0) * (double)(C * fmaf(a, yl.x, y0.x));
-    }
+    if (col_ok) acc = (2 * k == A.N ? 1.0 : 2.0) * (double)(C * fmaf(a, yls[lane], y0s[lane].x));
     acc = warp_sum_d(acc);
     if (lane == 0) partial[(size_t)field * (kMaxRowBlocks / 2) + kb] = acc;
+  }
+  if (warp == kTriSeg && kb == 0) {
+    const bool landed = mbar_wait(&bar, 0);
+    if (!landed) {  // the copy never completed: report, let it drain, stop
+      if (lane == 0) atomicExch(A.err, kErrBulkWait);
+      mbar_wait(&bar, 0);
+      return;
+    }
+    tri_column0(spec, fcol, field, A);
   }
 }
 
@@ -1632,9 +1681,12 @@ static cudaError_t fast_setup(K kernel, int threads, size_t smem, int* slots) {
 template <class RS, class CS, typename T, int MODE>
 static cudaError_t run_fast_mode(gfc_plan* P, const Bufs& bf, const T* in0, const T* in1, T* out0, T* out1, int nf,
                                  cudaStream_t st, const EditArgs* ed = nullptr) {
-  static_assert(RS::N <= 2048, "the adjoint packing pass covers a whole row in one block");
+  constexpr bool kCols = !std::is_same_v<CS, NoCols>;  // column transforms compiled for this shape
+  static_assert(!kCols || RS::N <= 2048, "the adjoint packing pass covers a whole row in one block");
+  static_assert(kCols || MODE != 2, "the adjoint runs the column transforms");
   constexpr bool kTriMode = MODE != 2;
   const bool tri = kTriMode && P->tri;
+  if (!kCols && !tri) return cudaErrorNotSupported;
   FastArgs A;
   A.H = P->H; A.W = P->W; A.p = P->pad; A.M = P->M; A.N = P->N; A.Nh = P->Nh; A.ldM = P->ldM;
   A.nrows = (MODE == 0) ? P->H + 1 : P->H;
@@ -1644,7 +1696,7 @@ static cudaError_t run_fast_mode(gfc_plan* P, const Bufs& bf, const T* in0, cons
   A.ngroups = (A.npairs + RS::F - 1) / RS::F;
   if (tri) A.ngroups = P->triG;  // the bands of the column solve: every mode uses the gradient's
   A.zpairs = A.ngroups * RS::F;
-  A.nparts = (P->Nh + CS::C - 1) / CS::C;
+  A.nparts = kCols ? (P->Nh + CS::C - 1) / CS::C : 0;
   A.nf = nf;
   A.ldY = (P->Nh + 3) & ~3;
   A.err = P->dev_err;
@@ -1661,44 +1713,45 @@ static cudaError_t run_fast_mode(gfc_plan* P, const Bufs& bf, const T* in0, cons
   cudaError_t e;
   {
     std::lock_guard<std::mutex> lock(mu);
-    if (!slots_a) {
+    static bool ready = false;
+    if (!ready) {
       int unused = 0;
       if ((e = fast_setup(k_fast_div<T, MODE>, 512, 0, &unused)) != cudaSuccess) return e;
-      if ((e = fast_setup(k_fast_cols<CS, MODE>, CS::THREADS, CS::smem_bytes(), &slots_b)) != cudaSuccess) return e;
-      if (MODE == 2) {
-        if ((e = fast_setup(k_fast_rows_adj<RS, T>, RS::THREADS, RS::smem_bytes_adj(), &slots_c)) != cudaSuccess)
+      if constexpr (kCols) {
+        if ((e = fast_setup(k_fast_cols<CS, MODE>, CS::THREADS, CS::smem_bytes(), &slots_b)) != cudaSuccess) return e;
+        if constexpr (MODE == 2) {
+          if ((e = fast_setup(k_fast_rows_adj<RS, T>, RS::THREADS, RS::smem_bytes_adj(), &slots_c)) != cudaSuccess)
+            return e;
+        } else {
+          if ((e = fast_setup(k_fast_rows_inv<RS, T, false, false>, RS::THREADS, RS::smem_bytes(), &slots_c)) !=
+              cudaSuccess)
+            return e;
+        }
+        if ((e = fast_setup(k_fast_rows_fwd<RS, false>, RS::THREADS, RS::smem_bytes_fwd(), &slots_a)) != cudaSuccess)
           return e;
-      } else {
-        if ((e = fast_setup(k_fast_rows_inv<RS, T, false, false>, RS::THREADS, RS::smem_bytes(), &slots_c)) !=
-            cudaSuccess)
+        if (MODE != 1 && (e = fast_setup(k_fast_rows_fwd_div<RS, T, MODE == 2, false>, RS::THREADS,
+                                         RS::smem_bytes_fwd(), &slots_d)) != cudaSuccess)
           return e;
+      }
+      if constexpr (MODE != 2) {
         if ((e = fast_setup(k_fast_rows_inv<RS, T, true, false>, RS::THREADS, RS::smem_bytes_tri_inv(), &slots_tc)) !=
             cudaSuccess)
-          return e;
-        if (MODE == 0 && (e = fast_setup(k_fast_rows_inv<RS, T, true, true>, RS::THREADS, RS::smem_bytes_tri_inv(),
-                                         &slots_ts)) != cudaSuccess)
-          return e;
-        // the sweep stages all bands of 32 columns: size it for the most bands any
-        // image on this torus has (H <= M - 2p)
-        int unused_k = 0;
-        constexpr int kGmax = (((CS::M - 2 * kP + 2) / 2) + RS::F - 1) / RS::F;
-        if ((e = fast_setup(k_tri_carries, 96, (size_t)2 * kGmax * kTriCols * (sizeof(float2) + sizeof(float)),
-                            &unused_k)) != cudaSuccess)
           return e;
         if ((e = fast_setup(k_fast_rows_fwd<RS, true>, RS::THREADS, RS::smem_bytes_fwd(), &slots_ta)) != cudaSuccess)
           return e;
       }
-      if ((e = fast_setup(k_fast_rows_fwd<RS, false>, RS::THREADS, RS::smem_bytes_fwd(), &slots_a)) != cudaSuccess)
-        return e;
-      if (MODE != 1 && (e = fast_setup(k_fast_rows_fwd_div<RS, T, MODE == 2, false>, RS::THREADS,
-                                       RS::smem_bytes_fwd(), &slots_d)) != cudaSuccess)
-        return e;
-      if (MODE == 0 && (e = fast_setup(k_fast_rows_fwd_div<RS, T, false, true>, RS::THREADS, RS::smem_bytes_fwd(),
-                                       &slots_td)) != cudaSuccess)
-        return e;
-      if (MODE == 0 && (e = fast_setup(k_fast_rows_fwd_div<RS, T, false, true, kEditThreshold>, RS::THREADS,
-                                       RS::smem_bytes_fwd(), &slots_tde)) != cudaSuccess)
-        return e;
+      if constexpr (MODE == 0) {
+        if ((e = fast_setup(k_fast_rows_inv<RS, T, true, true>, RS::THREADS, RS::smem_bytes_tri_inv(), &slots_ts)) !=
+            cudaSuccess)
+          return e;
+        if ((e = fast_setup(k_fast_rows_fwd_div<RS, T, false, true>, RS::THREADS, RS::smem_bytes_fwd(), &slots_td)) !=
+            cudaSuccess)
+          return e;
+        if ((e = fast_setup(k_fast_rows_fwd_div<RS, T, false, true, kEditThreshold>, RS::THREADS,
+                            RS::smem_bytes_fwd(), &slots_tde)) != cudaSuccess)
+          return e;
+      }
+      ready = true;
     }
   }
   auto grid_for = [](long items, int slots) { return (int)(items < slots ? items : slots); };
@@ -1722,10 +1775,10 @@ static cudaError_t run_fast_mode(gfc_plan* P, const Bufs& bf, const T* in0, cons
       else if (tri)
         k_fast_rows_fwd_div<RS, T, false, true><<<grid_for(a_items, slots_td), RS::THREADS, RS::smem_bytes_fwd(), st>>>(
             in0, in1, bf.spec, P->twN, bf.partial, A, bf.tri, P->colcoef);
-      else
+      else if constexpr (kCols)
         k_fast_rows_fwd_div<RS, T, false, false><<<grid_for(a_items, slots_d), RS::THREADS, RS::smem_bytes_fwd(), st>>>(
             in0, in1, bf.spec, P->twN, bf.partial, A, nullptr, nullptr);
-    } else {
+    } else if constexpr (kCols) {
       k_fast_rows_fwd_div<RS, T, MODE == 2, false><<<grid_for(a_items, slots_d), RS::THREADS, RS::smem_bytes_fwd(), st>>>(
           in0, in1, bf.spec, P->twN, bf.partial, A, nullptr, nullptr);
     }
@@ -1754,7 +1807,7 @@ static cudaError_t run_fast_mode(gfc_plan* P, const Bufs& bf, const T* in0, cons
     if (tri)
       k_fast_rows_fwd<RS, true><<<grid_for(a_items, slots_ta), RS::THREADS, RS::smem_bytes_fwd(), st>>>(
           bf.zbuf, bf.spec, P->twN, A, bf.tri, P->colcoef);
-    else
+    else if constexpr (kCols)
       k_fast_rows_fwd<RS, false><<<grid_for(a_items, slots_a), RS::THREADS, RS::smem_bytes_fwd(), st>>>(
           bf.zbuf, bf.spec, P->twN, A, nullptr, nullptr);
     prof_end(P, st);
@@ -1763,9 +1816,9 @@ static cudaError_t run_fast_mode(gfc_plan* P, const Bufs& bf, const T* in0, cons
   prof_begin(P, 1, st);
   const int nkb = (P->Nh + kTriCols - 1) / kTriCols;  // column blocks of the sweep (u[0,0] partials)
   if (tri) {
-    k_tri_carries<<<dim3(nkb, nf), 96, (size_t)2 * A.G * kTriCols * (sizeof(float2) + sizeof(float)), st>>>(
-        bf.spec, bf.tri, P->colcoef, P->powc, reinterpret_cast<double*>(bf.partial), A);
-  } else {
+    k_tri_carries<<<dim3(nkb, nf), 32 * (kTriSeg + 1), 0, st>>>(bf.spec, bf.tri, P->colcoef, P->powc,
+                                                                 reinterpret_cast<double*>(bf.partial), A);
+  } else if constexpr (kCols) {
     if (MODE == 2) {
       k_adj_total<<<nf, 32, 0, st>>>(reinterpret_cast<double*>(bf.partial), A.zpairs);
       P->prof.launches[1] += 1;  // a second launch in this pass
@@ -1782,6 +1835,7 @@ static cudaError_t run_fast_mode(gfc_plan* P, const Bufs& bf, const T* in0, cons
     k_fast_rows_adj<RS, T><<<grid_for((long)nf * C.ngroups, slots_c), RS::THREADS, RS::smem_bytes_adj(), st>>>(
         bf.zbuf, out0, out1, P->twN, C);
   } else {
+    (void)out1;
     C.ngroups = ((P->H + 1) / 2 + RS::F - 1) / RS::F;
     const bool stats = MODE == 0 && tri && ed && ed->ref_mean;
     if (stats && (kStatsOff + 3 * C.ngroups > kColorCoef / 2 || nkb > kStatsOff)) return cudaErrorInvalidConfiguration;
@@ -1795,7 +1849,7 @@ static cudaError_t run_fast_mode(gfc_plan* P, const Bufs& bf, const T* in0, cons
       k_fast_rows_inv<RS, T, true, false>
           <<<grid_for((long)nf * C.ngroups, slots_tc), RS::THREADS, RS::smem_bytes_tri_inv(), st>>>(
               bf.spec, bf.partial, out0, P->twN, C, bf.tri, P->colcoef);
-    } else {
+    } else if constexpr (kCols) {
       k_fast_rows_inv<RS, T, false, false>
           <<<grid_for((long)nf * C.ngroups, slots_c), RS::THREADS, RS::smem_bytes(), st>>>(
               bf.zbuf, bf.partial, out0, P->twN, C, nullptr, nullptr);
@@ -1818,6 +1872,21 @@ static cudaError_t run_fast_mode(gfc_plan* P, const Bufs& bf, const T* in0, cons
   }
   prof_end(P, st);
   return cudaGetLastError();
+}
+
+// Shapes compiled for their row length only (the recursive column solve needs
+// no column kernels): FP32 solves and edited solves; the caller falls back to
+// the generic passes for anything else (cudaErrorNotSupported).
+template <class RS>
+cudaError_t run_rows_shape(gfc_plan* P, const Bufs& bf, int mode, const void* in0, const void* in1, void* out0,
+                           void* out1, int nf, cudaStream_t st, const EditArgs* ed) {
+  if (P->dtype != GFC_F32 || mode == 2 || !P->tri) return cudaErrorNotSupported;
+  const float* a = static_cast<const float*>(in0);
+  const float* b = static_cast<const float*>(in1);
+  float* o0 = static_cast<float*>(out0);
+  float* o1 = static_cast<float*>(out1);
+  if (mode == 0) return run_fast_mode<RS, NoCols, float, 0>(P, bf, a, b, o0, o1, nf, st, ed);
+  return run_fast_mode<RS, NoCols, float, 1>(P, bf, a, b, o0, o1, nf, st);
 }
 
 template <class RS, class CS>

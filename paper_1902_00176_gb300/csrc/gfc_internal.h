@@ -10,6 +10,35 @@
 #include "fft_core.cuh"
 
 namespace gfc {
+// Row lengths with register-resident row passes, ascending: the SMOOTH size
+// policy picks N from them (the smallest >= W + 2p when W + 2p lies in
+// (kRowPolicyMin, last]), and the row kernels take the narrowest image that
+// maps to their N from them. solve_fast.cu registers a kernel set for each.
+constexpr int kRowLengthList[] = {108,  140,  160,  180,  200,  224,  252,  270,  294,  320,  360,
+                                  400,  448,  500,  560,  630,  700,  784,  882,  980,  1080, 1120,
+                                  1200, 1250, 1372, 1400, 1536, 1568, 1750, 1960, 2058};
+constexpr int kRowPolicyMin = 136;
+
+constexpr bool cx_is_smooth7(int n) {
+  if (n < 1) return false;
+  for (int f : {2, 3, 5, 7})
+    while (n % f == 0) n /= f;
+  return n == 1;
+}
+constexpr int cx_smooth_even_at_least(int x) {
+  int n = x + (x & 1);
+  while (!cx_is_smooth7(n)) n += 2;
+  return n;
+}
+// the SMOOTH policy's row length for W + 2p = n
+constexpr int cx_row_policy(int n) {
+  constexpr int last = kRowLengthList[sizeof(kRowLengthList) / sizeof(int) - 1];
+  if (n > kRowPolicyMin && n <= last)
+    for (int r : kRowLengthList)
+      if (r >= n) return r;
+  return cx_smooth_even_at_least(n);
+}
+
 // scratch of one chunk in flight
 struct Bufs {
   float2* spec;    // spectrum
@@ -50,7 +79,8 @@ struct gfc_plan {
   int Nh;     // N/2 + 1 Hermitian columns
   int ldS;    // row stride of the row-major spectrum scratch (generic passes), complex elements
   int ldM;    // column stride of the column-major spectrum scratch (fast passes)
-  bool fast;  // both transform lengths have register-resident schedules
+  bool fast;  // the row length has register-resident passes (fast_kernels.cuh)
+  bool fast_cols;  // ... and the column length has them too (column FFT path, adjoint)
   bool tri;   // fast passes with the column direction by recursive filters (gfc_column_solver)
   int triG;   // bands of the recursive column solve (pass A's items)
   size_t tri_field;  // complex elements per field of the band scratch
@@ -122,12 +152,17 @@ bool is_7smooth(long n);
 cudaError_t build_twiddles(float2* tw, int n, cudaStream_t s);
 cudaError_t build_green(float* G, int M, int N, int Nh, cudaStream_t s);
 cudaError_t build_green_t(float* GT, int M, int N, int Nh, int ldM, cudaStream_t s);
-// recursive column solve tables: cc [Nh][8], pw [2 G][ldY] (bands of `band` rows from row `pad`)
+// recursive column solve tables: cc [Nh][8], pw [tri_power_rows(G)][ldY] (bands of `band` rows
+// from row `pad`; the carry sweep cuts the G bands into 8 segments)
+constexpr int kTriSegments = 8;
+inline int tri_power_rows(int G) { return (G + kTriSegments - 1) / kTriSegments + 1; }
 cudaError_t build_colcoef(float* cc, float* pw, int M, int N, int Nh, int ldY, int pad, int G, int band,
                           cudaStream_t s);
 
 // register-resident passes (solve_fast.cu): spectrum laid out [l][r]
-bool fast_supported(int M, int N);
+bool fast_supported(int M, int N);      // row and column passes compiled for M x N
+bool fast_rows_supported(int N);        // row passes compiled for N alone (recursive column solve, FP32)
+int fast_row_lengths(int* out, int cap);  // compiled row lengths, ascending; returns the count
 size_t fast_zbuf_elems(int H, int M, int N);  // per field
 int fast_row_items(int M, int N);             // row pairs per item of the row passes (F)
 // mode 0 gradient, 1 Laplacian, 2 adjoint (out1 = grad_gy)

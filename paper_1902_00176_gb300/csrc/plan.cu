@@ -141,16 +141,12 @@ __global__ void k_build_colcoef(float* cc, float* dc, int M, int N, int Nh, int 
   }
 }
 
-// Carry weights of the bands, in tiles of 32 columns [ceil(ldY/32)][2 G][32]:
-// row g holds a^(band g) (the causal carry into band 0 reaching band g), row
-// G + g holds a^(tail + rows of the bands after g) (the anticausal carry at the
-// end of the last band reaching band g).
-__global__ void k_build_powc(float* pw, int N, int Nh, int ldY, int G, int band, int last, int tail) {
-  const int nkb = (ldY + 31) / 32;
-  const long total = (long)nkb * 2 * G * 32;
+// Segment transfers of the carry sweep, [rows][ldY]: row r holds a^(band r),
+// the transfer of r full bands (FP64, rounded once).
+__global__ void k_build_powc(float* pw, int N, int Nh, int ldY, int rows, int band) {
+  const long total = (long)rows * ldY;
   for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
-    const int kb = (int)(idx / (2L * G * 32)), rem = (int)(idx % (2L * G * 32));
-    const int row = rem / 32, l = kb * 32 + rem % 32;
+    const int r = (int)(idx / ldY), l = (int)(idx % ldY);
     if (l == 0 || l >= Nh) {
       pw[idx] = 0.0f;
       continue;
@@ -158,14 +154,7 @@ __global__ void k_build_powc(float* pw, int N, int Nh, int ldY, int G, int band,
     const double sn = sinpi((double)l / (double)N);
     const double d = 4.0 * sn * sn;
     const double a = 2.0 / (2.0 + d + sqrt(d * (4.0 + d)));
-    double e;
-    if (row < G) {
-      e = (double)band * row;
-    } else {
-      const int g = row - G;
-      e = (double)tail + (g < G - 1 ? (double)band * (G - 2 - g) + last : 0.0);
-    }
-    pw[idx] = (float)pow(a, e);
+    pw[idx] = (float)pow(a, (double)band * r);
   }
 }
 
@@ -174,10 +163,11 @@ cudaError_t build_colcoef(float* cc, float* pw, int M, int N, int Nh, int ldY, i
   const int last = (M - pad - band * (G - 1)) < band ? (M - pad - band * (G - 1)) : band;
   const int tail = (M - pad - band * G) > 0 ? (M - pad - band * G) : 0;
   k_build_colcoef<<<(ldY + 255) / 256, 256, 0, s>>>(cc, cc + (size_t)Nh * 8, M, N, Nh, ldY, pad, band, last, tail);
-  const long total = (long)((ldY + 31) / 32) * 2 * G * 32;
+  const int rows = tri_power_rows(G);
+  const long total = (long)rows * ldY;
   int blocks = (int)((total + 255) / 256);
   if (blocks > 4096) blocks = 4096;
-  k_build_powc<<<blocks, 256, 0, s>>>(pw, N, Nh, ldY, G, band, last, tail);
+  k_build_powc<<<blocks, 256, 0, s>>>(pw, N, Nh, ldY, rows, band);
   return cudaGetLastError();
 }
 
@@ -249,12 +239,19 @@ gfc_status gfc_padded_size(int H, int W, int pad, int size_policy, int* M, int* 
   if ((long)H + 2L * pad > kMaxFftLen || (long)W + 2L * pad > kMaxFftLen)
     return fail(GFC_ERR_UNSUPPORTED, "gfc_padded_size: H+2p=%ld or W+2p=%ld exceeds %d", (long)H + 2L * pad,
                 (long)W + 2L * pad, kMaxFftLen);
-  int m = smooth_even_at_least(H + 2 * pad), n = smooth_even_at_least(W + 2 * pad);
+  // M: the smallest even 7-smooth length; N: the smallest row length with
+  // register-resident passes when W + 2p lies in their range, else as M
+  const int m = smooth_even_at_least(H + 2 * pad), n = cx_row_policy(W + 2 * pad);
   if (m > kMaxFftLen || n > kMaxFftLen)
     return fail(GFC_ERR_UNSUPPORTED, "gfc_padded_size: padded size %dx%d exceeds %d", m, n, kMaxFftLen);
   *M = m;
   *N = n;
   return GFC_OK;
+}
+
+int gfc_row_lengths(int* lengths, int capacity) {
+  clear_error();
+  return fast_row_lengths(lengths, lengths ? capacity : 0);
 }
 
 gfc_status gfc_plan_create_ex(gfc_plan** out, const gfc_plan_opts* o) {
@@ -276,11 +273,16 @@ gfc_status gfc_plan_create_ex(gfc_plan** out, const gfc_plan_opts* o) {
   p->H = o->H; p->W = o->W; p->C = o->C; p->batch = o->batch; p->pad = pad; p->dtype = o->dtype;
   p->M = M; p->N = N; p->Nh = N / 2 + 1; p->ldS = (p->Nh + 3) & ~3; p->ldM = (M + 3) & ~3;
   p->exact = o->size_policy == GFC_SIZE_EXACT;
-  p->fast = !p->exact && fast_supported(M, N) && pad == 4 && getenv("GFC_FORCE_GENERIC") == nullptr;
   if (o->column_solver != GFC_COLUMN_RECURSIVE && o->column_solver != GFC_COLUMN_FFT) {
     free(p);
     return fail(GFC_ERR_INVALID_ARG, "gfc_plan_create: unknown column solver %d", o->column_solver);
   }
+  const bool usable = !p->exact && pad == 4 && getenv("GFC_FORCE_GENERIC") == nullptr;
+  p->fast_cols = usable && fast_supported(M, N);
+  // row-only lengths run FP32 with the recursive column solve
+  const bool rows_only = usable && !p->fast_cols && fast_rows_supported(N) && o->dtype == GFC_F32 &&
+                         o->column_solver == GFC_COLUMN_RECURSIVE;
+  p->fast = p->fast_cols || rows_only;
   p->tri = p->fast && o->column_solver == GFC_COLUMN_RECURSIVE;
   if (p->tri) {
     const int F = fast_row_items(M, N);
@@ -332,7 +334,7 @@ gfc_status gfc_plan_create_ex(gfc_plan** out, const gfc_plan_opts* o) {
 
   cudaError_t e = cudaGetDevice(&p->device);
   if (e == cudaSuccess) e = cudaMalloc(&p->G, (size_t)M * p->Nh * sizeof(float));
-  if (e == cudaSuccess && p->fast) e = cudaMalloc(&p->GT, (size_t)p->Nh * p->ldM * sizeof(float));
+  if (e == cudaSuccess && p->fast_cols) e = cudaMalloc(&p->GT, (size_t)p->Nh * p->ldM * sizeof(float));
   if (e == cudaSuccess && p->fast) e = cudaMalloc(&p->zbuf, p->zbuf_field * chunk * nslots * sizeof(float2));
   if (e == cudaSuccess) e = cudaMalloc(&p->twN, (size_t)N * sizeof(float2));
   if (e == cudaSuccess) e = cudaMalloc(&p->twM, (size_t)M * sizeof(float2));
@@ -340,8 +342,7 @@ gfc_status gfc_plan_create_ex(gfc_plan** out, const gfc_plan_opts* o) {
   if (e == cudaSuccess) e = cudaMalloc(&p->partial, (size_t)chunk * nslots * kMaxRowBlocks * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc(&p->edit_t2, (size_t)fields * sizeof(float));
   if (e == cudaSuccess && p->tri) e = cudaMalloc(&p->colcoef, ((size_t)p->Nh * 8 + 2 * (size_t)p->ldS) * sizeof(float));
-  if (e == cudaSuccess && p->tri)
-    e = cudaMalloc(&p->powc, (size_t)((p->ldS + 31) / 32) * 2 * p->triG * 32 * sizeof(float));
+  if (e == cudaSuccess && p->tri) e = cudaMalloc(&p->powc, (size_t)tri_power_rows(p->triG) * p->ldS * sizeof(float));
   // (+64 bytes: the sweep's bulk copy of a field's column 0 rounds up to 16 bytes)
   if (e == cudaSuccess && p->tri) e = cudaMalloc(&p->tri_buf, p->tri_field * chunk * nslots * sizeof(float2) + 64);
   for (int sl = 0; sl < nslots && e == cudaSuccess; ++sl) {
@@ -356,7 +357,7 @@ gfc_status gfc_plan_create_ex(gfc_plan** out, const gfc_plan_opts* o) {
   if (e == cudaSuccess) e = build_twiddles(p->twN, N, bs);
   if (e == cudaSuccess) e = build_twiddles(p->twM, M, bs);
   if (e == cudaSuccess) e = build_green(p->G, M, N, p->Nh, bs);
-  if (e == cudaSuccess && p->fast) e = build_green_t(p->GT, M, N, p->Nh, p->ldM, bs);
+  if (e == cudaSuccess && p->fast_cols) e = build_green_t(p->GT, M, N, p->Nh, p->ldM, bs);
   if (e == cudaSuccess && p->tri)
     e = build_colcoef(p->colcoef, p->powc, M, N, p->Nh, p->ldS, pad, p->triG, 2 * fast_row_items(M, N), bs);
   if (e == cudaSuccess && p->exact) e = exact_setup(p, bs);

@@ -475,7 +475,10 @@ template <typename T, int MODE>
 static cudaError_t run_chunk(gfc_plan* P, const Bufs& bf, const T* in0, const T* in1, T* out0, T* out1, int nf,
                              cudaStream_t st, const EditArgs* ed = nullptr) {
   if (P->exact) return run_chunk_exact(P, bf, MODE, in0, in1, out0, out1, nf, st, ed);
-  if (P->fast) return run_chunk_fast(P, bf, MODE, in0, in1, out0, out1, nf, st, ed);
+  if (P->fast) {  // register-resident passes; the generic ones serve what they do not cover
+    const cudaError_t e = run_chunk_fast(P, bf, MODE, in0, in1, out0, out1, nf, st, ed);
+    if (e != cudaErrorNotSupported) return e;
+  }
   const EditArgs none{kEditNone, 0.0f, nullptr, nullptr, nullptr, nullptr};
   const EditArgs& E = ed ? *ed : none;
   // pass A

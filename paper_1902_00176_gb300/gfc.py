@@ -71,6 +71,7 @@ _lib_lock = threading.Lock()
 _SIGNATURES = {
     "gfc_padded_size": [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                         ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
+    "gfc_row_lengths": [ctypes.POINTER(ctypes.c_int), ctypes.c_int],
     "gfc_plan_create": [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                         ctypes.c_int],
     "gfc_plan_create_ex": [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(_Opts)],
@@ -137,6 +138,14 @@ def padded_size(H: int, W: int, pad: int = 4, exact: bool = False):
     M, N = ctypes.c_int(), ctypes.c_int()
     _check(lib().gfc_padded_size(H, W, pad, 1 if exact else 0, ctypes.byref(M), ctypes.byref(N)))
     return M.value, N.value
+
+
+def row_lengths():
+    """Row lengths N with register-resident row passes, ascending (host-only)."""
+    n = lib().gfc_row_lengths(None, 0)
+    buf = (ctypes.c_int * n)()
+    lib().gfc_row_lengths(buf, n)
+    return list(buf)
 
 
 def _stream_ptr(device) -> int:

@@ -35,13 +35,33 @@ def _smooth(n):
 
 
 @pytest.mark.parametrize("H,W,pad", [(64, 96, 4), (801, 1200, 4), (1024, 1536, 4), (256, 256, 4), (16, 16, 4),
-                                     (2, 2, 1), (127, 2048, 4), (999, 4000, 3), (500, 700, 0)])
+                                     (2, 2, 1), (127, 2048, 4), (999, 4000, 3), (500, 700, 0), (300, 1000, 4),
+                                     (40, 129, 4), (40, 128, 4), (2040, 2050, 4), (123, 2051, 4)])
 def test_padded_size_policy(gfc_lib, H, W, pad):
+    """M: the smallest even 7-smooth size >= H + 2p. N: the smallest compiled row
+    length >= W + 2p when W + 2p lies in (136, max length], else as M."""
     M, N = gfc.padded_size(H, W, pad)
     p = 4 if pad <= 0 else pad
-    for size, need in ((M, H + 2 * p), (N, W + 2 * p)):
-        assert size % 2 == 0 and _smooth(size) and size >= need
-        assert not any(m % 2 == 0 and _smooth(m) for m in range(need, size))
+    rows = gfc.row_lengths()
+    need = H + 2 * p
+    assert M % 2 == 0 and _smooth(M) and M >= need
+    assert not any(m % 2 == 0 and _smooth(m) for m in range(need, M))
+    need = W + 2 * p
+    assert N % 2 == 0 and _smooth(N) and N >= need
+    if 136 < need <= rows[-1]:
+        assert N in rows and not any(need <= r < N for r in rows)
+    else:
+        assert not any(m % 2 == 0 and _smooth(m) for m in range(need, N))
+
+
+def test_row_lengths_are_even_smooth_and_ascending(gfc_lib):
+    rows = gfc.row_lengths()
+    assert rows == sorted(set(rows)) and len(rows) >= 25
+    assert all(r % 2 == 0 and _smooth(r) for r in rows)
+    assert {108, 270, 1250, 1568} <= set(rows) and rows[-1] >= 2048 + 8
+    # consecutive lengths above the policy's lower end are within 15% of each other
+    big = [r for r in rows if r >= 140]
+    assert all(b / a <= 1.15 for a, b in zip(big, big[1:]))
 
 
 def test_padded_sizes_of_the_paper_workloads(gfc_lib):

@@ -44,8 +44,9 @@ def test_pure_python_size_rule_matches_the_library(gfc_lib):
     from paper_1902_00176_gb300 import gfc
 
     for H, W in [(801, 1200), (64, 96), (1024, 1536), (256, 256), (2, 2), (13, 7), (2000, 2000), (2040, 2048),
-                 (127, 1999), (600, 333)]:
+                 (127, 1999), (600, 333), (300, 1000), (40, 129), (40, 128), (9, 2051)]:
         assert bench.padded_size(H, W) == gfc.padded_size(H, W), (H, W)
+    assert tuple(gfc.row_lengths()) == bench.ROW_LENGTHS
 
 
 def test_gpus_flag_relaunches_under_torchrun_outside_a_job():

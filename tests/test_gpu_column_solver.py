@@ -116,3 +116,56 @@ def test_unknown_column_solver_is_rejected():
     o = gfc._Opts(64, 96, 1, 1, 0, 4, 0, 0, None, 0, 7)
     h = ctypes.c_void_p()
     assert gfc.lib().gfc_plan_create_ex(ctypes.byref(h), ctypes.byref(o)) == 1
+
+
+def _torch_fp32_adjoint(gout, M, N, p):
+    """The adjoint in plain PyTorch FP32 (rfft2 / irfft2): the FP32 baseline error."""
+    H, W = gout.shape
+    G = torch.from_numpy(O.green_spectrum(M, N)[:, : N // 2 + 1]).float().to(DEV)
+    z = torch.zeros((M, N), device=DEV)
+    g = torch.from_numpy(np.ascontiguousarray(gout)).float().to(DEV)
+    z[p:p + H, p:p + W] = g
+    z[0, 0] -= g.sum()
+    w = torch.fft.irfft2(torch.fft.rfft2(z) * G, s=(M, N))
+    gx = (w - torch.roll(w, -1, -1))[p:p + H, p:p + W]
+    gy = (w - torch.roll(w, -1, -2))[p:p + H, p:p + W]
+    return gx.double().cpu().numpy(), gy.double().cpu().numpy()
+
+
+def _random_sizes(n=10, seed=9100):
+    rng = np.random.default_rng(seed)
+    return [(int(rng.integers(128, 2049)), int(rng.integers(128, 2049))) for _ in range(n)]
+
+
+@pytest.mark.parametrize("H,W", _random_sizes())
+def test_random_sizes_on_the_row_length_family(H, W, monkeypatch):
+    """Ten seeded sizes in [128, 2048]: the row length comes from the compiled family
+    (register-resident row passes, recursive column solve); the result matches the
+    oracle on the plan's torus and the generic passes on the same torus."""
+    gx, gy = synth.ragged_item_gradients((1, H, W), item=H % 97, seed=9200)
+    tx, ty = _dev(gx[None]), _dev(gy[None])
+    p = gfc.Plan(H, W, 1, 1, device=DEV)
+    assert p.N in gfc.row_lengths()
+    out = _np(p.solve_from_gradient(tx, ty))[0, 0]
+    ref = O.solve_from_gradient(gx[0].astype(np.float64), gy[0].astype(np.float64), p.M, p.N, p.pad)
+    assert _rel(out, ref) <= REL_F32, _rel(out, ref)
+    assert np.abs(out - ref).max() <= MAXABS_F32
+    monkeypatch.setenv("GFC_FORCE_GENERIC", "1")
+    q = gfc.Plan(H, W, 1, 1, device=DEV)
+    monkeypatch.delenv("GFC_FORCE_GENERIC")
+    assert (q.M, q.N) == (p.M, p.N)
+    assert _rel(out, _np(q.solve_from_gradient(tx, ty))[0, 0]) <= 2e-6
+    # the Laplacian entry and the adjoint (generic fallback) on the same plan
+    lap = (gx[0] - np.pad(gx[0], ((0, 0), (1, 0)))[:, :-1]) + (gy[0] - np.pad(gy[0], ((1, 0), (0, 0)))[:-1, :])
+    lo = _np(p.solve_from_laplacian(_dev(lap[None, None])))[0, 0]
+    assert _rel(lo, O.solve_from_laplacian(lap.astype(np.float64), p.M, p.N, p.pad)) <= REL_F32
+    # the adjoint (generic passes) of a gradient-shaped upstream field: its output is
+    # large and dominated by the lowest bins, the FP32 conditioning limit documented
+    # for white inputs; the bar is 3x the error of a plain torch FP32 evaluation
+    bx, by = p.backward(_dev(gx[None]))
+    rx, ry = O.backward(gx[0].astype(np.float64), p.M, p.N, p.pad)
+    tx_, ty_ = _torch_fp32_adjoint(gx[0], p.M, p.N, p.pad)
+    assert _rel(_np(bx)[0, 0], rx) <= max(REL_F32, 3.0 * _rel(tx_, rx))
+    assert _rel(_np(by)[0, 0], ry) <= max(REL_F32, 3.0 * _rel(ty_, ry))
+    p.close()
+    q.close()
