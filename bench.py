@@ -279,6 +279,7 @@ def run_gfc(args, rank, world, local_rank):
     ty = torch.from_numpy(gy).to(dev)
     out = torch.empty_like(tx)
     plan = gfc.Plan(H, W, 1, B, torch.float32, device=dev)
+    tuned = plan.autotune()  # column solver and pipeline split, timed on this GPU
     stream = torch.cuda.current_stream(dev)
 
     def barrier():
@@ -352,6 +353,13 @@ def run_gfc(args, rank, world, local_rank):
     fused = prof["launches"][3] == 0
     pass_bytes = [B * ((8 * fe if fused else z_b) + s_b + band_b), B * 2 * band_b, B * (s_b + band_b + 4 * fe),
                   B * (8 * fe + z_b)]
+    if tuned["column_solver"] == 1:  # column FFTs: column-major spectrum, row-major Y
+        names[0:3] = ["row pass (div + pad + row FFT)", "column pass (FFT, x G, inverse FFT)",
+                      "inverse row pass (FFT, offset, crop)"]
+        spec_b = nh * ld4(plan.M) * 8
+        y_b = H * ld4(nh) * 8
+        pass_bytes = [B * ((8 * fe if fused else z_b) + spec_b), B * (spec_b + y_b) + G_bytes, B * (y_b + 4 * fe),
+                      B * (8 * fe + z_b)]
     per_kernel = []
     for i in range(4):
         if not prof["launches"][i]:
@@ -368,7 +376,8 @@ def run_gfc(args, rank, world, local_rank):
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "batch_per_gpu": B, "H": H, "W": W, "padded": [plan.M, plan.N],
-                   "pad": plan.pad, "chunk_fields": None,
+                   "pad": plan.pad, "chunk_fields": tuned["chunk"], "streams": tuned["streams"],
+                   "column_solver": ["recursive", "fft"][tuned["column_solver"]],
                    "l2": "inputs+outputs 1.15 GB per step exceed the 129 MB L2; no flush needed"},
         "roofline": {"bound": "hbm", "kernel": "solve call (row, column, inverse-row passes)",
                      "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
@@ -577,6 +586,7 @@ def _ragged_workload(dev, samples):
 
     items = synth.ragged_items()
     rp = gfc.RaggedPlan(items, device=dev)
+    tuned = rp.autotune()
     gxr, gyr = rp.empty(), rp.empty()
     for i, ((c, h, w), o) in enumerate(zip(items, rp.offsets)):
         a, b = synth.ragged_item_gradients((c, h, w), i)
@@ -599,7 +609,7 @@ def _ragged_workload(dev, samples):
     nf = sum(c for c, h, w in items)
     peak = _peaks()[0]
     nbytes = sum(12 * c * h * w + 4 * padded_size(h, w)[0] * (padded_size(h, w)[1] // 2 + 1) for c, h, w in items)
-    res = {"fields": nf, "ms": ms, "ms_graph": msg, "solves_per_s": nf * 1000.0 / ms,
+    res = {"fields": nf, "autotuned": tuned, "ms": ms, "ms_graph": msg, "solves_per_s": nf * 1000.0 / ms,
            "ms_sequential_plans": ms_seq, "speedup_vs_sequential": ms_seq / ms, "min_bytes": nbytes,
            "frac_of_hbm": nbytes / (ms / 1000.0) / 1e9 / peak}
     # two items (smallest and largest) for the oracle-error leg

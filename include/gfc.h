@@ -217,6 +217,41 @@ gfc_status gfc_plan_set_profiling(gfc_plan* plan, int enable);
  * clears it afterwards. */
 gfc_status gfc_plan_get_profile(gfc_plan* plan, gfc_profile* out, int reset);
 
+/* ---- Autotuning ----
+ * A plan's results do not depend on how its work is split, only its speed
+ * does. gfc_plan_autotune times the plan's candidate splits on synthetic
+ * inputs (CUDA events on the plan's stream, after warm-up runs) and keeps the
+ * fastest: for uniform plans the column solver (gfc_column_solver, where both
+ * exist) and the pipeline split (one chunk of all fields, or chunks sized for
+ * 32 or 64 MB of L2 on two streams); for ragged plans the number of internal
+ * streams (1, 2, 4, 8) the per-item sub-plans are spread over. The plan handle
+ * stays valid (a uniform plan's internals are replaced by the winner's). With
+ * a cache_path (may be NULL) the choice is looked up first under the plan's
+ * key (gfc_plan_tune_key: the problem, the device and the library build) and
+ * stored after timing, in a text file of "key<TAB>value" lines rewritten
+ * atomically (a temporary file renamed). Synchronous; allocates temporary
+ * device buffers of the plan's input and output size while timing. */
+typedef struct {
+  int column_solver;  /* uniform plans: the chosen gfc_column_solver */
+  int chunk;          /* uniform plans: fields per pipeline chunk */
+  int streams;        /* uniform plans: chunks in flight */
+  int rag_streams;    /* ragged plans: streams of the per-item sub-plans */
+  double ms;          /* the winner's time per solve (0 when read from the cache) */
+  int candidates;     /* candidates timed (0 when read from the cache) */
+  int from_cache;     /* 1 when the choice came from the cache */
+} gfc_tune_result;
+gfc_status gfc_plan_autotune(gfc_plan* plan, const char* cache_path, gfc_tune_result* result);
+
+/* The tuning-cache key of a plan, NUL-terminated in key[capacity]. */
+gfc_status gfc_plan_tune_key(const gfc_plan* plan, char* key, int capacity);
+
+/* The tuning cache itself (host-only): gfc_tune_cache_get copies the value of
+ * the last entry for `key` into value[capacity] and returns 1, returns 0 when
+ * the file or the key is absent, -1 on bad arguments. gfc_tune_cache_put
+ * replaces the entry for `key` (keys and values may hold no tab or newline). */
+int gfc_tune_cache_get(const char* path, const char* key, char* value, int capacity);
+gfc_status gfc_tune_cache_put(const char* path, const char* key, const char* value);
+
 /* Allocation-free solve from gradients, for callers that cannot allocate
  * device memory: plug-ins whose host application owns all device memory,
  * fixed-budget real-time or embedded pipelines, and latency-bound loops where

@@ -8,6 +8,7 @@ from __future__ import annotations
 
 import concurrent.futures as cf
 import glob
+import hashlib
 import os
 import shutil
 import subprocess
@@ -38,17 +39,34 @@ def _newer(target: str, deps) -> bool:
     return all(os.path.getmtime(d) <= t for d in deps)
 
 
+def _write_build_id(srcs, headers) -> str:
+    """_build/gfc_build_id.h: a hash of the CUDA sources and the C header (the
+    tuning cache keys its entries by it); rewritten only when it changes."""
+    h = hashlib.sha256()
+    for p in sorted(srcs + headers):
+        with open(p, "rb") as f:
+            h.update(os.path.basename(p).encode() + b"\0" + f.read())
+    text = f'#pragma once\n#define GFC_BUILD_ID "{h.hexdigest()[:16]}"\n'
+    path = os.path.join(BUILD, "gfc_build_id.h")
+    if not os.path.exists(path) or open(path).read() != text:
+        with open(path, "w") as f:
+            f.write(text)
+    return path
+
+
 def build_library(verbose: bool = False, extra_flags=None, force: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     headers = glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.h")) + \
         glob.glob(os.path.join(ROOT, "include", "*.h"))
-    flags = NVCC_FLAGS + list(extra_flags or [])
+    build_id = _write_build_id(srcs, headers)
+    flags = NVCC_FLAGS + ["-I", BUILD] + list(extra_flags or [])
     nv = nvcc()
 
     def compile_one(src):
         obj = os.path.join(BUILD, os.path.basename(src) + ".o")
-        if not force and _newer(obj, [src] + headers):
+        deps = [src] + headers + ([build_id] if os.path.basename(src) == "tune.cu" else [])
+        if not force and _newer(obj, deps):
             return obj
         cmd = [nv] + ARCH + flags + ["-c", src, "-o", obj]
         if verbose:
@@ -60,7 +78,7 @@ def build_library(verbose: bool = False, extra_flags=None, force: bool = False) 
             print(r.stdout, r.stderr)
         return obj
 
-    with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
+    with cf.ThreadPoolExecutor(max_workers=min(max(os.cpu_count() or 8, 8), len(srcs))) as ex:
         objs = list(ex.map(compile_one, srcs))
     if force or not _newer(LIB, objs):
         tmp = LIB + ".tmp"

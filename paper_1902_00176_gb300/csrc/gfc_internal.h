@@ -47,6 +47,7 @@ struct Bufs {
   float2* tri;     // band sums and carries of the recursive column solve (fast passes)
 };
 constexpr int kMaxSlots = 4;
+constexpr int kMaxRagStreams = 8;  // streams of a ragged plan's per-item sub-plans
 constexpr int kHostBufs = 4;  // most staging buffers of the host-buffer pipeline
 
 // One transform length of an EXACT-size plan (exact.cu).
@@ -126,6 +127,21 @@ struct gfc_plan {
   gfc::FieldDesc* d_desc;    // [nfields] device
   gfc::FftPlan* d_plans;     // [2 * sizes] device: row, column schedule per distinct size
   int maxM, maxN, maxNh, maxH, maxW;
+  // ragged batches on the register-resident passes: one uniform sub-plan per item
+  // (batch 1, the item's C), run on rag_streams internal streams forked from and
+  // joined into the plan's stream; the other items (nfields of them) go through
+  // the generic per-field passes above
+  int nsub;
+  gfc_plan** sub;          // [nsub]
+  long long* sub_off;      // [nsub] element offset of each sub-plan's item in the packed arrays
+  int* sub_stream;         // [nsub] the stream each sub-plan runs on
+  double* sub_work;        // [nsub] the item's size (C H W), for the stream assignment
+  long long rag_total;      // elements of the packed arrays the items span
+  int rag_streams;          // streams created
+  int rag_active;           // streams the sub-plans are spread over (<= rag_streams)
+  cudaStream_t rag_stream[gfc::kMaxRagStreams];
+  cudaEvent_t rag_done[gfc::kMaxRagStreams];
+  cudaEvent_t rag_fork;
   // tracing
   gfc_profile prof;
   bool profiling;
@@ -194,6 +210,9 @@ cudaError_t run_chunk_exact(gfc_plan* P, const Bufs& B, int mode, const void* in
 // per-field squared thresholds of Sec. 3.2.3 into P->edit_t2 (edit.cu): from
 // the fields' largest gradient magnitudes when ref <= 0, else from ref
 gfc_status edit_prepare_threshold(gfc_plan* P, const void* gx, const void* gy, float frac, float ref);
+
+// spread a ragged plan's sub-plans over k internal streams (plan.cu)
+gfc_status ragged_set_streams(gfc_plan* P, int k);
 
 // free the host-buffer pipeline and the profiling event pool (plan teardown)
 void release_host_state(gfc_plan* P);

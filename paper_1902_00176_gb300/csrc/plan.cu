@@ -372,9 +372,11 @@ gfc_status gfc_plan_create_ex(gfc_plan** out, const gfc_plan_opts* o) {
   return GFC_OK;
 }
 
-gfc_status gfc_plan_create_ragged(gfc_plan** out, int n, const gfc_item* items, gfc_dtype dtype) {
-  clear_error();
-  if (!out || !items || n < 1) return fail(GFC_ERR_INVALID_ARG, "gfc_plan_create_ragged: bad arguments (n=%d)", n);
+}  // extern "C"
+
+// The generic part of a ragged plan: per-field descriptors over the given items
+// (n >= 1), pooled tables, chunked scratch.
+static gfc_status create_ragged_generic(gfc_plan** out, int n, const gfc_item* items, gfc_dtype dtype) {
   *out = nullptr;
   if (dtype != GFC_F32 && dtype != GFC_F16 && dtype != GFC_BF16)
     return fail(GFC_ERR_INVALID_ARG, "gfc_plan_create_ragged: unknown dtype %d", (int)dtype);
@@ -501,6 +503,98 @@ gfc_status gfc_plan_create_ragged(gfc_plan** out, int n, const gfc_item* items, 
   return GFC_OK;
 }
 
+// Ragged plans: FP32 items whose padded size has register-resident row passes
+// run as uniform sub-plans (batch 1, the item's C) on internal streams; the
+// others go through the generic per-field passes.
+static gfc_status attach_subplans(gfc_plan* p, const std::vector<int>& fast_items, const gfc_item* items) {
+  const int ns = (int)fast_items.size();
+  p->nsub = 0;
+  if (ns == 0) return GFC_OK;
+  p->sub = (gfc_plan**)calloc((size_t)ns, sizeof(gfc_plan*));
+  p->sub_off = (long long*)calloc((size_t)ns, sizeof(long long));
+  p->sub_stream = (int*)calloc((size_t)ns, sizeof(int));
+  p->sub_work = (double*)calloc((size_t)ns, sizeof(double));
+  if (!p->sub || !p->sub_off || !p->sub_stream || !p->sub_work)
+    return fail(GFC_ERR_ALLOC, "gfc_plan_create_ragged: host allocation failed");
+  for (int j = 0; j < ns; ++j) {
+    const gfc_item& it = items[fast_items[j]];
+    gfc_plan_opts o;
+    memset(&o, 0, sizeof(o));
+    o.H = it.H; o.W = it.W; o.C = it.C; o.batch = 1; o.dtype = GFC_F32; o.pad = 4; o.streams = 1;
+    gfc_status st = gfc_plan_create_ex(&p->sub[j], &o);
+    if (st != GFC_OK) return st;
+    p->nsub = j + 1;
+    p->sub_off[j] = it.offset;
+    p->sub_work[j] = (double)it.C * it.H * it.W;
+  }
+  return ragged_set_streams(p, 4);
+}
+
+extern "C" {
+
+gfc_status gfc_plan_create_ragged(gfc_plan** out, int n, const gfc_item* items, gfc_dtype dtype) {
+  clear_error();
+  if (!out || !items || n < 1) return fail(GFC_ERR_INVALID_ARG, "gfc_plan_create_ragged: bad arguments (n=%d)", n);
+  *out = nullptr;
+  if (dtype != GFC_F32 && dtype != GFC_F16 && dtype != GFC_BF16)
+    return fail(GFC_ERR_INVALID_ARG, "gfc_plan_create_ragged: unknown dtype %d", (int)dtype);
+  std::vector<int> fast_items, generic_items;
+  int maxM = 0, maxN = 0, maxH = 0, maxW = 0;
+  long long nfields = 0, rag_total = 0;
+  for (int i = 0; i < n; ++i) {
+    const gfc_item& it = items[i];
+    if (it.C < 1 || it.offset < 0)
+      return fail(GFC_ERR_INVALID_ARG, "gfc_plan_create_ragged: item %d has C=%d offset=%lld", i, it.C, it.offset);
+    int M, N;
+    gfc_status st = gfc_padded_size(it.H, it.W, 4, GFC_SIZE_SMOOTH, &M, &N);
+    if (st != GFC_OK) return st;
+    maxM = std::max(maxM, M); maxN = std::max(maxN, N); maxH = std::max(maxH, it.H); maxW = std::max(maxW, it.W);
+    nfields += it.C;
+    rag_total = std::max(rag_total, it.offset + (long long)it.C * it.H * it.W);
+    const bool fast = dtype == GFC_F32 && getenv("GFC_FORCE_GENERIC") == nullptr &&
+                      (fast_supported(M, N) || fast_rows_supported(N));
+    if (fast) fast_items.push_back(i);
+    else generic_items.push_back(i);
+  }
+  if (nfields > (1 << 24)) return fail(GFC_ERR_UNSUPPORTED, "gfc_plan_create_ragged: too many fields");
+  gfc_plan* p = nullptr;
+  if (!generic_items.empty()) {
+    const int ng = (int)generic_items.size();
+    gfc_item* gen = (gfc_item*)malloc((size_t)ng * sizeof(gfc_item));
+    if (!gen) return fail(GFC_ERR_ALLOC, "gfc_plan_create_ragged: host allocation failed");
+    for (int i = 0; i < ng; ++i) gen[i] = items[generic_items[i]];
+    gfc_status st = create_ragged_generic(&p, ng, gen, dtype);
+    free(gen);
+    if (st != GFC_OK) return st;
+  } else {
+    p = (gfc_plan*)calloc(1, sizeof(gfc_plan));
+    if (!p) return fail(GFC_ERR_ALLOC, "gfc_plan_create_ragged: host allocation failed");
+    p->ragged = true;
+    p->pad = 4;
+    p->dtype = dtype;
+    p->C = 1;
+    cudaError_t e = cudaGetDevice(&p->device);
+    if (e == cudaSuccess) e = cudaMalloc(&p->dev_err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(p->dev_err, 0, sizeof(int));
+    if (e != cudaSuccess) {
+      gfc_status st = cuda_fail(e, "gfc_plan_create_ragged");
+      destroy_plan(p);
+      return st;
+    }
+  }
+  // the query reports the largest torus over all items
+  p->M = maxM; p->N = maxN; p->Nh = maxN / 2 + 1; p->H = maxH; p->W = maxW;
+  p->rag_total = rag_total;
+  gfc_status st = attach_subplans(p, fast_items, items);
+  if (st != GFC_OK) {
+    destroy_plan(p);
+    return st;
+  }
+  *out = p;
+  return GFC_OK;
+}
+
+
 gfc_status gfc_plan_create(gfc_plan** plan, int H, int W, int C, int batch, gfc_dtype dtype) {
   gfc_plan_opts o;
   memset(&o, 0, sizeof(o));
@@ -535,6 +629,8 @@ gfc_status gfc_plan_copy_green(const gfc_plan* plan, float* host_out) {
 gfc_status gfc_plan_sync(gfc_plan* plan) {
   clear_error();
   if (!plan) return fail(GFC_ERR_INVALID_ARG, "gfc_plan_sync: null plan");
+  for (int j = 0; j < plan->nsub; ++j)
+    if (gfc_status st = gfc_plan_sync(plan->sub[j])) return st;
   GFC_CUDA_TRY(cudaStreamSynchronize(plan->stream));
   int h = 0;
   GFC_CUDA_TRY(cudaMemcpy(&h, plan->dev_err, sizeof(int), cudaMemcpyDeviceToHost));
@@ -547,8 +643,55 @@ gfc_status gfc_plan_sync(gfc_plan* plan) {
 
 }  // extern "C"
 
+// (Re)assign a ragged plan's sub-plans to `k` internal streams: items in
+// decreasing size, each to the stream with the least work so far.
+gfc_status gfc::ragged_set_streams(gfc_plan* p, int k) {
+  if (k < 1) k = 1;
+  if (k > kMaxRagStreams) k = kMaxRagStreams;
+  if (k > p->nsub) k = p->nsub;
+  if (k < 1) k = 1;
+  for (int s = p->rag_streams; s < k; ++s) {  // create the streams this needs beyond those there
+    GFC_CUDA_TRY(cudaStreamCreateWithFlags(&p->rag_stream[s], cudaStreamNonBlocking));
+    GFC_CUDA_TRY(cudaEventCreateWithFlags(&p->rag_done[s], cudaEventDisableTiming));
+  }
+  if (p->rag_streams < k) p->rag_streams = k;
+  if (!p->rag_fork) GFC_CUDA_TRY(cudaEventCreateWithFlags(&p->rag_fork, cudaEventDisableTiming));
+  int* order = (int*)malloc((size_t)p->nsub * sizeof(int));
+  if (!order) return fail(GFC_ERR_ALLOC, "gfc_plan_create_ragged: host allocation failed");
+  for (int j = 0; j < p->nsub; ++j) {  // insertion sort, largest item first (stable)
+    int i = j;
+    while (i > 0 && p->sub_work[order[i - 1]] < p->sub_work[j]) {
+      order[i] = order[i - 1];
+      --i;
+    }
+    order[i] = j;
+  }
+  double load[kMaxRagStreams] = {};
+  for (int i = 0; i < p->nsub; ++i) {
+    const int j = order[i];
+    int best = 0;
+    for (int s2 = 1; s2 < k; ++s2)
+      if (load[s2] < load[best]) best = s2;
+    p->sub_stream[j] = best;
+    load[best] += p->sub_work[j];
+  }
+  free(order);
+  p->rag_active = k;
+  return GFC_OK;
+}
+
 static void destroy_plan(gfc_plan* p) {
   if (!p) return;
+  for (int j = 0; j < p->nsub; ++j) destroy_plan(p->sub[j]);
+  free(p->sub);
+  free(p->sub_off);
+  free(p->sub_stream);
+  free(p->sub_work);
+  for (int s = 0; s < p->rag_streams; ++s) {
+    if (p->rag_stream[s]) cudaStreamDestroy(p->rag_stream[s]);
+    if (p->rag_done[s]) cudaEventDestroy(p->rag_done[s]);
+  }
+  if (p->rag_fork) cudaEventDestroy(p->rag_fork);
   release_host_state(p);
   cudaFree(p->G);
   cudaFree(p->GT);

@@ -651,8 +651,42 @@ static gfc_status run_ragged(gfc_plan* P, const void* a, const void* b, void* o0
 
 template <int MODE>
 static gfc_status dispatch(gfc_plan* P, const void* a, const void* b, void* o0, void* o1,
-                           const EditArgs* ed = nullptr) {
+                           const EditArgs* ed = nullptr);
+
+// A ragged plan's sub-plans (one per item on the register-resident passes), each
+// on its internal stream, forked from and joined into the plan's stream; the
+// generic part runs on the plan's stream meanwhile.
+template <int MODE>
+static gfc_status run_ragged_subplans(gfc_plan* P, const void* a, const void* b, void* o0, void* o1) {
+  const size_t es = dtype_size(P->dtype);
+  auto at = [&](const void* base, long long off) -> const void* {
+    return base ? static_cast<const char*>(base) + off * (long long)es : nullptr;
+  };
+  GFC_CUDA_TRY(cudaEventRecord(P->rag_fork, P->stream));
+  for (int s = 0; s < P->rag_active; ++s) GFC_CUDA_TRY(cudaStreamWaitEvent(P->rag_stream[s], P->rag_fork, 0));
+  for (int j = 0; j < P->nsub; ++j) {
+    gfc_plan* Q = P->sub[j];
+    Q->stream = P->rag_stream[P->sub_stream[j]];
+    const long long off = P->sub_off[j];
+    gfc_status st = dispatch<MODE>(Q, at(a, off), at(b, off), const_cast<void*>(at(o0, off)),
+                                   const_cast<void*>(at(o1, off)));
+    if (st != GFC_OK) return st;
+  }
+  for (int s = 0; s < P->rag_active; ++s) {
+    GFC_CUDA_TRY(cudaEventRecord(P->rag_done[s], P->rag_stream[s]));
+    GFC_CUDA_TRY(cudaStreamWaitEvent(P->stream, P->rag_done[s], 0));
+  }
+  return GFC_OK;
+}
+
+template <int MODE>
+static gfc_status dispatch(gfc_plan* P, const void* a, const void* b, void* o0, void* o1, const EditArgs* ed) {
   if (P->ragged) {
+    if (P->nsub) {
+      P->prof.calls += 1;
+      if (gfc_status st = run_ragged_subplans<MODE>(P, a, b, o0, o1)) return st;
+      if (P->nfields == 0) return GFC_OK;
+    }
     switch (P->dtype) {
       case GFC_F32: return run_ragged<float, MODE>(P, a, b, o0, o1);
       case GFC_F16: return run_ragged<__half, MODE>(P, a, b, o0, o1);

@@ -54,6 +54,16 @@ class _Edit(ctypes.Structure):
 EDIT_KINDS = {"none": 0, "threshold": 1, "merge": 2}
 
 
+class TuneResult(ctypes.Structure):
+    """Mirror of gfc_tune_result."""
+    _fields_ = [("column_solver", ctypes.c_int), ("chunk", ctypes.c_int), ("streams", ctypes.c_int),
+                ("rag_streams", ctypes.c_int), ("ms", ctypes.c_double), ("candidates", ctypes.c_int),
+                ("from_cache", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class Profile(ctypes.Structure):
     """Mirror of gfc_profile: per-pass device time (ms) and launch counts."""
     _fields_ = [("pass_ms", ctypes.c_double * 4), ("launches", ctypes.c_long * 4), ("calls", ctypes.c_long),
@@ -106,6 +116,10 @@ _SIGNATURES = {
     "gfc_plan_selftest_wait": [ctypes.c_void_p, ctypes.c_int],
     "gfc_plan_sync": [ctypes.c_void_p],
     "gfc_destroy": [ctypes.c_void_p],
+    "gfc_plan_autotune": [ctypes.c_void_p, ctypes.c_char_p, ctypes.POINTER(TuneResult)],
+    "gfc_plan_tune_key": [ctypes.c_void_p, ctypes.c_char_p, ctypes.c_int],
+    "gfc_tune_cache_get": [ctypes.c_char_p, ctypes.c_char_p, ctypes.c_char_p, ctypes.c_int],
+    "gfc_tune_cache_put": [ctypes.c_char_p, ctypes.c_char_p, ctypes.c_char_p],
     "gfc_last_error": [],
     "gfc_status_string": [ctypes.c_int],
 }
@@ -146,6 +160,33 @@ def row_lengths():
     buf = (ctypes.c_int * n)()
     lib().gfc_row_lengths(buf, n)
     return list(buf)
+
+
+def tune_cache_get(path: str, key: str):
+    """The cached tuning value for ``key`` in the cache file, or None."""
+    buf = ctypes.create_string_buffer(512)
+    r = lib().gfc_tune_cache_get(path.encode(), key.encode(), buf, len(buf))
+    if r < 0:
+        raise GFCError(1, lib().gfc_last_error().decode(errors="replace"))
+    return buf.value.decode() if r == 1 else None
+
+
+def tune_cache_put(path: str, key: str, value: str):
+    _check(lib().gfc_tune_cache_put(path.encode(), key.encode(), value.encode()))
+
+
+def _autotune(handle, device, bind, cache):
+    r = TuneResult()
+    bind()
+    with torch.cuda.device(device):
+        _check(lib().gfc_plan_autotune(handle, cache.encode() if cache else None, ctypes.byref(r)))
+    return r.as_dict()
+
+
+def _tune_key(handle):
+    buf = ctypes.create_string_buffer(1024)
+    _check(lib().gfc_plan_tune_key(handle, buf, len(buf)))
+    return buf.value.decode()
 
 
 def _stream_ptr(device) -> int:
@@ -364,6 +405,14 @@ class Plan:
         _check(lib().gfc_plan_get_profile(self._h, ctypes.byref(pr), 1 if reset else 0))
         return pr.as_dict()
 
+    def autotune(self, cache=None) -> dict:
+        """Time the plan's candidate splits and keep the fastest (gfc_plan_autotune);
+        ``cache`` is an optional path of the tuning cache file."""
+        return _autotune(self._h, self.device, self._bind_stream, cache)
+
+    def tune_key(self) -> str:
+        return _tune_key(self._h)
+
     def green(self):
         """The plan's FP32 Green spectrum, M x (N/2+1), as a CPU tensor (1/(MN) folded in)."""
         g = torch.empty((self.M, self.N // 2 + 1), dtype=torch.float32)
@@ -513,6 +562,13 @@ class RaggedPlan:
 
     def unpack(self, flat):
         return [flat[o:o + C * H * W].view(C, H, W) for (C, H, W), o in zip(self.items, self.offsets)]
+
+    def autotune(self, cache=None) -> dict:
+        """Time 1, 2, 4 and 8 internal streams for the per-item sub-plans and keep the fastest."""
+        return _autotune(self._h, self.device, self._bind_stream, cache)
+
+    def tune_key(self) -> str:
+        return _tune_key(self._h)
 
     def _check_flat(self, t, name):
         if not t.is_cuda or t.device != self.device or t.dtype != self.dtype or t.numel() != self.total \
