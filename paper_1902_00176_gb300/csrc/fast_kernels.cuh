@@ -884,6 +884,7 @@ static __global__ void __launch_bounds__(32) k_adj_total(double* __restrict__ pa
 // ---------------------------------------------------------------------------
 constexpr int kTriMaxM = 2112;  // column 0 of the longest supported column
 constexpr int kTriSeg = kTriSegments;  // band segments (warps) per sweep block
+constexpr int kTriTileMaxG = 160;      // bands whose sums a sweep block stages (80 KB)
 
 __device__ __forceinline__ double warp_sum_d(double v) {
 #pragma unroll
@@ -947,12 +948,15 @@ static __global__ void __launch_bounds__(32 * (kTriSeg + 1)) k_tri_carries(float
   __shared__ float2 y0s[kTriCols];
   __shared__ float yls[2 * kTriCols];
   __shared__ __align__(16) float fcol[kTriMaxM + 4];  // block 0: column 0 of S (compact copy)
-  __shared__ __align__(8) uint64_t bar;
+  __shared__ __align__(8) uint64_t bar, tbar;
+  extern __shared__ __align__(16) float2 tile[];  // the block's band sums when they fit (staged)
   const int kb = blockIdx.x, field = blockIdx.y, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int k = kb * kTriCols + lane;
   const bool col_ok = k >= 1 && k < A.Nh;
-  const float2* sums = tri_sums(tri, field, A) + (size_t)kb * 2 * A.G * kTriCols + lane;  // [g][2][32]
-  float2* carry = tri + (size_t)field * A.tri_field + k;                                 // [g][2][ldY]
+  const float2* gsums = tri_sums(tri, field, A) + (size_t)kb * 2 * A.G * kTriCols;  // [g][2][32], contiguous
+  const bool staged = A.G <= kTriTileMaxG;
+  const float2* sums = (staged ? tile : gsums) + lane;
+  float2* carry = tri + (size_t)field * A.tri_field + k;  // [g][2][ldY]
   // column 0's compact copy for block 0's extra warp, in flight during the sweeps
   const int nr = min(A.srows, A.M - A.p);
   const unsigned cbytes = (unsigned)((nr * sizeof(float) + 15) & ~(size_t)15);
@@ -960,6 +964,20 @@ static __global__ void __launch_bounds__(32 * (kTriSeg + 1)) k_tri_carries(float
     mbar_init(&bar, 1);
     mbar_expect_tx(&bar, cbytes);
     bulk_copy(fcol + A.p, tri_col0(tri, field, A), cbytes, &bar);
+  }
+  if (staged) {  // the whole tile of band sums by one bulk copy
+    if (tid == 0) {
+      mbar_init(&tbar, 1);
+      bulk_load(tile, gsums, (unsigned)(2 * A.G * kTriCols * sizeof(float2)), &tbar);
+    }
+    __syncthreads();
+    const bool landed = mbar_wait(&tbar, 0);
+    if (__syncthreads_or(!landed)) {  // the copy never completed: report, let it drain, stop
+      if (tid == 0) atomicExch(A.err, kErrBulkWait);
+      mbar_wait(&tbar, 0);
+      if (kb == 0 && tid == 32 * kTriSeg) mbar_wait(&bar, 0);
+      return;
+    }
   }
   float4 c03 = make_float4(0.0f, 0.0f, 0.0f, 0.0f), c47 = c03;
   if (col_ok) {
@@ -1734,6 +1752,10 @@ static cudaError_t run_fast_mode(gfc_plan* P, const Bufs& bf, const T* in0, cons
           return e;
       }
       if constexpr (MODE != 2) {
+        int unused_k = 0;
+        if ((e = fast_setup(k_tri_carries, 32 * (kTriSeg + 1), (size_t)2 * kTriTileMaxG * kTriCols * sizeof(float2),
+                            &unused_k)) != cudaSuccess)
+          return e;
         if ((e = fast_setup(k_fast_rows_inv<RS, T, true, false>, RS::THREADS, RS::smem_bytes_tri_inv(), &slots_tc)) !=
             cudaSuccess)
           return e;
@@ -1816,8 +1838,9 @@ static cudaError_t run_fast_mode(gfc_plan* P, const Bufs& bf, const T* in0, cons
   prof_begin(P, 1, st);
   const int nkb = (P->Nh + kTriCols - 1) / kTriCols;  // column blocks of the sweep (u[0,0] partials)
   if (tri) {
-    k_tri_carries<<<dim3(nkb, nf), 32 * (kTriSeg + 1), 0, st>>>(bf.spec, bf.tri, P->colcoef, P->powc,
-                                                                 reinterpret_cast<double*>(bf.partial), A);
+    const size_t tsm = A.G <= kTriTileMaxG ? (size_t)2 * A.G * kTriCols * sizeof(float2) : 0;
+    k_tri_carries<<<dim3(nkb, nf), 32 * (kTriSeg + 1), tsm, st>>>(bf.spec, bf.tri, P->colcoef, P->powc,
+                                                                   reinterpret_cast<double*>(bf.partial), A);
   } else if constexpr (kCols) {
     if (MODE == 2) {
       k_adj_total<<<nf, 32, 0, st>>>(reinterpret_cast<double*>(bf.partial), A.zpairs);
