@@ -222,8 +222,10 @@ gfc_status gfc_plan_get_profile(gfc_plan* plan, gfc_profile* out, int reset);
  * does. gfc_plan_autotune times the plan's candidate splits on synthetic
  * inputs (CUDA events on the plan's stream, after warm-up runs) and keeps the
  * fastest: for uniform plans the column solver (gfc_column_solver, where both
- * exist) and the pipeline split (one chunk of all fields, or chunks sized for
- * 32 or 64 MB of L2 on two streams); for ragged plans the number of internal
+ * exist) and the pipeline split (one chunk of all fields, or on two streams
+ * chunks whose hand-off scratch fits 32 or 64 MB of L2, halves or quarters of
+ * the batch, thirds on three streams, quarters on four); for ragged plans the
+ * number of internal
  * streams (1, 2, 4, 8) the per-item sub-plans are spread over. The plan handle
  * stays valid (a uniform plan's internals are replaced by the winner's). With
  * a cache_path (may be NULL) the choice is looked up first under the plan's

@@ -95,7 +95,7 @@ __device__ __forceinline__ float* tri_col0(float2* tri, int field, const FastArg
 // one step of y <- x + a y with a = 1 - delta, as (x + y) - delta y: delta is
 // held to full relative precision, so the pole near DC is not rounded away
 __device__ __forceinline__ float2 tri_step(float2 x, float2 y, float delta) {
-  return make_float2(fmaf(-delta, y.x, x.x + y.x), fmaf(-delta, y.y, x.y + y.y));
+  return __ffma2_rn(make_float2(-delta, -delta), y, cadd(x, y));  // packed pair arithmetic
 }
 
 __device__ __forceinline__ float f_to_f(float x) { return x; }
@@ -440,9 +440,12 @@ __device__ __forceinline__ void tri_store_item(const float2* buf2, float2* __res
     float2 x[RW];
 #pragma unroll
     for (int q = 0; q < S::F; ++q) {
+      // X_a = (Z[k] + conj Z[N-k]) / 2, X_b = -i (Z[k] - conj Z[N-k]) / 2, in packed pair arithmetic
       const float2 zk = buf2[q * S::NO + k], zm = buf2[q * S::NO + km];
-      x[2 * q] = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
-      x[2 * q + 1] = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
+      const float2 zc = make_float2(zm.x, -zm.y);
+      x[2 * q] = cscale(cadd(zk, zc), 0.5f);
+      const float2 d = csub(zk, zc);
+      x[2 * q + 1] = cscale(make_float2(d.y, -d.x), 0.5f);
     }
 #pragma unroll
     for (int r = 0; r < RW; ++r) Sr[(size_t)r * A.ldY + k] = x[r];
@@ -995,13 +998,13 @@ static __global__ void __launch_bounds__(32 * (kTriSeg + 1)) k_tri_carries(float
       for (int g = g0; g < g1; ++g) {
         const float T = (g == A.G - 1) ? Tl : Tb;
         const float2 e = sums[(size_t)g * 2 * kTriCols];
-        t = make_float2(fmaf(T, t.x, e.x), fmaf(T, t.y, e.y));
+        t = __ffma2_rn(make_float2(T, T), t, e);
       }
 #pragma unroll 4
       for (int g = g1 - 1; g >= g0; --g) {
         const float T = (g == A.G - 1) ? Tl : Tb;
         const float2 e = sums[(size_t)g * 2 * kTriCols + kTriCols];
-        q = make_float2(fmaf(T, q.x, e.x), fmaf(T, q.y, e.y));
+        q = __ffma2_rn(make_float2(T, T), q, e);
       }
     }
     seg_e[warp][lane] = t;
@@ -1066,7 +1069,7 @@ static __global__ void __launch_bounds__(32 * (kTriSeg + 1)) k_tri_carries(float
       const float T = (g == A.G - 1) ? Tl : Tb;
       const float2 e = sums[(size_t)g * 2 * kTriCols];
       carry[(size_t)(2 * g) * A.ldY] = c;
-      c = make_float2(fmaf(T, c.x, e.x), fmaf(T, c.y, e.y));
+      c = __ffma2_rn(make_float2(T, T), c, e);
     }
     float2 q = seg_q[warp][lane];
 #pragma unroll 4
@@ -1074,7 +1077,7 @@ static __global__ void __launch_bounds__(32 * (kTriSeg + 1)) k_tri_carries(float
       const float T = (g == A.G - 1) ? Tl : Tb;
       const float2 e = sums[(size_t)g * 2 * kTriCols + kTriCols];
       carry[(size_t)(2 * g + 1) * A.ldY] = q;
-      q = make_float2(fmaf(T, q.x, e.x), fmaf(T, q.y, e.y));
+      q = __ffma2_rn(make_float2(T, T), q, e);
     }
   }
   if (warp == 0) {
@@ -1269,8 +1272,9 @@ __device__ __forceinline__ void tri_solve_band(float2* buf, const float2* cbuf, 
         ya0 = tri_step(make_float2(x[r].x, x[r].y), ya0, dl0);
         ya1 = tri_step(make_float2(x[r].z, x[r].w), ya1, dl1);
         const float4 y = col[(size_t)r * (S::LDY / 2)];
-        float4 u = make_float4(C0 * ((y.x + ya0.x) - x[r].x), C0 * ((y.y + ya0.y) - x[r].y),
-                               C1 * ((y.z + ya1.x) - x[r].z), C1 * ((y.w + ya1.y) - x[r].w));
+        const float2 u0 = cscale(csub(cadd(make_float2(y.x, y.y), ya0), make_float2(x[r].x, x[r].y)), C0);
+        const float2 u1 = cscale(csub(cadd(make_float2(y.z, y.w), ya1), make_float2(x[r].z, x[r].w)), C1);
+        float4 u = make_float4(u0.x, u0.y, u1.x, u1.y);
         if (!v0) {  // column 0 keeps its exact solution
           u.x = x[r].x;
           u.y = x[r].y;

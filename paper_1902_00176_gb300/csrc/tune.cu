@@ -246,20 +246,30 @@ gfc_status gfc_plan_autotune(gfc_plan* plan, const char* cache_path, gfc_tune_re
   base.pad = plan->pad; base.size_policy = plan->exact ? GFC_SIZE_EXACT : GFC_SIZE_SMOOTH;
   base.stream = plan->stream; base.streams = 1;
   base.column_solver = plan->tri ? GFC_COLUMN_RECURSIVE : GFC_COLUMN_FFT;
-  gfc_plan_opts cand[8];  // (a plain array: the options type is an unnamed struct)
+  gfc_plan_opts cand[14];  // (a plain array: the options type is an unnamed struct)
   int ncand = 0;
   const long fields = (long)plan->batch * plan->C;
-  const size_t per_field = (size_t)plan->spec_field * sizeof(float2) + (plan->zbuf_field + plan->tri_field) * sizeof(float2);
+  // scratch the passes hand off per field (the packed rows only when pass L runs)
+  const size_t per_field = ((size_t)plan->spec_field + plan->tri_field) * sizeof(float2);
   const int nsolvers = plan->fast_cols ? 2 : 1;
   for (int si = 0; si < nsolvers; ++si) {
     gfc_plan_opts o = base;
     o.column_solver = si == 0 ? GFC_COLUMN_RECURSIVE : GFC_COLUMN_FFT;
     cand[ncand++] = o;  // one chunk
-    for (size_t mb : {32, 64}) {  // chunks whose scratch fits that many MB of L2, two streams
-      const long c = (long)(((size_t)mb << 20) / (per_field ? per_field : 1));
-      if (c >= 1 && c < fields) {
+    // chunks whose scratch fits 32 or 64 MB of L2, and halves and quarters of
+    // the batch, two streams (one chunk's carry sweep and inverse pass can
+    // overlap the next chunk's row pass)
+    const long cs[6] = {(long)(((size_t)32 << 20) / (per_field ? per_field : 1)),
+                        (long)(((size_t)64 << 20) / (per_field ? per_field : 1)), (fields + 1) / 2, (fields + 3) / 4,
+                        (fields + 2) / 3, (fields + 3) / 4};
+    const int ss[6] = {2, 2, 2, 2, 3, 4};  // streams of each split
+    for (int i = 0; i < 6 && ncand < 12; ++i) {
+      const long c = cs[i];
+      bool dup = false;
+      for (int j = 0; j < i; ++j) dup = dup || (cs[j] == c && ss[j] == ss[i]);
+      if (c >= 1 && c < fields && !dup) {
         o.chunk = (int)c;
-        o.streams = 2;
+        o.streams = ss[i];
         cand[ncand++] = o;
         o.chunk = 0;
         o.streams = 1;
