@@ -278,8 +278,14 @@ def run_gfc(args, rank, world, local_rank):
     tx = torch.from_numpy(gx).to(dev)
     ty = torch.from_numpy(gy).to(dev)
     out = torch.empty_like(tx)
-    plan = gfc.Plan(H, W, 1, B, torch.float32, device=dev)
-    tuned = plan.autotune()  # column solver and pipeline split, timed on this GPU
+    if args.split is None:
+        plan = gfc.Plan(H, W, 1, B, torch.float32, device=dev)
+        tuned = plan.autotune()  # column solver, pipeline split and grids, timed on this GPU
+    else:  # a fixed split (ncu captures: no tuning launches before the captured ones)
+        solver, chunk, streams, block_items = parse_split(args.split)
+        plan = gfc.Plan(H, W, 1, B, torch.float32, device=dev, chunk=chunk, streams=streams,
+                        column_fft=solver == 1, block_items=block_items == 1)
+        tuned = {"column_solver": solver, "chunk": chunk, "streams": streams, "block_items": block_items}
     stream = torch.cuda.current_stream(dev)
 
     def barrier():
@@ -365,10 +371,12 @@ def run_gfc(args, rank, world, local_rank):
         if not prof["launches"][i]:
             continue
         ms1 = prof["pass_ms"][i] / prof["launches"][i]
-        gbs = pass_bytes[i] / (ms1 / 1000.0) / 1e9
+        # pass_bytes is per step of B fields; a launch covers one chunk of them
+        launch_bytes = pass_bytes[i] * prof_steps / prof["launches"][i]
+        gbs = launch_bytes / (ms1 / 1000.0) / 1e9
         per_kernel.append({"kernel": names[i], "launches_per_step": prof["launches"][i] / prof_steps,
                            "ms_per_step": prof["pass_ms"][i] / prof_steps, "share": prof["pass_ms"][i] / tot_ms,
-                           "ms_per_launch": ms1, "algorithmic_bytes_per_launch": pass_bytes[i], "gb_per_s": gbs,
+                           "ms_per_launch": ms1, "algorithmic_bytes_per_launch": launch_bytes, "gb_per_s": gbs,
                            "frac": gbs / peak})
     traffic = stored_traffic()
     line = {
@@ -378,6 +386,7 @@ def run_gfc(args, rank, world, local_rank):
         "config": {"workload": WORKLOAD, "batch_per_gpu": B, "H": H, "W": W, "padded": [plan.M, plan.N],
                    "pad": plan.pad, "chunk_fields": tuned["chunk"], "streams": tuned["streams"],
                    "column_solver": ["recursive", "fft"][tuned["column_solver"]],
+                   "grids": ["persistent", "block_per_item"][tuned["block_items"]],
                    "l2": "inputs+outputs 1.15 GB per step exceed the 129 MB L2; no flush needed"},
         "roofline": {"bound": "hbm", "kernel": "solve call (row, column, inverse-row passes)",
                      "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
@@ -385,6 +394,9 @@ def run_gfc(args, rank, world, local_rank):
                      "per_kernel": per_kernel,
                      "per_kernel_note": f"per-pass times from a separate run of {prof_steps} steps with CUDA "
                                         "events around every launch; the headline is timed without them"},
+        "roofline_issue": issue_roofline(
+            stored_record(os.path.join(ROOT, "profiles", "issue_solve_801x1200.txt"), ISSUE_KEYS)
+            if tuned["column_solver"] == 0 else None, B, ms_step, clocks),
         "e2e": e2e,
         "gpu_launches": int(round(launches_per_step * args.steps)),
         "clocks": clocks,
@@ -793,19 +805,63 @@ def _edit_workload(dev, samples):
     return res
 
 
-def stored_traffic(path=None):
-    """DRAM bytes per step from the committed ncu capture, or None when the CUDA
-    sources have changed since it was taken (or the record is missing)."""
-    path = path or os.path.join(ROOT, "profiles", "traffic_solve_801x1200_b100.txt")
+def parse_split(text):
+    """``solver:chunk:streams:block_items`` (solver 0 = recursive, 1 = column FFTs) as
+    the autotuner reports it, e.g. ``0:50:2:0``."""
+    parts = [int(v) for v in text.split(":")]
+    if len(parts) != 4 or parts[0] not in (0, 1) or parts[1] < 0 or parts[2] < 0 or parts[3] not in (0, 1):
+        raise ValueError(f"--split wants solver:chunk:streams:block_items, got {text!r}")
+    return tuple(parts)
+
+
+def stored_record(path, keys):
+    """The named numbers of a committed ncu record (``key: value`` lines), or None
+    when the CUDA sources have changed since it was taken, or the record is missing
+    or lacks one of ``keys``."""
     if not os.path.exists(path):
         return None
     try:
         kv = dict(ln.split(":", 1) for ln in open(path).read().splitlines() if ":" in ln and not ln.startswith("#"))
         if kv.get("kernel_build", "").strip() != _kernel_build_id():
             return None
-        return float(kv["dram_bytes_per_step"])
+        return {k: float(kv[k]) for k in keys}
     except (KeyError, ValueError):
         return None
+
+
+def stored_traffic(path=None):
+    """DRAM bytes per step from the committed ncu capture, or None when the CUDA
+    sources have changed since it was taken (or the record is missing)."""
+    rec = stored_record(path or os.path.join(ROOT, "profiles", "traffic_solve_801x1200_b100.txt"),
+                        ["dram_bytes_per_step"])
+    return None if rec is None else rec["dram_bytes_per_step"]
+
+
+ISSUE_KEYS = ["warp_inst_per_field_a", "warp_inst_per_field_sweep", "warp_inst_per_field_c",
+              "fp32_lane_ops_per_field_a", "fp32_lane_ops_per_field_sweep", "fp32_lane_ops_per_field_c"]
+
+
+def issue_roofline(rec, fields, ms_step, clocks, sms=152):
+    """The solve's instruction issue against the SMs' issue limit: each of the 4
+    schedulers of an SM issues at most one warp instruction per clock, so the
+    peak is SMs x 4 x the SM clock sampled under load (the maximum clock when no
+    sample was taken). ``rec`` holds ncu's per-field counts of the three passes."""
+    if rec is None or ms_step <= 0:
+        return None
+    mhz = (clocks or {}).get("sm_mhz") or 2070.0
+    inst = fields * (rec["warp_inst_per_field_a"] + rec["warp_inst_per_field_sweep"] + rec["warp_inst_per_field_c"])
+    lane = fields * (rec["fp32_lane_ops_per_field_a"] + rec["fp32_lane_ops_per_field_sweep"]
+                     + rec["fp32_lane_ops_per_field_c"])
+    peak = sms * 4 * mhz * 1e6 / 1e12  # tera warp instructions per second
+    achieved = inst / (ms_step / 1000.0) / 1e12
+    fp32_peak = sms * 128 * mhz * 1e6 / 1e12  # FP32 lanes: 128 per SM per clock
+    fp32 = lane / (ms_step / 1000.0) / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "T warp-inst/s", "frac": achieved / peak,
+            "sm_mhz": mhz, "warp_inst_per_step": inst,
+            "fp32": {"achieved": fp32, "peak": fp32_peak, "unit": "T lane-ops/s", "frac": fp32 / fp32_peak,
+                     "lane_ops_per_step": lane},
+            "note": "per-field counts from the committed ncu record of the same CUDA sources; peak from "
+                    "152 SMs x 4 issue slots (x 128 FP32 lanes) per clock at the sampled SM clock"}
 
 
 def _kernel_build_id() -> str:
@@ -831,6 +887,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--batch", type=int, default=100, help="fields per GPU (lower only for ncu captures)")
     ap.add_argument("--no-extra", action="store_true", help="skip the other workload shapes")
+    ap.add_argument("--split", default=None,
+                    help="solver:chunk:streams:block_items instead of autotuning (for ncu captures)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

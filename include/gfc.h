@@ -98,6 +98,9 @@ typedef struct {
   int streams;       /* chunks in flight at once (1..4), each on an internal stream
                         forked from and joined back into the plan's stream; 0 = auto */
   int column_solver; /* gfc_column_solver (register-resident sizes only) */
+  int block_items;   /* register-resident passes: 0 = persistent grids (as many blocks as fit,
+                        each looping over items), 1 = one block per item (blocks of passes
+                        on other streams interleave as soon as blocks retire) */
 } gfc_plan_opts;
 
 /* One item of a ragged batch: C fields of H x W, stored contiguously
@@ -224,8 +227,9 @@ gfc_status gfc_plan_get_profile(gfc_plan* plan, gfc_profile* out, int reset);
  * fastest: for uniform plans the column solver (gfc_column_solver, where both
  * exist) and the pipeline split (one chunk of all fields, or on two streams
  * chunks whose hand-off scratch fits 32 or 64 MB of L2, halves or quarters of
- * the batch, thirds on three streams, quarters on four); for ragged plans the
- * number of internal
+ * the batch, thirds on three streams, quarters on four) x the grids
+ * (persistent, or one block per item, gfc_plan_opts.block_items); for ragged
+ * plans the number of internal
  * streams (1, 2, 4, 8) the per-item sub-plans are spread over. The plan handle
  * stays valid (a uniform plan's internals are replaced by the winner's). With
  * a cache_path (may be NULL) the choice is looked up first under the plan's
@@ -235,6 +239,7 @@ gfc_status gfc_plan_get_profile(gfc_plan* plan, gfc_profile* out, int reset);
  * device buffers of the plan's input and output size while timing. */
 typedef struct {
   int column_solver;  /* uniform plans: the chosen gfc_column_solver */
+  int block_items;    /* uniform plans: the chosen gfc_plan_opts.block_items */
   int chunk;          /* uniform plans: fields per pipeline chunk */
   int streams;        /* uniform plans: chunks in flight */
   int rag_streams;    /* ragged plans: streams of the per-item sub-plans */

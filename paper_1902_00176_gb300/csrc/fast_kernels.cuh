@@ -1780,7 +1780,9 @@ static cudaError_t run_fast_mode(gfc_plan* P, const Bufs& bf, const T* in0, cons
       ready = true;
     }
   }
-  auto grid_for = [](long items, int slots) { return (int)(items < slots ? items : slots); };
+  // persistent grids (as many blocks as fit, each looping over items), or one block per item
+  const bool one = P->block_items;
+  auto grid_for = [one](long items, int slots) { return (int)((one || items < slots) ? items : slots); };
   // Plain gradient solves fold pass L into the row pass, and the adjoint folds
   // its packing of grad_out (with the row-pair sums) into it, when the rows can
   // be bulk-copied and their staging fits the exchange buffers.

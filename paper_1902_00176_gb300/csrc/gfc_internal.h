@@ -83,6 +83,7 @@ struct gfc_plan {
   bool fast;  // the row length has register-resident passes (fast_kernels.cuh)
   bool fast_cols;  // ... and the column length has them too (column FFT path, adjoint)
   bool tri;   // fast passes with the column direction by recursive filters (gfc_column_solver)
+  bool block_items;  // fast passes launch one block per item (else persistent grids)
   int triG;   // bands of the recursive column solve (pass A's items)
   size_t tri_field;  // complex elements per field of the band scratch
   float* colcoef;    // [Nh][8] column coefficients of the recursive solve

@@ -284,6 +284,7 @@ gfc_status gfc_plan_create_ex(gfc_plan** out, const gfc_plan_opts* o) {
                          o->column_solver == GFC_COLUMN_RECURSIVE;
   p->fast = p->fast_cols || rows_only;
   p->tri = p->fast && o->column_solver == GFC_COLUMN_RECURSIVE;
+  p->block_items = o->block_items != 0;
   if (p->tri) {
     const int F = fast_row_items(M, N);
     p->triG = (((o->H + 2) / 2) + F - 1) / F;

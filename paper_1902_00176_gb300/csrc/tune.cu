@@ -246,7 +246,8 @@ gfc_status gfc_plan_autotune(gfc_plan* plan, const char* cache_path, gfc_tune_re
   base.pad = plan->pad; base.size_policy = plan->exact ? GFC_SIZE_EXACT : GFC_SIZE_SMOOTH;
   base.stream = plan->stream; base.streams = 1;
   base.column_solver = plan->tri ? GFC_COLUMN_RECURSIVE : GFC_COLUMN_FFT;
-  gfc_plan_opts cand[14];  // (a plain array: the options type is an unnamed struct)
+  base.block_items = 0;
+  gfc_plan_opts cand[24];  // (a plain array: the options type is an unnamed struct)
   int ncand = 0;
   const long fields = (long)plan->batch * plan->C;
   // scratch the passes hand off per field (the packed rows only when pass L runs)
@@ -263,7 +264,7 @@ gfc_status gfc_plan_autotune(gfc_plan* plan, const char* cache_path, gfc_tune_re
                         (long)(((size_t)64 << 20) / (per_field ? per_field : 1)), (fields + 1) / 2, (fields + 3) / 4,
                         (fields + 2) / 3, (fields + 3) / 4};
     const int ss[6] = {2, 2, 2, 2, 3, 4};  // streams of each split
-    for (int i = 0; i < 6 && ncand < 12; ++i) {
+    for (int i = 0; i < 6 && ncand < 22; ++i) {
       const long c = cs[i];
       bool dup = false;
       for (int j = 0; j < i; ++j) dup = dup || (cs[j] == c && ss[j] == ss[i]);
@@ -271,15 +272,26 @@ gfc_status gfc_plan_autotune(gfc_plan* plan, const char* cache_path, gfc_tune_re
         o.chunk = (int)c;
         o.streams = ss[i];
         cand[ncand++] = o;
+        if (si == 0 && plan->fast) {  // the same split with one block per item
+          o.block_items = 1;
+          cand[ncand++] = o;
+          o.block_items = 0;
+        }
         o.chunk = 0;
         o.streams = 1;
       }
+    }
+    if (si == 0 && plan->fast && ncand < 24) {  // one chunk, one block per item
+      o.block_items = 1;
+      cand[ncand++] = o;
+      o.block_items = 0;
     }
   }
   gfc_plan_opts best = base;
   double best_ms = 0.0;
   int n = 0;
-  if (hit && sscanf(cached, "column_solver=%d chunk=%d streams=%d", &best.column_solver, &best.chunk, &best.streams) == 3) {
+  if (hit && sscanf(cached, "column_solver=%d chunk=%d streams=%d block_items=%d", &best.column_solver, &best.chunk,
+                    &best.streams, &best.block_items) == 4) {
     r.from_cache = 1;
   } else {
     TuneBufs t;
@@ -308,13 +320,15 @@ gfc_status gfc_plan_autotune(gfc_plan* plan, const char* cache_path, gfc_tune_re
   *w = tmp;
   gfc_destroy(w);
   r.column_solver = best.column_solver;
+  r.block_items = best.block_items;
   r.chunk = plan->chunk;
   r.streams = plan->nslots;
   r.ms = best_ms;
   r.candidates = n;
   if (cache_path && !r.from_cache && n > 0) {
     char v[96];
-    snprintf(v, sizeof v, "column_solver=%d chunk=%d streams=%d", best.column_solver, best.chunk, best.streams);
+    snprintf(v, sizeof v, "column_solver=%d chunk=%d streams=%d block_items=%d", best.column_solver, best.chunk,
+             best.streams, best.block_items);
     if (gfc_status s = gfc_tune_cache_put(cache_path, key.c_str(), v)) return s;
   }
   if (out) *out = r;

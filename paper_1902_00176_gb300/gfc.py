@@ -38,7 +38,7 @@ class _Opts(ctypes.Structure):
     _fields_ = [("H", ctypes.c_int), ("W", ctypes.c_int), ("C", ctypes.c_int), ("batch", ctypes.c_int),
                 ("dtype", ctypes.c_int), ("pad", ctypes.c_int), ("size_policy", ctypes.c_int),
                 ("chunk", ctypes.c_int), ("stream", ctypes.c_void_p), ("streams", ctypes.c_int),
-                ("column_solver", ctypes.c_int)]
+                ("column_solver", ctypes.c_int), ("block_items", ctypes.c_int)]
 
 
 class Item(ctypes.Structure):
@@ -56,9 +56,9 @@ EDIT_KINDS = {"none": 0, "threshold": 1, "merge": 2}
 
 class TuneResult(ctypes.Structure):
     """Mirror of gfc_tune_result."""
-    _fields_ = [("column_solver", ctypes.c_int), ("chunk", ctypes.c_int), ("streams", ctypes.c_int),
-                ("rag_streams", ctypes.c_int), ("ms", ctypes.c_double), ("candidates", ctypes.c_int),
-                ("from_cache", ctypes.c_int)]
+    _fields_ = [("column_solver", ctypes.c_int), ("block_items", ctypes.c_int), ("chunk", ctypes.c_int),
+                ("streams", ctypes.c_int), ("rag_streams", ctypes.c_int), ("ms", ctypes.c_double),
+                ("candidates", ctypes.c_int), ("from_cache", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -207,7 +207,8 @@ class Plan:
     """A GFC plan: Green spectrum, transform tables and scratch for one problem shape."""
 
     def __init__(self, H: int, W: int, C: int = 1, batch: int = 1, dtype=torch.float32, pad: int = 4,
-                 chunk: int = 0, device=None, streams: int = 0, exact: bool = False, column_fft: bool = False):
+                 chunk: int = 0, device=None, streams: int = 0, exact: bool = False, column_fft: bool = False,
+                 block_items: bool = False):
         """``exact=True`` solves on Algorithm A's own padded size (H + 2p) x (W + 2p)
         instead of the next even 7-smooth size. ``column_fft=True`` applies the column
         direction of the Green multiply by column FFTs instead of the recursive
@@ -218,7 +219,7 @@ class Plan:
                                    torch.device(device).index or 0)
         self.H, self.W, self.C, self.batch, self.dtype = H, W, C, batch, dtype
         o = _Opts(H, W, C, batch, _DTYPES[dtype], pad, 1 if exact else 0, chunk, None, streams,
-                  1 if column_fft else 0)
+                  1 if column_fft else 0, 1 if block_items else 0)
         h = ctypes.c_void_p()
         with torch.cuda.device(self.device):
             _check(lib().gfc_plan_create_ex(ctypes.byref(h), ctypes.byref(o)))

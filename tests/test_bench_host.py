@@ -83,3 +83,28 @@ def test_oracle_error_leg_on_cpu():
     e = bench.oracle_errors(smp)
     assert e["a"]["rel_l2"] < 1e-14 and e["a"]["fields"] == 1
     assert abs(e["b"]["max_abs"] - 1e-3) < 1e-9
+
+
+def test_split_flag_parsing():
+    assert bench.parse_split("0:50:2:0") == (0, 50, 2, 0)
+    assert bench.parse_split("1:0:1:1") == (1, 0, 1, 1)
+    for bad in ("0:50:2", "2:0:1:0", "0:-1:1:0", "0:1:1:2", "a:b:c:d"):
+        try:
+            bench.parse_split(bad)
+        except ValueError:
+            continue
+        raise AssertionError(bad)
+
+
+def test_issue_roofline_from_a_record(tmp_path):
+    p = tmp_path / "i.txt"
+    counts = {k: 1.0e6 for k in bench.ISSUE_KEYS}
+    p.write_text(f"kernel_build: {bench._kernel_build_id()}\n" + "".join(f"{k}: {v}\n" for k, v in counts.items()))
+    rec = bench.stored_record(str(p), bench.ISSUE_KEYS)
+    r = bench.issue_roofline(rec, fields=100, ms_step=0.5, clocks={"sm_mhz": 2000.0})
+    # 3e8 warp instructions in 0.5 ms = 0.6 T/s against 152 x 4 x 2 GHz = 1.216 T/s
+    assert abs(r["achieved"] - 0.6) < 1e-12 and abs(r["peak"] - 1.216) < 1e-12
+    assert abs(r["fp32"]["peak"] - 152 * 128 * 2e9 / 1e12) < 1e-9
+    assert bench.issue_roofline(None, 100, 0.5, None) is None
+    p.write_text("kernel_build: 0000\n" + "".join(f"{k}: 1\n" for k in bench.ISSUE_KEYS))
+    assert bench.stored_record(str(p), bench.ISSUE_KEYS) is None

@@ -30,13 +30,14 @@ def test_autotune_uniform_plan_and_cache(tmp_path):
     cache = str(tmp_path / "tune.txt")
     r = p.autotune(cache)
     assert r["from_cache"] == 0 and r["candidates"] >= 2 and r["ms"] > 0
-    assert r["column_solver"] in (0, 1) and r["streams"] in (1, 2)
+    assert r["column_solver"] in (0, 1) and r["streams"] in (1, 2, 3, 4) and r["block_items"] in (0, 1)
     after = p.solve_from_gradient(tx, ty)
     assert _rel(after, before) <= 2e-6
     assert gfc.tune_cache_get(cache, p.tune_key()) is not None
     q = gfc.Plan(H, W, 1, B, device=DEV)
     r2 = q.autotune(cache)
     assert r2["from_cache"] == 1 and r2["column_solver"] == r["column_solver"] and r2["chunk"] == r["chunk"]
+    assert r2["streams"] == r["streams"] and r2["block_items"] == r["block_items"]
     assert torch.equal(q.solve_from_gradient(tx, ty), after)
     p.close()
     q.close()
@@ -54,7 +55,7 @@ def test_autotune_ragged_plan_keeps_its_results(tmp_path):
     before = rp.solve_from_gradient(gx, gy).clone()
     cache = str(tmp_path / "tune.txt")
     r = rp.autotune(cache)
-    assert r["rag_streams"] in (1, 2, 4) and r["candidates"] >= 2
+    assert r["rag_streams"] in (1, 2, 4, 8) and r["candidates"] >= 2
     assert torch.equal(rp.solve_from_gradient(gx, gy), before)
     rp2 = gfc.RaggedPlan(items, device=DEV)
     r2 = rp2.autotune(cache)
@@ -62,3 +63,18 @@ def test_autotune_ragged_plan_keeps_its_results(tmp_path):
     assert torch.equal(rp2.solve_from_gradient(gx, gy), before)
     rp.close()
     rp2.close()
+
+
+@pytest.mark.parametrize("H,W,B", [(801, 1200, 7), (256, 256, 40)])
+def test_block_per_item_grids_give_the_same_bits(H, W, B):
+    """One block per item runs the same per-item arithmetic as the persistent grids:
+    results are bitwise equal, whole batch and in chunks over streams."""
+    gx, gy = synth.perturbed_gradient_batch(batch=B, H=H, W=W, seed=9500 + H)
+    tx, ty = torch.from_numpy(gx).to(DEV), torch.from_numpy(gy).to(DEV)
+    ref = gfc.Plan(H, W, 1, B, device=DEV)
+    want = ref.solve_from_gradient(tx, ty)
+    for chunk, streams in ((0, 1), (3, 2)):
+        p = gfc.Plan(H, W, 1, B, device=DEV, chunk=chunk, streams=streams, block_items=True)
+        assert torch.equal(p.solve_from_gradient(tx, ty), want), (chunk, streams)
+        p.close()
+    ref.close()
