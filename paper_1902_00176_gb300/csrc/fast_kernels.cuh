@@ -85,6 +85,11 @@ struct FastArgs {
 // exact solution into it.
 // (The plan sizes this per field in tri_field.)
 constexpr int kTriCols = 32;
+// Slots of a field's FP64 partial-sum area used by the recursive column solve:
+// [0, nkb) the sweep blocks' partials of u[0,0]; kTriCnt a counter of sweep
+// blocks done (reset by the row pass, which runs first); kTriU00 u[0,0] itself,
+// combined by the last sweep block of the field.
+constexpr int kTriCnt = 150, kTriU00 = 151;
 __device__ __forceinline__ float2* tri_sums(float2* tri, int field, const FastArgs& A) {
   return tri + (size_t)field * A.tri_field + (size_t)2 * A.G * A.ldY;
 }
@@ -480,7 +485,8 @@ __global__ void __launch_bounds__(S::THREADS, S::MINB_FWD) k_fast_rows_fwd(const
                                                                  float2* __restrict__ spec,
                                                                  const float2* __restrict__ twg, FastArgs A,
                                                                  float2* __restrict__ tri,
-                                                                 const float* __restrict__ cc) {
+                                                                 const float* __restrict__ cc,
+                                                                 float* __restrict__ partial = nullptr) {
   extern __shared__ __align__(16) float2 sm[];
   float2* tw2 = sm;                   // [R1][R2]: w_N^(r j)
   float2* buf = sm + S::R1 * S::R2;   // staged packed rows [F][ldz], then the exchange (m -> m + m / R1)
@@ -499,18 +505,27 @@ __global__ void __launch_bounds__(S::THREADS, S::MINB_FWD) k_fast_rows_fwd(const
   const int uf = tid % S::F, uk0 = tid / S::F;
   const bool uact = tid < S::F * S::T;
   const int items = A.nf * A.ngroups;
-  auto issue = [&](int w) {  // one thread: stage the packed rows of item w (zero padded, whole rows)
+  // one thread: stage the packed rows of item w (zero padded, whole rows);
+  // prefetch: only start fetching them into L2, for the copy one item later
+  auto issue = [&](int w, bool prefetch) {
     const int field = w / A.ngroups, g = w - field * A.ngroups;
-    bulk_load(buf, z + ((size_t)field * A.zpairs + (size_t)g * S::F) * A.ldz,
-              (unsigned)(S::F * A.ldz * sizeof(float2)), &bar);
+    const float2* zs = z + ((size_t)field * A.zpairs + (size_t)g * S::F) * A.ldz;
+    const unsigned nb = (unsigned)(S::F * A.ldz * sizeof(float2));
+    if (prefetch)
+      l2_prefetch(zs, nb);
+    else
+      bulk_load(buf, zs, nb, &bar);
   };
   if (tid == 0) mbar_init(&bar, 1);
   __syncthreads();
-  if (tid == 0 && (int)blockIdx.x < items) issue(blockIdx.x);
+  if (tid == 0 && (int)blockIdx.x < items) issue(blockIdx.x, false);
+  if (tid == 0 && (int)(blockIdx.x + gridDim.x) < items) issue(blockIdx.x + gridDim.x, true);
   unsigned phase = 0;
 #pragma unroll 1
   for (int w = blockIdx.x; w < items; w += gridDim.x, phase ^= 1u) {
     const int field = w / A.ngroups, g = w - field * A.ngroups;
+    if (TRI && g == 0 && tid == 0)  // the sweep's count of finished blocks for this field starts at 0
+      reinterpret_cast<unsigned*>(reinterpret_cast<double*>(partial) + (size_t)field * (kMaxRowBlocks / 2) + kTriCnt)[0] = 0u;
     const bool landed = mbar_wait(&bar, phase);
     if (__syncthreads_or(!landed)) {  // the copy never completed: report, let it drain, stop
       if (tid == 0) atomicExch(A.err, kErrBulkWait);
@@ -544,7 +559,8 @@ __global__ void __launch_bounds__(S::THREADS, S::MINB_FWD) k_fast_rows_fwd(const
       if (jj == S::J2 - 1) {
         fence_proxy_async_smem();  // this thread's accesses of buf precede the next bulk copy into it
         __syncthreads();           // buf free
-        if (tid == 0 && w + (int)gridDim.x < items) issue(w + gridDim.x);
+        if (tid == 0 && w + (int)gridDim.x < items) issue(w + gridDim.x, false);
+        if (tid == 0 && w + 2 * (int)gridDim.x < items) issue(w + 2 * gridDim.x, true);
       }
       if (act2) {
         dft_reg<S::R2, -1>(u);
@@ -650,29 +666,40 @@ __global__ void __launch_bounds__(S::THREADS, S::MINB_FWD) k_fast_rows_fwd_div(c
   const bool uact = tid < S::F * S::T;
   const int items = A.nf * A.ngroups;
   const size_t fe = (size_t)A.H * A.W;
-  auto issue = [&](int w) {  // one thread: stage the gradient rows of item w
+  // one thread: stage the gradient rows of item w (prefetch: only start
+  // fetching the same rows into L2, for the copy one item later)
+  auto issue = [&](int w, bool prefetch) {
     const int field = w / A.ngroups, g = w - field * A.ngroups;
     const int r0 = g * RW;
     const int nx = (A.H - r0) < RW ? (A.H - r0) : RW;             // gx rows r0 .. r0 + nx - 1 (nx may be 0)
     const int y0 = r0 > 0 ? r0 - 1 : 0, y1 = (A.H < r0 + RW) ? A.H : r0 + RW;  // gy rows y0 .. y1 - 1
     const unsigned row = (unsigned)(A.W * sizeof(T));
+    const T* xs = gx + field * fe + (size_t)r0 * A.W;
+    const T* ys = gy + field * fe + (size_t)y0 * A.W;
+    if (prefetch) {
+      if (nx > 0) l2_prefetch(xs, (unsigned)nx * row);
+      if (!ADJ) l2_prefetch(ys, (unsigned)(y1 - y0) * row);
+      return;
+    }
     if constexpr (ADJ) {
-      bulk_load(sgx, gx + field * fe + (size_t)r0 * A.W, (unsigned)nx * row, &bar);  // nx >= 1 here
+      bulk_load(sgx, xs, (unsigned)nx * row, &bar);  // nx >= 1 here
     } else {
       mbar_expect_tx(&bar, (unsigned)(nx > 0 ? nx : 0) * row + (unsigned)(y1 - y0) * row);
-      if (nx > 0) bulk_copy(sgx, gx + field * fe + (size_t)r0 * A.W, (unsigned)nx * row, &bar);
-      bulk_copy(sgy + (size_t)(y0 - (r0 - 1)) * A.W, gy + field * fe + (size_t)y0 * A.W, (unsigned)(y1 - y0) * row,
-                &bar);
+      if (nx > 0) bulk_copy(sgx, xs, (unsigned)nx * row, &bar);
+      bulk_copy(sgy + (size_t)(y0 - (r0 - 1)) * A.W, ys, (unsigned)(y1 - y0) * row, &bar);
     }
   };
   if (tid == 0) mbar_init(&bar, 1);
   __syncthreads();
-  if (tid == 0 && (int)blockIdx.x < items) issue(blockIdx.x);
+  if (tid == 0 && (int)blockIdx.x < items) issue(blockIdx.x, false);
+  if (tid == 0 && (int)(blockIdx.x + gridDim.x) < items) issue(blockIdx.x + gridDim.x, true);
   unsigned phase = 0;
   constexpr int kEdW = (S::N + S::THREADS - 1) / S::THREADS;  // gx values of the row above, per thread
 #pragma unroll 1
   for (int w = blockIdx.x; w < items; w += gridDim.x, phase ^= 1u) {
     const int field = w / A.ngroups, g = w - field * A.ngroups;
+    if (TRI && g == 0 && tid == 0)  // the sweep's count of finished blocks for this field starts at 0
+      reinterpret_cast<unsigned*>(reinterpret_cast<double*>(partial) + (size_t)field * (kMaxRowBlocks / 2) + kTriCnt)[0] = 0u;
     float gxa[EDIT == kEditThreshold ? kEdW : 1];
     if constexpr (EDIT == kEditThreshold) {
       const int r0 = g * RW;
@@ -835,7 +862,8 @@ __global__ void __launch_bounds__(S::THREADS, S::MINB_FWD) k_fast_rows_fwd_div(c
     }
     fence_proxy_async_smem();  // this thread's accesses of the buffers precede the next bulk copies
     __syncthreads();
-    if (tid == 0 && w + (int)gridDim.x < items) issue(w + gridDim.x);
+    if (tid == 0 && w + (int)gridDim.x < items) issue(w + gridDim.x, false);
+    if (tid == 0 && w + 2 * (int)gridDim.x < items) issue(w + 2 * gridDim.x, true);
   }
 }
 
@@ -1084,7 +1112,24 @@ static __global__ void __launch_bounds__(32 * (kTriSeg + 1)) k_tri_carries(float
     double acc = 0.0;
     if (col_ok) acc = (2 * k == A.N ? 1.0 : 2.0) * (double)(C * fmaf(a, yls[lane], y0s[lane].x));
     acc = warp_sum_d(acc);
-    if (lane == 0) partial[(size_t)field * (kMaxRowBlocks / 2) + kb] = acc;
+    double* pp = partial + (size_t)field * (kMaxRowBlocks / 2);
+    unsigned done = 0;
+    if (lane == 0) {
+      pp[kb] = acc;
+      __threadfence();  // this partial is visible before the count says so
+      done = atomicAdd(reinterpret_cast<unsigned*>(pp + kTriCnt), 1u);
+    }
+    done = __shfl_sync(0xffffffffu, done, 0);
+    if (done == (unsigned)gridDim.x - 1) {
+      // the field's last sweep block: u[0,0] from every block's partial,
+      // lane-strided then a fixed shuffle tree (the same order on every call)
+      __threadfence();
+      double s2 = 0.0;
+      for (int i = lane; i < (int)gridDim.x; i += 32) s2 += __ldcg(pp + i);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s2 += __shfl_down_sync(0xffffffffu, s2, o);
+      if (lane == 0) pp[kTriU00] = s2;
+    }
   }
   if (warp == kTriSeg && kb == 0) {
     const bool landed = mbar_wait(&bar, 0);
@@ -1312,38 +1357,62 @@ __global__ void __launch_bounds__(S::THREADS, S::MINB_INV) k_fast_rows_inv(const
   float2* mybuf = buf + (act ? f : 0) * S::NP;
   const int half = S::N / 2;
   const int items = A.nf * A.ngroups;
-  auto issue = [&](int w) {  // one thread: stage the rows of item w
+  // one thread: stage the rows of item w (prefetch: only start fetching them
+  // into L2, for the copy one item later)
+  auto issue = [&](int w, bool prefetch) {
     const int field = w / A.ngroups, g = w - field * A.ngroups;
     const int r0 = g * RW, nr = (A.H - r0) < RW ? (A.H - r0) : RW;
     if constexpr (TRI) {  // the whole band of S (its rows past the image feed the recursions) and its carries
       const unsigned rb = (unsigned)(RW * A.ldY * sizeof(float2)), cb = (unsigned)(2 * A.ldY * sizeof(float2));
+      const float2* ss = Y + ((size_t)field * A.srows + r0) * A.ldY;
+      const float2* cs = tri + (size_t)field * A.tri_field + (size_t)g * 2 * A.ldY;
+      if (prefetch) {
+        l2_prefetch(ss, rb);
+        l2_prefetch(cs, cb);
+        return;
+      }
       mbar_expect_tx(&bar, rb + cb);
-      bulk_copy(buf, Y + ((size_t)field * A.srows + r0) * A.ldY, rb, &bar);
-      bulk_copy(cbuf, tri + (size_t)field * A.tri_field + (size_t)g * 2 * A.ldY, cb, &bar);
-    } else
-      bulk_load(buf, Y + ((size_t)field * A.H + r0) * A.ldY, (unsigned)(nr * A.ldY * sizeof(float2)), &bar);
+      bulk_copy(buf, ss, rb, &bar);
+      bulk_copy(cbuf, cs, cb, &bar);
+    } else {
+      const float2* ys = Y + ((size_t)field * A.H + r0) * A.ldY;
+      const unsigned nb = (unsigned)(nr * A.ldY * sizeof(float2));
+      if (prefetch)
+        l2_prefetch(ys, nb);
+      else
+        bulk_load(buf, ys, nb, &bar);
+    }
   };
   // warp 0 loads the u[0,0] partial sums of the next item while this one is
-  // transformed (lane-strided, the same order as a plain loop over them)
-  constexpr int KPF = 5;
+  // transformed (lane-strided, the same order as a plain loop over them); with
+  // the recursive column solve the carry sweep has already combined them into
+  // the field's u[0,0] (kTriU00), one value to load
+  constexpr int KPF = TRI ? 1 : 5;
   double pf[KPF];
   auto prefetch = [&](int w) {
     if (tid < 32 && w < items) {
       const double* pp = reinterpret_cast<const double*>(partial) + (size_t)(w / A.ngroups) * (kMaxRowBlocks / 2);
+      if constexpr (TRI) {
+        pf[0] = tid == 0 ? pp[kTriU00] : 0.0;
+      } else {
 #pragma unroll
-      for (int k = 0; k < KPF; ++k) pf[k] = (tid + 32 * k < A.nparts) ? pp[tid + 32 * k] : 0.0;
+        for (int k = 0; k < KPF; ++k) pf[k] = (tid + 32 * k < A.nparts) ? pp[tid + 32 * k] : 0.0;
+      }
     }
   };
   if (tid == 0) mbar_init(&bar, 1);
   __syncthreads();
-  if (tid == 0 && (int)blockIdx.x < items) issue(blockIdx.x);
+  if (tid == 0 && (int)blockIdx.x < items) issue(blockIdx.x, false);
+  if (tid == 0 && (int)(blockIdx.x + gridDim.x) < items) issue(blockIdx.x + gridDim.x, true);
   prefetch(blockIdx.x);
   int parity = 0;
   unsigned phase = 0;
 #pragma unroll 1
   for (int w = blockIdx.x; w < items; w += gridDim.x, parity ^= 1, phase ^= 1u) {
     const int field = w / A.ngroups, g = w - field * A.ngroups;
-    if (tid < 32) {
+    if constexpr (TRI) {
+      if (tid == 0) u00s[parity] = (float)pf[0];
+    } else if (tid < 32) {
       // u[0,0] from the column blocks' FP64 partial sums: lane-strided, then a
       // fixed shuffle tree (the same order on every call)
       double s2 = 0.0;
@@ -1424,7 +1493,8 @@ __global__ void __launch_bounds__(S::THREADS, S::MINB_INV) k_fast_rows_inv(const
       if (jj == S::J2 - 1) {
         fence_proxy_async_smem();  // this thread's accesses of buf precede the next bulk copy into it
         __syncthreads();           // buf free
-        if (tid == 0 && w + (int)gridDim.x < items) issue(w + gridDim.x);
+        if (tid == 0 && w + (int)gridDim.x < items) issue(w + gridDim.x, false);
+        if (tid == 0 && w + 2 * (int)gridDim.x < items) issue(w + 2 * gridDim.x, true);
         prefetch(w + gridDim.x);
       }
       if (act2) {
@@ -1586,14 +1656,22 @@ __global__ void __launch_bounds__(S::THREADS, S::MINB_ADJ) k_fast_rows_adj(const
   }
   float2* mybuf = buf + (act ? f : 0) * S::NP;
   const int items = A.nf * A.ngroups;
-  auto issue = [&](int w) {  // one thread: rows gF .. gF + F of Y (fewer at the end of a field)
+  // one thread: rows gF .. gF + F of Y (fewer at the end of a field); prefetch:
+  // only start fetching them into L2, for the copy one item later
+  auto issue = [&](int w, bool prefetch) {
     const int field = w / A.ngroups, g = w - field * A.ngroups;
     const int r0 = g * S::F, nr = (A.H + 1 - r0) < S::F + 1 ? (A.H + 1 - r0) : S::F + 1;
-    bulk_load(stg, Y + ((size_t)field * (A.H + 1) + r0) * A.ldY, (unsigned)(nr * A.ldY * sizeof(float2)), &bar);
+    const float2* ys = Y + ((size_t)field * (A.H + 1) + r0) * A.ldY;
+    const unsigned nb = (unsigned)(nr * A.ldY * sizeof(float2));
+    if (prefetch)
+      l2_prefetch(ys, nb);
+    else
+      bulk_load(stg, ys, nb, &bar);
   };
   if (tid == 0) mbar_init(&bar, 1);
   __syncthreads();
-  if (tid == 0 && (int)blockIdx.x < items) issue(blockIdx.x);
+  if (tid == 0 && (int)blockIdx.x < items) issue(blockIdx.x, false);
+  if (tid == 0 && (int)(blockIdx.x + gridDim.x) < items) issue(blockIdx.x + gridDim.x, true);
   unsigned phase = 0;
 #pragma unroll 1
   for (int w = blockIdx.x; w < items; w += gridDim.x, phase ^= 1u) {
@@ -1629,7 +1707,8 @@ __global__ void __launch_bounds__(S::THREADS, S::MINB_ADJ) k_fast_rows_adj(const
       return;
     }
     // every staged row read, and the previous item's stage 2 done with buf
-    if (tid == 0 && w + (int)gridDim.x < items) issue(w + gridDim.x);
+    if (tid == 0 && w + (int)gridDim.x < items) issue(w + gridDim.x, false);
+    if (tid == 0 && w + 2 * (int)gridDim.x < items) issue(w + 2 * gridDim.x, true);
     if (act) {
       dft_reg<S::R1, +1>(v);
 #pragma unroll
@@ -1729,6 +1808,7 @@ static cudaError_t run_fast_mode(gfc_plan* P, const Bufs& bf, const T* in0, cons
   if ((size_t)2 * RS::F * A.ldY > (size_t)RS::F * RS::NP || A.ldz > RS::NP || A.zpairs > kAdjTotal)
     return cudaErrorInvalidConfiguration;
   if (tri && (size_t)A.srows * A.ldY > P->spec_field) return cudaErrorInvalidConfiguration;
+  if (tri && (P->Nh + kTriCols - 1) / kTriCols > kTriCnt) return cudaErrorInvalidConfiguration;
   static std::mutex mu;
   static int slots_a = 0, slots_b = 0, slots_c = 0, slots_d = 0, slots_ta = 0, slots_tc = 0, slots_td = 0,
              slots_ts = 0, slots_tde = 0;
@@ -1834,7 +1914,7 @@ static cudaError_t run_fast_mode(gfc_plan* P, const Bufs& bf, const T* in0, cons
     prof_begin(P, 0, st);
     if (tri)
       k_fast_rows_fwd<RS, true><<<grid_for(a_items, slots_ta), RS::THREADS, RS::smem_bytes_fwd(), st>>>(
-          bf.zbuf, bf.spec, P->twN, A, bf.tri, P->colcoef);
+          bf.zbuf, bf.spec, P->twN, A, bf.tri, P->colcoef, bf.partial);
     else if constexpr (kCols)
       k_fast_rows_fwd<RS, false><<<grid_for(a_items, slots_a), RS::THREADS, RS::smem_bytes_fwd(), st>>>(
           bf.zbuf, bf.spec, P->twN, A, nullptr, nullptr);
