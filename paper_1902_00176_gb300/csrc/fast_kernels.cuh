@@ -72,6 +72,7 @@ struct FastArgs {
   int srows;         // rows of S per field (2 zpairs; rows past the support are zero)
   int G;             // bands per field
   size_t tri_field;  // complex elements per field of the band scratch
+  int stage_out;     // inverse row pass: output rows staged in shared memory, stored by bulk copy
 };
 
 // Band scratch of one field (recursive column solve), complex elements:
@@ -154,9 +155,18 @@ struct RowShape {
   static constexpr size_t smem_bytes_tri_inv() { return (size_t)(CBUF + 2 * LDY_) * sizeof(float2); }
   static constexpr size_t smem_bytes_fwd() { return (size_t)(R1 * R2 + F * NP + F * NO) * sizeof(float2); }
   // blocks per SM the register allocation must allow: long rows fill shared
-  // memory at 2 (3 for the inverse pass); short rows leave room for 4
+  // memory at 2 (3 for the inverse pass); short rows leave room for 4. Wider
+  // blocks and long stage-2 radices get fewer, so that the transforms keep
+  // their values in registers (at least ~200 registers a thread in the forward
+  // passes, ~160 in the inverse one; stage-2 radices >= 48 take 2 blocks)
   static constexpr bool SHORT = N <= 512;
-  static constexpr int MINB_FWD = SHORT ? 4 : 2, MINB_INV = SHORT ? 4 : 3, MINB_ADJ = SHORT ? 4 : 2;
+  static constexpr int cx_blocks(int cap, int regs) {
+    const int b = 65536 / (THREADS * regs);
+    return b < 1 ? 1 : (b > cap ? cap : b);
+  }
+  static constexpr int MINB_FWD = SHORT ? 4 : cx_blocks(2, 200);
+  static constexpr int MINB_INV = SHORT ? 4 : cx_blocks(R2 >= 48 ? 2 : 3, 160);
+  static constexpr int MINB_ADJ = SHORT ? 4 : cx_blocks(2, 200);
   // adjoint inverse row pass: twiddles, exchange, the factor table
   // 1 - exp(2 pi i l / N) for l <= N/2, then (16-byte aligned) the F + 1 rows of
   // Y an item needs, LDY complex each
@@ -1288,6 +1298,32 @@ __device__ __forceinline__ void tri_solve_band(float2* buf, const float2* cbuf, 
                                                const FastArgs& A) {
   constexpr int RW = 2 * S::F;
   const int nb = min(RW, A.M - A.p - g * RW);
+  if constexpr (S::SHORT) {
+    // short rows: one column per thread (the band's RW values of a column pair
+    // would not fit the registers of four blocks per SM)
+    const float2* dcs = reinterpret_cast<const float2*>(cc + (size_t)A.Nh * 8);  // (delta, C) per column
+    for (int k = 1 + threadIdx.x; k < A.Nh; k += blockDim.x) {
+      const float2 dc = __ldg(dcs + k);
+      float2 yc = cbuf[k], ya = cbuf[S::LDY + k];
+      float2* col = buf + k;
+      float2 x[RW];
+#pragma unroll
+      for (int r = 0; r < RW; ++r) x[r] = col[(size_t)r * S::LDY];
+#pragma unroll
+      for (int r = 0; r < RW; ++r)
+        if (r < nb) {
+          yc = tri_step(x[r], yc, dc.x);
+          col[(size_t)r * S::LDY] = yc;
+        }
+#pragma unroll
+      for (int r = RW - 1; r >= 0; --r)
+        if (r < nb) {
+          ya = tri_step(x[r], ya, dc.x);
+          col[(size_t)r * S::LDY] = cscale(csub(cadd(col[(size_t)r * S::LDY], ya), x[r]), dc.y);
+        }
+    }
+    return;
+  }
   // thread t takes the column pair (2j, 2j + 1), 16-byte shared-memory accesses;
   // column 0 (already solved) and columns >= Nh pass through unchanged
   for (int j = threadIdx.x; 2 * j < A.Nh; j += blockDim.x) {
@@ -1431,6 +1467,7 @@ __global__ void __launch_bounds__(S::THREADS, S::MINB_INV) k_fast_rows_inv(const
     if (__syncthreads_or(!landed)) {  // the copy never completed: report, let it drain, stop
       if (tid == 0) atomicExch(A.err, kErrBulkWait);
       mbar_wait(&bar, phase);
+      if (tid == 0) bulk_store_wait();
       return;
     }
     if constexpr (TRI) {
@@ -1471,6 +1508,11 @@ __global__ void __launch_bounds__(S::THREADS, S::MINB_INV) k_fast_rows_inv(const
     const bool act2 = act && t < S::JSPAN;
     const float u00 = u00s[parity];
     T* o = out + (size_t)field * A.H * A.W;
+    // one stage-2 butterfly per thread: once its inputs are in registers the
+    // exchange buffer is free, and the item's output rows are staged there
+    // ([2F][W], the output's own row pitch) and leave by one bulk copy
+    const bool stage = S::J2 == 1 && A.stage_out;
+    T* srows = reinterpret_cast<T*>(buf);
     // STATS: this thread's stored values as float sums about its first value
     float st_sh = 0.0f, st_s = 0.0f, st_q = 0.0f;
     int st_n = 0;
@@ -1491,11 +1533,15 @@ __global__ void __launch_bounds__(S::THREADS, S::MINB_INV) k_fast_rows_inv(const
         for (int r = 1; r < S::R2; ++r) u[r] = cmul(mybuf[j + (S::R1 + 1) * r], cconj(tw2[j * S::R2 + r]));
       }
       if (jj == S::J2 - 1) {
-        fence_proxy_async_smem();  // this thread's accesses of buf precede the next bulk copy into it
-        __syncthreads();           // buf free
-        if (tid == 0 && w + (int)gridDim.x < items) issue(w + gridDim.x, false);
-        if (tid == 0 && w + 2 * (int)gridDim.x < items) issue(w + 2 * gridDim.x, true);
-        prefetch(w + gridDim.x);
+        if (stage) {
+          __syncthreads();  // every stage-2 input read: buf takes the output rows
+        } else {
+          fence_proxy_async_smem();  // this thread's accesses of buf precede the next bulk copy into it
+          __syncthreads();           // buf free
+          if (tid == 0 && w + (int)gridDim.x < items) issue(w + gridDim.x, false);
+          if (tid == 0 && w + 2 * (int)gridDim.x < items) issue(w + 2 * gridDim.x, true);
+          prefetch(w + gridDim.x);
+        }
       }
       if (act2) {
         dft_reg<S::R2, +1>(u);
@@ -1506,8 +1552,13 @@ __global__ void __launch_bounds__(S::THREADS, S::MINB_INV) k_fast_rows_inv(const
           const bool sure = (S::R2 * jj + S::R1 * s2 >= kP) && (S::R2 * jj + S::JSPAN - 1 + S::R1 * s2 - kP < S::WMIN);
           if (sure || (jc >= 0 && jc < A.W)) {
             const T qa = f_from_f<T>(u[s2].x - u00), qb = f_from_f<T>(u[s2].y - u00);
-            if (va) o[(size_t)ia * A.W + jc] = qa;
-            if (vb) o[(size_t)ib * A.W + jc] = qb;
+            if (stage) {
+              srows[(size_t)(2 * f) * A.W + jc] = qa;
+              srows[(size_t)(2 * f + 1) * A.W + jc] = qb;
+            } else {
+              if (va) o[(size_t)ia * A.W + jc] = qa;
+              if (vb) o[(size_t)ib * A.W + jc] = qb;
+            }
             if constexpr (STATS) {
               if (va) st_add(f_to_f(qa));
               if (vb) st_add(f_to_f(qb));
@@ -1515,6 +1566,18 @@ __global__ void __launch_bounds__(S::THREADS, S::MINB_INV) k_fast_rows_inv(const
           }
         }
       }
+    }
+    if (stage) {
+      fence_proxy_async_smem();  // the staged rows precede the bulk copy that reads them
+      __syncthreads();
+      if (tid == 0) {
+        const int r0 = g * 2 * S::F, nr = (A.H - r0) < 2 * S::F ? (A.H - r0) : 2 * S::F;
+        bulk_store(o + (size_t)r0 * A.W, srows, (unsigned)((size_t)nr * A.W * sizeof(T)));
+        bulk_store_wait_read();  // buf read out: the next item may land in it
+        if (w + (int)gridDim.x < items) issue(w + gridDim.x, false);
+        if (w + 2 * (int)gridDim.x < items) issue(w + 2 * gridDim.x, true);
+      }
+      prefetch(w + gridDim.x);
     }
     if constexpr (STATS) {
       // (count, mean, M2) of the thread, combined pairwise (Chan et al.'s update,
@@ -1554,6 +1617,7 @@ __global__ void __launch_bounds__(S::THREADS, S::MINB_INV) k_fast_rows_inv(const
       // st_red is rewritten only after the next item's barriers
     }
   }
+  if (tid == 0) bulk_store_wait();  // the last staged rows are stored before the kernel ends
 }
 
 // Colour correction of Eq. 25 for fields whose statistics the inverse row pass
@@ -1789,6 +1853,7 @@ static cudaError_t run_fast_mode(gfc_plan* P, const Bufs& bf, const T* in0, cons
   const bool tri = kTriMode && P->tri;
   if (!kCols && !tri) return cudaErrorNotSupported;
   FastArgs A;
+  A.stage_out = 0;
   A.H = P->H; A.W = P->W; A.p = P->pad; A.M = P->M; A.N = P->N; A.Nh = P->Nh; A.ldM = P->ldM;
   A.nrows = (MODE == 0) ? P->H + 1 : P->H;
   A.ncols = (MODE == 0) ? P->W + 1 : P->W;
@@ -1938,6 +2003,10 @@ static cudaError_t run_fast_mode(gfc_plan* P, const Bufs& bf, const T* in0, cons
   prof_end(P, st);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   FastArgs C = A;
+  // the inverse row pass stages its output rows in its exchange buffer and
+  // stores them by bulk copy when the rows are whole 16-byte multiples
+  C.stage_out = MODE != 2 && (P->W * sizeof(T)) % 16 == 0 && (reinterpret_cast<uintptr_t>(out0) & 15) == 0 &&
+                (size_t)2 * RS::F * P->W * sizeof(T) <= (size_t)RS::F * RS::NP * sizeof(float2);
   prof_begin(P, 2, st);
   if constexpr (MODE == 2) {
     C.ngroups = (P->H + RS::F - 1) / RS::F;

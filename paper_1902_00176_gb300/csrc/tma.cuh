@@ -66,6 +66,24 @@ __device__ __forceinline__ void l2_prefetch(const void* src_gmem, unsigned bytes
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(src_gmem), "r"(bytes) : "memory");
 }
 
+// one thread: start a copy of `bytes` (a multiple of 16; both addresses 16-byte
+// aligned) from shared to global memory, in this thread's current bulk group
+__device__ __forceinline__ void bulk_store(void* dst_gmem, const void* src_smem, unsigned bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;\n" ::"l"(dst_gmem),
+               "r"(smem_addr(src_smem)), "r"(bytes)
+               : "memory");
+  asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
+}
+
+// the issuing thread: wait until its bulk stores have read their shared-memory
+// sources (the buffer may be written again)
+__device__ __forceinline__ void bulk_store_wait_read() {
+  asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory");
+}
+
+// the issuing thread: wait until its bulk stores have completed
+__device__ __forceinline__ void bulk_store_wait() { asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory"); }
+
 // wait until the barrier's phase `parity` has completed; false if the time
 // bound ran out
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity,
