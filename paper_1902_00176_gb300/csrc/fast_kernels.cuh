@@ -73,6 +73,7 @@ struct FastArgs {
   int G;             // bands per field
   size_t tri_field;  // complex elements per field of the band scratch
   int stage_out;     // inverse row pass: output rows staged in shared memory, stored by bulk copy
+  double invM, invN; // 1 / M, 1 / N (FP64 divisions are slow on this part)
 };
 
 // Band scratch of one field (recursive column solve), complex elements:
@@ -144,7 +145,10 @@ struct RowShape {
   static constexpr int T = R2;                            // threads per transform
   static constexpr int J2 = (R1 >= R2) ? R1 / R2 : 1;     // stage-2 butterflies per thread
   static constexpr int JSPAN = (R1 >= R2) ? R2 : R1;      // stage-2 butterflies j = t + R2 jj, t < JSPAN
-  static constexpr int NP = N + N / R1;                   // padded transform buffer
+  // exchange stride of a thread's R1 stage-1 outputs: odd, so that the threads'
+  // 8-byte accesses spread over the banks
+  static constexpr int R1P = (R1 % 2 == 0) ? R1 + 1 : R1 + 2;
+  static constexpr int NP = (N / R1) * R1P;               // padded transform buffer
   static constexpr int THREADS = ((F * T + 31) / 32) * 32;
   static_assert(R1 % R2 == 0 || R1 < R2, "row schedule needs R2 | R1 or R1 < R2");
   static constexpr int NO = N + 1;        // stage-2 output buffer stride (natural order)
@@ -175,9 +179,9 @@ struct RowShape {
     return (((size_t)(R1 * R2 + F * NP + (N / 2 + 1)) * sizeof(float2)) + 15) / 16 * 16;
   }
   static constexpr size_t smem_bytes_adj() { return adj_stage_offset() + (size_t)(F + 1) * LDY * sizeof(float2); }
-  // The exchange keeps one spare slot every R1 elements (element m at
-  // m + m / R1, conflict-free stage-1 writes); the kernels use the closed forms
-  // t (R1 + 1) + s for m = t R1 + s and j + (R1 + 1) r for m = j + R1 r.
+  // The exchange stores each run of R1 elements at a stride of R1P (element
+  // m = t R1 + s at t R1P + s, conflict-free stage-1 writes); the kernels use
+  // the closed forms t R1P + s for m = t R1 + s and j + R1P r for m = j + R1 r.
 };
 
 // Shared-memory wavefronts of the column pass's four exchange accesses for a
@@ -551,20 +555,20 @@ __global__ void __launch_bounds__(S::THREADS, S::MINB_FWD) k_fast_rows_fwd(const
     __syncthreads();  // every staged row read: buf becomes the exchange buffer
     if (act) {
       dft_reg<S::R1, -1>(v);
-      // Stockham stage 1 writes t R1 + s; its padded index is t (R1 + 1) + s
+      // Stockham stage 1 writes t R1 + s; its padded index is t R1P + s
 #pragma unroll
-      for (int s2 = 0; s2 < S::R1; ++s2) mybuf[t * (S::R1 + 1) + s2] = v[s2];
+      for (int s2 = 0; s2 < S::R1; ++s2) mybuf[t * S::R1P + s2] = v[s2];
     }
     __syncthreads();  // stage-1 results visible; previous unpack done with buf2
     const bool act2 = act && t < S::JSPAN;
 #pragma unroll
     for (int jj = 0; jj < S::J2; ++jj) {
-      const int j = t + S::R2 * jj;  // j < R1, so the padded index of j + R1 r is j + (R1 + 1) r
+      const int j = t + S::R2 * jj;  // j < R1, so the padded index of j + R1 r is j + R1P r
       float2 u[S::R2];
       if (act2) {
         u[0] = mybuf[j];
 #pragma unroll
-        for (int r = 1; r < S::R2; ++r) u[r] = cmul(mybuf[j + (S::R1 + 1) * r], tw2[j * S::R2 + r]);
+        for (int r = 1; r < S::R2; ++r) u[r] = cmul(mybuf[j + S::R1P * r], tw2[j * S::R2 + r]);
       }
       if (jj == S::J2 - 1) {
         fence_proxy_async_smem();  // this thread's accesses of buf precede the next bulk copy into it
@@ -823,7 +827,7 @@ __global__ void __launch_bounds__(S::THREADS, S::MINB_FWD) k_fast_rows_fwd_div(c
     if (act) {
       dft_reg<S::R1, -1>(v);
 #pragma unroll
-      for (int s2 = 0; s2 < S::R1; ++s2) mybuf[t * (S::R1 + 1) + s2] = v[s2];
+      for (int s2 = 0; s2 < S::R1; ++s2) mybuf[t * S::R1P + s2] = v[s2];
     }
     __syncthreads();
     if (act && t < S::JSPAN) {
@@ -833,7 +837,7 @@ __global__ void __launch_bounds__(S::THREADS, S::MINB_FWD) k_fast_rows_fwd_div(c
         float2 u[S::R2];
         u[0] = mybuf[j];
 #pragma unroll
-        for (int r = 1; r < S::R2; ++r) u[r] = cmul(mybuf[j + (S::R1 + 1) * r], tw2[j * S::R2 + r]);
+        for (int r = 1; r < S::R2; ++r) u[r] = cmul(mybuf[j + S::R1P * r], tw2[j * S::R2 + r]);
         dft_reg<S::R2, -1>(u);
 #pragma unroll
         for (int s2 = 0; s2 < S::R2; ++s2) mybuf2[j + S::R1 * s2] = u[s2];
@@ -961,16 +965,16 @@ static __device__ __noinline__ void tri_column0(float2* __restrict__ spec, float
   const int r0 = min(lane * run, A.M), r1 = min(r0 + run, A.M);
   double s0 = 0.0;
   for (int r = r0; r < r1; ++r) s0 += (double)fcol[r];
-  const double mean = warp_sum_d(s0) / (double)A.M;
+  const double mean = warp_sum_d(s0) * A.invM;
   const double off = warp_exclusive_scan_d(s0 - mean * (double)(r1 - r0));
   double Gr = off, Gs = 0.0;
   for (int r = r0; r < r1; ++r) {
     Gr += (double)fcol[r] - mean;
     Gs += Gr;
   }
-  const double D = -warp_sum_d(Gs) / (double)A.M;
+  const double D = -warp_sum_d(Gs) * A.invM;
   double u = warp_exclusive_scan_d(D * (double)(r1 - r0) + Gs);
-  const double invN = 1.0 / (double)A.N;
+  const double invN = A.invN;
   Gr = off;
   for (int r = r0; r < r1; ++r) {
     const int i = r - A.p;
@@ -1149,6 +1153,111 @@ static __global__ void __launch_bounds__(32 * (kTriSeg + 1)) k_tri_carries(float
       return;
     }
     tri_column0(spec, fcol, field, A);
+  }
+}
+
+// The carry sweep for fields of at most kTriRegG bands: one warp per (field,
+// block of 32 columns), one column per lane, all of the block's band sums in
+// registers (one round of loads per direction), each direction swept from a
+// zero carry and then from the true carries, as above; no shared-memory
+// staging and no block barriers. The warp of column block 0 then solves
+// column 0 exactly (fcol: M + 4 floats of shared memory per warp), and each
+// field's last warp to finish combines the u[0,0] partials.
+constexpr int kTriRegG = 32;
+constexpr int kTriRegWarps = 8;
+static __global__ void __launch_bounds__(32 * kTriRegWarps) k_tri_carries_reg(float2* __restrict__ spec,
+                                                                           float2* __restrict__ tri,
+                                                                           const float* __restrict__ cc,
+                                                                           double* __restrict__ partial, FastArgs A,
+                                                                           int nkb) {
+  extern __shared__ __align__(16) float fcols[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int task = blockIdx.x * kTriRegWarps + warp;
+  if (task >= A.nf * nkb) return;
+  const int field = task / nkb, kb = task - field * nkb;
+  const int k = kb * kTriCols + lane;
+  const bool col_ok = k >= 1 && k < A.Nh;
+  const int G = A.G;
+  const float2* sums = tri_sums(tri, field, A) + (size_t)kb * 2 * G * kTriCols + lane;  // [g][2][32]
+  float2* carry = tri + (size_t)field * A.tri_field + k;                                 // [g][2][ldY]
+  double acc = 0.0;
+  if (col_ok) {
+    const float4 c03 = __ldg(reinterpret_cast<const float4*>(cc + (size_t)k * 8));
+    const float4 c47 = __ldg(reinterpret_cast<const float4*>(cc + (size_t)k * 8) + 1);
+    const float a = c03.y, C = c03.z, Tb = c03.w, Tl = c47.x, Tp = c47.y, inv = c47.z, Tt = c47.w;
+    float2 yl, y0;
+    {  // causal: the band sums in registers, from a zero carry, close the cycle, carries out
+      float2 e[kTriRegG];
+#pragma unroll
+      for (int g = 0; g < kTriRegG; ++g)
+        if (g < G) e[g] = sums[(size_t)g * 2 * kTriCols];
+      float2 t = make_float2(0.0f, 0.0f);
+#pragma unroll
+      for (int g = 0; g < kTriRegG; ++g)
+        if (g < G) {
+          const float T = (g == G - 1) ? Tl : Tb;
+          t = __ffma2_rn(make_float2(T, T), t, e[g]);
+        }
+      yl = make_float2(Tt * t.x * inv, Tt * t.y * inv);  // y[M-1]
+      float2 c = make_float2(Tp * yl.x, Tp * yl.y);     // carry into band 0
+#pragma unroll
+      for (int g = 0; g < kTriRegG; ++g)
+        if (g < G) {
+          const float T = (g == G - 1) ? Tl : Tb;
+          carry[(size_t)(2 * g) * A.ldY] = c;
+          c = __ffma2_rn(make_float2(T, T), c, e[g]);
+        }
+    }
+    {  // anticausal, the same way up the bands
+      float2 ep[kTriRegG];
+#pragma unroll
+      for (int g = 0; g < kTriRegG; ++g)
+        if (g < G) ep[g] = sums[(size_t)g * 2 * kTriCols + kTriCols];
+      float2 q = make_float2(0.0f, 0.0f);
+#pragma unroll
+      for (int g = kTriRegG - 1; g >= 0; --g)
+        if (g < G) {
+          const float T = (g == G - 1) ? Tl : Tb;
+          q = __ffma2_rn(make_float2(T, T), q, ep[g]);
+        }
+      y0 = make_float2(Tp * q.x * inv, Tp * q.y * inv);  // y'[0]
+      float2 c = make_float2(Tt * y0.x, Tt * y0.y);     // carry from below the last band
+#pragma unroll
+      for (int g = kTriRegG - 1; g >= 0; --g)
+        if (g < G) {
+          const float T = (g == G - 1) ? Tl : Tb;
+          carry[(size_t)(2 * g + 1) * A.ldY] = c;
+          c = __ffma2_rn(make_float2(T, T), c, ep[g]);
+        }
+    }
+    acc = (2 * k == A.N ? 1.0 : 2.0) * (double)(C * fmaf(a, yl.x, y0.x));
+  }
+  acc = warp_sum_d(acc);
+  double* pp = partial + (size_t)field * (kMaxRowBlocks / 2);
+  if (kb == 0) {  // column 0, from the compact copy of S's column 0
+    float* fcol = fcols + (size_t)warp * (A.M + 4);
+    const int nr = min(A.srows, A.M - A.p);
+    const float* c0 = tri_col0(tri, field, A);
+    for (int i = lane; i < nr; i += 32) fcol[A.p + i] = c0[i];
+    __syncwarp();
+    tri_column0(spec, fcol, field, A);
+  }
+  unsigned done = 0;
+  if (lane == 0) {
+    pp[kb] = acc;
+    __threadfence();  // this partial is visible before the count says so
+    done = atomicAdd(reinterpret_cast<unsigned*>(pp + kTriCnt), 1u);
+  }
+  done = __shfl_sync(0xffffffffu, done, 0);
+  if (done == (unsigned)nkb - 1) {
+    // the field's last warp: u[0,0] from every column block's partial,
+    // lane-strided then a fixed shuffle tree (the same order on every call)
+    __threadfence();
+    double s2 = 0.0;
+    for (int i = lane; i < nkb; i += 32) s2 += __ldcg(pp + i);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s2 += __shfl_down_sync(0xffffffffu, s2, o);
+    if (lane == 0) pp[kTriU00] = s2;
   }
 }
 
@@ -1502,7 +1611,7 @@ __global__ void __launch_bounds__(S::THREADS, S::MINB_INV) k_fast_rows_inv(const
     __syncthreads();  // every staged row read: buf becomes the exchange buffer
     if (act) {
 #pragma unroll
-      for (int s2 = 0; s2 < S::R1; ++s2) mybuf[t * (S::R1 + 1) + s2] = v[s2];
+      for (int s2 = 0; s2 < S::R1; ++s2) mybuf[t * S::R1P + s2] = v[s2];
     }
     __syncthreads();
     const bool act2 = act && t < S::JSPAN;
@@ -1530,7 +1639,7 @@ __global__ void __launch_bounds__(S::THREADS, S::MINB_INV) k_fast_rows_inv(const
       if (act2) {
         u[0] = mybuf[j];
 #pragma unroll
-        for (int r = 1; r < S::R2; ++r) u[r] = cmul(mybuf[j + (S::R1 + 1) * r], cconj(tw2[j * S::R2 + r]));
+        for (int r = 1; r < S::R2; ++r) u[r] = cmul(mybuf[j + S::R1P * r], cconj(tw2[j * S::R2 + r]));
       }
       if (jj == S::J2 - 1) {
         if (stage) {
@@ -1776,7 +1885,7 @@ __global__ void __launch_bounds__(S::THREADS, S::MINB_ADJ) k_fast_rows_adj(const
     if (act) {
       dft_reg<S::R1, +1>(v);
 #pragma unroll
-      for (int s2 = 0; s2 < S::R1; ++s2) mybuf[t * (S::R1 + 1) + s2] = v[s2];
+      for (int s2 = 0; s2 < S::R1; ++s2) mybuf[t * S::R1P + s2] = v[s2];
     }
     __syncthreads();
     if (act && t < S::JSPAN && vi) {
@@ -1788,7 +1897,7 @@ __global__ void __launch_bounds__(S::THREADS, S::MINB_ADJ) k_fast_rows_adj(const
         float2 u[S::R2];
         u[0] = mybuf[j];
 #pragma unroll
-        for (int r = 1; r < S::R2; ++r) u[r] = cmul(mybuf[j + (S::R1 + 1) * r], cconj(tw2[j * S::R2 + r]));
+        for (int r = 1; r < S::R2; ++r) u[r] = cmul(mybuf[j + S::R1P * r], cconj(tw2[j * S::R2 + r]));
         dft_reg<S::R2, +1>(u);
 #pragma unroll
         for (int s2 = 0; s2 < S::R2; ++s2) {
@@ -1854,6 +1963,8 @@ static cudaError_t run_fast_mode(gfc_plan* P, const Bufs& bf, const T* in0, cons
   if (!kCols && !tri) return cudaErrorNotSupported;
   FastArgs A;
   A.stage_out = 0;
+  A.invM = 1.0 / (double)P->M;
+  A.invN = 1.0 / (double)P->N;
   A.H = P->H; A.W = P->W; A.p = P->pad; A.M = P->M; A.N = P->N; A.Nh = P->Nh; A.ldM = P->ldM;
   A.nrows = (MODE == 0) ? P->H + 1 : P->H;
   A.ncols = (MODE == 0) ? P->W + 1 : P->W;
@@ -1988,7 +2099,12 @@ static cudaError_t run_fast_mode(gfc_plan* P, const Bufs& bf, const T* in0, cons
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   prof_begin(P, 1, st);
   const int nkb = (P->Nh + kTriCols - 1) / kTriCols;  // column blocks of the sweep (u[0,0] partials)
-  if (tri) {
+  if (tri && A.G <= kTriRegG && (size_t)kTriRegWarps * (P->M + 4) * sizeof(float) <= 48 * 1024) {
+    const int tasks = nf * nkb;
+    k_tri_carries_reg<<<(tasks + kTriRegWarps - 1) / kTriRegWarps, 32 * kTriRegWarps,
+                        (size_t)kTriRegWarps * (P->M + 4) * sizeof(float), st>>>(
+        bf.spec, bf.tri, P->colcoef, reinterpret_cast<double*>(bf.partial), A, nkb);
+  } else if (tri) {
     const size_t tsm = A.G <= kTriTileMaxG ? (size_t)2 * A.G * kTriCols * sizeof(float2) : 0;
     k_tri_carries<<<dim3(nkb, nf), 32 * (kTriSeg + 1), tsm, st>>>(bf.spec, bf.tri, P->colcoef, P->powc,
                                                                    reinterpret_cast<double*>(bf.partial), A);
