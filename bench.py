@@ -708,8 +708,9 @@ def _backward_workload(dev, samples):
     peak, kind = _peaks()
     min_bytes = 3 * 4 * H * W * B + 4 * p.M * (p.N // 2 + 1)
     gbs = min_bytes / (ms_b / 1000.0) / 1e9
-    names = ["row pass (grad_out packing folded in)", "sum(grad_out) + column pass",
-             "inverse row pass (grad_gx, grad_gy)"]
+    names = ["row pass (grad_out packing folded in, half-band sums)",
+             "sum(grad_out) + half-band carry sweep (recursive column solve)",
+             "inverse row pass (half-band solve, grad_gx, grad_gy)"]
     passes = [{"pass": names[i], "ms": prof["pass_ms"][i] / reps, "launches_per_call": prof["launches"][i] / reps}
               for i in range(3)]
     return {"ms_forward": ms_f, "ms_backward": ms_b, "fwd_bwd_solves_per_s": B * 1000.0 / (ms_f + ms_b),

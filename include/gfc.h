@@ -82,8 +82,12 @@ typedef enum { GFC_SIZE_SMOOTH = 0, GFC_SIZE_EXACT = 1 } gfc_size_policy;
  * (bands of rows with carries swept around the cycle; column l = 0, where the
  * operator is singular, is solved exactly with its mean removed, the reading
  * G[0,0] = 0). Same operator as the column FFTs, O(M) per column instead of
- * two length-M transforms, no spectrum transpose. Used by solves and edited
- * solves; gfc_backward runs the column transforms.
+ * two length-M transforms, no spectrum transpose. Used by solves, edited
+ * solves and gfc_backward (which sweeps half-bands of rows so its inverse row
+ * pass can produce one band of output rows per item; the -(sum grad_out) e_00
+ * term enters the sweep and column 0 at torus row 0). Where the adjoint's
+ * grad_out rows cannot be bulk-copied (W x element size not a multiple of 16
+ * bytes) it runs the column transforms instead.
  * GFC_COLUMN_FFT: column FFT, multiply by G, inverse column FFT. */
 typedef enum { GFC_COLUMN_RECURSIVE = 0, GFC_COLUMN_FFT = 1 } gfc_column_solver;
 

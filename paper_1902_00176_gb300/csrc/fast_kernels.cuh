@@ -74,6 +74,7 @@ struct FastArgs {
   size_t tri_field;  // complex elements per field of the band scratch
   int stage_out;     // inverse row pass: output rows staged in shared memory, stored by bulk copy
   double invM, invN; // 1 / M, 1 / N (FP64 divisions are slow on this part)
+  int adj;           // the recursive column solve runs the adjoint (half-bands, the sum term at row 0)
 };
 
 // Band scratch of one field (recursive column solve), complex elements:
@@ -179,6 +180,8 @@ struct RowShape {
     return (((size_t)(R1 * R2 + F * NP + (N / 2 + 1)) * sizeof(float2)) + 15) / 16 * 16;
   }
   static constexpr size_t smem_bytes_adj() { return adj_stage_offset() + (size_t)(F + 1) * LDY * sizeof(float2); }
+  // the recursive column solve's adjoint also stages the half-band's two carries
+  static constexpr size_t smem_bytes_adj_tri() { return adj_stage_offset() + (size_t)(F + 3) * LDY * sizeof(float2); }
   // The exchange stores each run of R1 elements at a stride of R1P (element
   // m = t R1 + s at t R1P + s, conflict-free stage-1 writes); the kernels use
   // the closed forms t R1P + s for m = t R1 + s and j + R1P r for m = j + R1 r.
@@ -445,7 +448,10 @@ __global__ void __launch_bounds__(512) k_fast_div_edit(const T* __restrict__ gx,
 // over the nb band rows that lie on the torus. Thread t takes columns t, t +
 // blockDim, ...: the row stores and sums are coalesced across threads.
 // ---------------------------------------------------------------------------
-template <class S>
+// HALF (the adjoint): the sums are taken per half-band of F rows (half-bands
+// 2g and 2g + 1; A.G counts half-bands), so that the inverse pass can solve F
+// rows at a time.
+template <class S, bool HALF = false>
 __device__ __forceinline__ void tri_store_item(const float2* buf2, float2* __restrict__ spec, float2* __restrict__ tri,
                                                const float* __restrict__ cc, int field, int g, const FastArgs& A) {
   constexpr int RW = 2 * S::F;
@@ -474,15 +480,32 @@ __device__ __forceinline__ void tri_store_item(const float2* buf2, float2* __res
       for (int r = 0; r < RW; ++r) c0[r] = x[r].x;
     }
     const float dl = __ldg(cc + (size_t)k * 8);
-    float2 e = make_float2(0.0f, 0.0f), ep = make_float2(0.0f, 0.0f);
+    if constexpr (HALF) {
 #pragma unroll
-    for (int r = 0; r < RW; ++r)
-      if (r < nb) e = tri_step(x[r], e, dl);
+      for (int h = 0; h < 2; ++h) {
+        if (h * S::F >= nb) break;  // the second half lies past the torus
+        float2 e = make_float2(0.0f, 0.0f), ep = make_float2(0.0f, 0.0f);
 #pragma unroll
-    for (int r = RW - 1; r >= 0; --r)
-      if (r < nb) ep = tri_step(x[r], ep, dl);
-    *te = e;
-    *tp = ep;
+        for (int r = h * S::F; r < (h + 1) * S::F; ++r)
+          if (r < nb) e = tri_step(x[r], e, dl);
+#pragma unroll
+        for (int r = (h + 1) * S::F - 1; r >= h * S::F; --r)
+          if (r < nb) ep = tri_step(x[r], ep, dl);
+        float2* th = sums + ((size_t)(k / kTriCols) * A.G + 2 * g + h) * 2 * kTriCols + (k % kTriCols);
+        th[0] = e;
+        th[kTriCols] = ep;
+      }
+    } else {
+      float2 e = make_float2(0.0f, 0.0f), ep = make_float2(0.0f, 0.0f);
+#pragma unroll
+      for (int r = 0; r < RW; ++r)
+        if (r < nb) e = tri_step(x[r], e, dl);
+#pragma unroll
+      for (int r = RW - 1; r >= 0; --r)
+        if (r < nb) ep = tri_step(x[r], ep, dl);
+      *te = e;
+      *tp = ep;
+    }
   }
 }
 
@@ -656,7 +679,6 @@ __global__ void __launch_bounds__(S::THREADS, S::MINB_FWD) k_fast_rows_fwd_div(c
                                                                      float2* __restrict__ tri,
                                                                      const float* __restrict__ cc,
                                                                      const float* __restrict__ t2s = nullptr) {
-  static_assert(!(ADJ && TRI), "the adjoint runs the column transforms");
   static_assert(EDIT == kEditNone || (EDIT == kEditThreshold && !ADJ), "only the threshold edit is staged");
   extern __shared__ __align__(16) float2 sm[];
   float2* tw2 = sm;
@@ -695,8 +717,9 @@ __global__ void __launch_bounds__(S::THREADS, S::MINB_FWD) k_fast_rows_fwd_div(c
       if (!ADJ) l2_prefetch(ys, (unsigned)(y1 - y0) * row);
       return;
     }
-    if constexpr (ADJ) {
-      bulk_load(sgx, xs, (unsigned)nx * row, &bar);  // nx >= 1 here
+    if constexpr (ADJ) {  // (with the recursive column solve the last band may hold no row of grad_out)
+      mbar_expect_tx(&bar, (unsigned)(nx > 0 ? nx : 0) * row);
+      if (nx > 0) bulk_copy(sgx, xs, (unsigned)nx * row, &bar);
     } else {
       mbar_expect_tx(&bar, (unsigned)(nx > 0 ? nx : 0) * row + (unsigned)(y1 - y0) * row);
       if (nx > 0) bulk_copy(sgx, xs, (unsigned)nx * row, &bar);
@@ -712,7 +735,7 @@ __global__ void __launch_bounds__(S::THREADS, S::MINB_FWD) k_fast_rows_fwd_div(c
 #pragma unroll 1
   for (int w = blockIdx.x; w < items; w += gridDim.x, phase ^= 1u) {
     const int field = w / A.ngroups, g = w - field * A.ngroups;
-    if (TRI && g == 0 && tid == 0)  // the sweep's count of finished blocks for this field starts at 0
+    if (TRI && !ADJ && g == 0 && tid == 0)  // the sweep's count of finished blocks for this field starts at 0
       reinterpret_cast<unsigned*>(reinterpret_cast<double*>(partial) + (size_t)field * (kMaxRowBlocks / 2) + kTriCnt)[0] = 0u;
     float gxa[EDIT == kEditThreshold ? kEdW : 1];
     if constexpr (EDIT == kEditThreshold) {
@@ -845,7 +868,7 @@ __global__ void __launch_bounds__(S::THREADS, S::MINB_FWD) k_fast_rows_fwd_div(c
     }
     __syncthreads();  // stage-2 results visible
     if constexpr (TRI) {
-      tri_store_item<S>(buf2, spec, tri, cc, field, g, A);
+      tri_store_item<S, ADJ>(buf2, spec, tri, cc, field, g, A);
     } else {
     if (g == 0) {
       float2* Sz = spec + (size_t)field * A.Nh * A.ldM;
@@ -954,12 +977,13 @@ __device__ __forceinline__ double warp_exclusive_scan_d(double v) {
 // i (bulk copy of pass A's compact copy); each lane walks a contiguous run of
 // torus rows; the solution (1/N folded in) replaces column 0 of S.
 static __device__ __noinline__ void tri_column0(float2* __restrict__ spec, float* fcol, int field,
-                                                const FastArgs& A) {
+                                                const FastArgs& A, float x0) {
   const int lane = threadIdx.x & 31;
   float2* col = spec + (size_t)field * A.srows * A.ldY;
   const int nr = min(A.srows, A.M - A.p);  // S rows on the torus
   for (int r = lane; r < A.M; r += 32)
     if (r < A.p || r >= A.p + nr) fcol[r] = 0.0f;
+  if (lane == 0) fcol[0] = x0;  // torus row 0 (the adjoint's -(sum grad_out) e_00; else 0)
   __syncwarp();
   const int run = (A.M + 31) / 32;
   const int r0 = min(lane * run, A.M), r1 = min(r0 + run, A.M);
@@ -998,6 +1022,8 @@ static __global__ void __launch_bounds__(32 * (kTriSeg + 1)) k_tri_carries(float
   const int kb = blockIdx.x, field = blockIdx.y, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int k = kb * kTriCols + lane;
   const bool col_ok = k >= 1 && k < A.Nh;
+  // the adjoint's z has -(sum grad_out) at torus (0, 0): -s in every column of row 0
+  const float sadj = A.adj ? (float)partial[(size_t)field * (kMaxRowBlocks / 2) + kAdjTotal] : 0.0f;
   const float2* gsums = tri_sums(tri, field, A) + (size_t)kb * 2 * A.G * kTriCols;  // [g][2][32], contiguous
   const bool staged = A.G <= kTriTileMaxG;
   const float2* sums = (staged ? tile : gsums) + lane;
@@ -1074,6 +1100,7 @@ static __global__ void __launch_bounds__(32 * (kTriSeg + 1)) k_tri_carries(float
       }
       const float2 yl = make_float2(Tt * t.x * inv, Tt * t.y * inv);  // y[M-1]
       float2 c = make_float2(Tp * yl.x, Tp * yl.y);                   // y[p-1]: carry into band 0
+      if (A.adj) c.x -= (Tp / a) * sadj * inv;  // row 0's -s, carried a^(p-1) down
 #pragma unroll
       for (int s = 0; s < kTriSeg; ++s) {
         const float T = seg_T(s);
@@ -1090,7 +1117,8 @@ static __global__ void __launch_bounds__(32 * (kTriSeg + 1)) k_tri_carries(float
         const float2 e = seg_q[s][lane];
         q = make_float2(fmaf(T, q.x, e.x), fmaf(T, q.y, e.y));
       }
-      const float2 y0 = make_float2(Tp * q.x * inv, Tp * q.y * inv);  // y'[0]
+      float2 y0 = make_float2(Tp * q.x * inv, Tp * q.y * inv);  // y'[0]
+      if (A.adj) y0.x = (Tp * q.x - sadj) * inv;
       float2 c = make_float2(Tt * y0.x, Tt * y0.y);                   // carry from below the last band
 #pragma unroll
       for (int s = kTriSeg - 1; s >= 0; --s) {
@@ -1122,7 +1150,7 @@ static __global__ void __launch_bounds__(32 * (kTriSeg + 1)) k_tri_carries(float
       q = __ffma2_rn(make_float2(T, T), q, e);
     }
   }
-  if (warp == 0) {
+  if (warp == 0 && !A.adj) {  // u[0,0] (the adjoint has no offset)
     double acc = 0.0;
     if (col_ok) acc = (2 * k == A.N ? 1.0 : 2.0) * (double)(C * fmaf(a, yls[lane], y0s[lane].x));
     acc = warp_sum_d(acc);
@@ -1152,7 +1180,7 @@ static __global__ void __launch_bounds__(32 * (kTriSeg + 1)) k_tri_carries(float
       mbar_wait(&bar, 0);
       return;
     }
-    tri_column0(spec, fcol, field, A);
+    tri_column0(spec, fcol, field, A, -sadj);
   }
 }
 
@@ -1165,7 +1193,7 @@ static __global__ void __launch_bounds__(32 * (kTriSeg + 1)) k_tri_carries(float
 // field's last warp to finish combines the u[0,0] partials.
 constexpr int kTriRegG = 32;
 constexpr int kTriRegWarps = 8;
-static __global__ void __launch_bounds__(32 * kTriRegWarps) k_tri_carries_reg(float2* __restrict__ spec,
+static __global__ void __launch_bounds__(32 * kTriRegWarps, 2) k_tri_carries_reg(float2* __restrict__ spec,
                                                                            float2* __restrict__ tri,
                                                                            const float* __restrict__ cc,
                                                                            double* __restrict__ partial, FastArgs A,
@@ -1178,6 +1206,8 @@ static __global__ void __launch_bounds__(32 * kTriRegWarps) k_tri_carries_reg(fl
   const int k = kb * kTriCols + lane;
   const bool col_ok = k >= 1 && k < A.Nh;
   const int G = A.G;
+  // the adjoint's z has -(sum grad_out) at torus (0, 0): -s in every column of row 0
+  const float sadj = A.adj ? (float)partial[(size_t)field * (kMaxRowBlocks / 2) + kAdjTotal] : 0.0f;
   const float2* sums = tri_sums(tri, field, A) + (size_t)kb * 2 * G * kTriCols + lane;  // [g][2][32]
   float2* carry = tri + (size_t)field * A.tri_field + k;                                 // [g][2][ldY]
   double acc = 0.0;
@@ -1200,6 +1230,7 @@ static __global__ void __launch_bounds__(32 * kTriRegWarps) k_tri_carries_reg(fl
         }
       yl = make_float2(Tt * t.x * inv, Tt * t.y * inv);  // y[M-1]
       float2 c = make_float2(Tp * yl.x, Tp * yl.y);     // carry into band 0
+      if (A.adj) c.x -= (Tp / a) * sadj * inv;          // row 0's -s, carried a^(p-1) down
 #pragma unroll
       for (int g = 0; g < kTriRegG; ++g)
         if (g < G) {
@@ -1221,6 +1252,7 @@ static __global__ void __launch_bounds__(32 * kTriRegWarps) k_tri_carries_reg(fl
           q = __ffma2_rn(make_float2(T, T), q, ep[g]);
         }
       y0 = make_float2(Tp * q.x * inv, Tp * q.y * inv);  // y'[0]
+      if (A.adj) y0.x = (Tp * q.x - sadj) * inv;
       float2 c = make_float2(Tt * y0.x, Tt * y0.y);     // carry from below the last band
 #pragma unroll
       for (int g = kTriRegG - 1; g >= 0; --g)
@@ -1240,8 +1272,9 @@ static __global__ void __launch_bounds__(32 * kTriRegWarps) k_tri_carries_reg(fl
     const float* c0 = tri_col0(tri, field, A);
     for (int i = lane; i < nr; i += 32) fcol[A.p + i] = c0[i];
     __syncwarp();
-    tri_column0(spec, fcol, field, A);
+    tri_column0(spec, fcol, field, A, -sadj);
   }
+  if (A.adj) return;  // u[0,0]: the adjoint has no offset
   unsigned done = 0;
   if (lane == 0) {
     pp[kb] = acc;
@@ -1431,8 +1464,7 @@ __device__ __forceinline__ void tri_solve_band(float2* buf, const float2* cbuf, 
           col[(size_t)r * S::LDY] = cscale(csub(cadd(col[(size_t)r * S::LDY], ya), x[r]), dc.y);
         }
     }
-    return;
-  }
+  } else {
   // thread t takes the column pair (2j, 2j + 1), 16-byte shared-memory accesses;
   // column 0 (already solved) and columns >= Nh pass through unchanged
   for (int j = threadIdx.x; 2 * j < A.Nh; j += blockDim.x) {
@@ -1471,6 +1503,7 @@ __device__ __forceinline__ void tri_solve_band(float2* buf, const float2* cbuf, 
         }
         col[(size_t)r * (S::LDY / 2)] = u;
       }
+  }
   }
 }
 
@@ -1802,15 +1835,59 @@ __global__ void __launch_bounds__(256) k_fast_color_apply(T* __restrict__ out, c
 // Both spectra are Hermitian, so one complex inverse transform of
 // A + i B gives grad_gx in its real part and grad_gy in its imaginary part.
 // ---------------------------------------------------------------------------
-template <class S, typename T>
+// Recursive column solve, the adjoint's inverse pass side: the F staged rows of
+// half-band g of S (and row F, the next half-band's first row) become rows of
+// the solved spectrum U in place, from the half-band's two carries, one column
+// per thread: the causal recursion down the half-band, row F from the causal
+// value above it and the anticausal carry (which is y' at row F), then the
+// anticausal recursion up, U = C_l (y + y' - X). Column 0 already holds its
+// exact solution; rows past the torus are left alone (no output row needs them).
+template <class S>
+__device__ __forceinline__ void tri_solve_half(float2* stg, const float2* cbuf, const float* __restrict__ cc, int g,
+                                               const FastArgs& A) {
+  constexpr int F = S::F;
+  const int nb = min(F, A.M - A.p - g * F);
+  const bool extra = nb == F && g * F + F < A.srows;
+  const float2* dcs = reinterpret_cast<const float2*>(cc + (size_t)A.Nh * 8);  // (delta, C) per column
+  for (int k = 1 + threadIdx.x; k < A.Nh; k += blockDim.x) {
+    const float2 dc = __ldg(dcs + k);
+    float2 yc = cbuf[k], ya = cbuf[S::LDY + k];
+    float2* col = stg + k;
+    float2 x[F + 1];
+#pragma unroll
+    for (int r = 0; r < F; ++r) x[r] = col[(size_t)r * S::LDY];
+    x[F] = extra ? col[(size_t)F * S::LDY] : make_float2(0.0f, 0.0f);
+#pragma unroll
+    for (int r = 0; r < F; ++r)
+      if (r < nb) {
+        yc = tri_step(x[r], yc, dc.x);
+        col[(size_t)r * S::LDY] = yc;
+      }
+    if (extra) col[(size_t)F * S::LDY] = cscale(csub(cadd(tri_step(x[F], yc, dc.x), ya), x[F]), dc.y);
+#pragma unroll
+    for (int r = F - 1; r >= 0; --r)
+      if (r < nb) {
+        ya = tri_step(x[r], ya, dc.x);
+        col[(size_t)r * S::LDY] = cscale(csub(cadd(col[(size_t)r * S::LDY], ya), x[r]), dc.y);
+      }
+  }
+}
+
+// TRI: the recursive column solve's adjoint; Y is then the row-major spectrum
+// S of Crop^T(grad_out) (srows rows per field), an item is half-band g (output
+// rows gF .. gF + F - 1), whose F + 1 rows of S and two carries arrive by bulk
+// copy and are solved in place (tri_solve_half) before the output transforms.
+template <class S, typename T, bool TRI = false>
 __global__ void __launch_bounds__(S::THREADS, S::MINB_ADJ) k_fast_rows_adj(const float2* __restrict__ Y, T* __restrict__ ggx,
                                                                  T* __restrict__ ggy, const float2* __restrict__ twg,
-                                                                 FastArgs A) {
+                                                                 FastArgs A, const float2* __restrict__ tri = nullptr,
+                                                                 const float* __restrict__ cc = nullptr) {
   extern __shared__ __align__(16) float2 sm[];
   float2* tw2 = sm;                          // [R1][R2]: w_N^(r j)
   float2* buf = sm + S::R1 * S::R2;          // [F][NP] exchange
   float2* dtab = buf + S::F * S::NP;         // [N/2 + 1] 1 - exp(2 pi i l / N)
   float2* stg = reinterpret_cast<float2*>(reinterpret_cast<char*>(sm) + S::adj_stage_offset());  // [F + 1][ldY]
+  float2* cbuf = stg + (size_t)(S::F + 1) * S::LDY;  // TRI: the half-band's carries [2][LDY]
   __shared__ __align__(8) uint64_t bar;
   const int tid = threadIdx.x;
   const int f = tid / S::T, t = tid - f * S::T;
@@ -1833,7 +1910,23 @@ __global__ void __launch_bounds__(S::THREADS, S::MINB_ADJ) k_fast_rows_adj(const
   // only start fetching them into L2, for the copy one item later
   auto issue = [&](int w, bool prefetch) {
     const int field = w / A.ngroups, g = w - field * A.ngroups;
-    const int r0 = g * S::F, nr = (A.H + 1 - r0) < S::F + 1 ? (A.H + 1 - r0) : S::F + 1;
+    const int r0 = g * S::F;
+    if constexpr (TRI) {
+      const int nr = (A.srows - r0) < S::F + 1 ? (A.srows - r0) : S::F + 1;
+      const float2* ys = Y + ((size_t)field * A.srows + r0) * A.ldY;
+      const float2* cs = tri + (size_t)field * A.tri_field + (size_t)g * 2 * A.ldY;
+      const unsigned nb = (unsigned)(nr * A.ldY * sizeof(float2)), cb = (unsigned)(2 * A.ldY * sizeof(float2));
+      if (prefetch) {
+        l2_prefetch(ys, nb);
+        l2_prefetch(cs, cb);
+      } else {
+        mbar_expect_tx(&bar, nb + cb);
+        bulk_copy(stg, ys, nb, &bar);
+        bulk_copy(cbuf, cs, cb, &bar);
+      }
+      return;
+    }
+    const int nr = (A.H + 1 - r0) < S::F + 1 ? (A.H + 1 - r0) : S::F + 1;
     const float2* ys = Y + ((size_t)field * (A.H + 1) + r0) * A.ldY;
     const unsigned nb = (unsigned)(nr * A.ldY * sizeof(float2));
     if (prefetch)
@@ -1852,6 +1945,15 @@ __global__ void __launch_bounds__(S::THREADS, S::MINB_ADJ) k_fast_rows_adj(const
     const int i = g * S::F + f;  // output row of this transform
     const bool vi = act && i < A.H;
     const bool landed = mbar_wait(&bar, phase);
+    if constexpr (TRI) {
+      if (__syncthreads_or(!landed)) {  // the copies never completed: report, let them drain, stop
+        if (tid == 0) atomicExch(A.err, kErrBulkWait);
+        mbar_wait(&bar, phase);
+        return;
+      }
+      tri_solve_half<S>(stg, cbuf, cc, g, A);
+      __syncthreads();
+    }
     const float2* y0 = stg + (size_t)(vi ? f : 0) * A.ldY;
     const float2* y1 = y0 + A.ldY;  // row i + 1 (Y holds H + 1 rows)
     float2 v[S::R1];
@@ -1948,6 +2050,96 @@ static cudaError_t fast_setup(K kernel, int threads, size_t smem, int* slots) {
   return cudaSuccess;
 }
 
+// The adjoint on a plan with the recursive column solve (reading: the
+// transpose of the solve, z = Crop^T(grad_out) - (sum grad_out) e_00 through
+// the same Green operator, then the forward differences' transposes): the
+// forward row pass packs grad_out into z's rows (row-pair sums for the e_00
+// term) and stores S with half-band sums; one warp per field reduces the sum;
+// the carry sweep runs over the half-bands with -sum at torus row 0; the
+// adjoint's inverse row pass solves each half-band in shared memory and writes
+// grad_gx, grad_gy. Needs grad_out rows that can be bulk-copied into the
+// forward pass's staging; returns cudaErrorNotSupported otherwise.
+template <class RS, typename T>
+static cudaError_t run_fast_adj_tri(gfc_plan* P, const Bufs& bf, const T* gout, T* ggx, T* ggy, int nf,
+                                    cudaStream_t st) {
+  if ((P->W * sizeof(T)) % 16 != 0 || (size_t)2 * RS::F * P->W * sizeof(T) > fused_exchange_bytes<RS>() ||
+      getenv("GFC_UNFUSED_DIV") != nullptr)
+    return cudaErrorNotSupported;
+  FastArgs A;
+  A.stage_out = 0;
+  A.invM = 1.0 / (double)P->M;
+  A.invN = 1.0 / (double)P->N;
+  A.adj = 1;
+  A.H = P->H; A.W = P->W; A.p = P->pad; A.M = P->M; A.N = P->N; A.Nh = P->Nh; A.ldM = P->ldM;
+  A.nrows = P->H;
+  A.ncols = P->W;
+  A.npairs = (A.nrows + 1) / 2;
+  A.ldz = (RS::N + 3) & ~3;
+  A.ngroups = P->triG;  // the forward pass's items: the bands of 2F rows
+  A.zpairs = A.ngroups * RS::F;
+  A.nparts = 0;
+  A.nf = nf;
+  A.ldY = (P->Nh + 3) & ~3;
+  A.err = P->dev_err;
+  A.srows = 2 * A.zpairs;
+  A.G = P->triGh;       // the sweep's half-bands of F rows
+  A.tri_field = P->tri_field;
+  const int nkb = (P->Nh + kTriCols - 1) / kTriCols;
+  if ((size_t)2 * RS::F * A.ldY > (size_t)RS::F * RS::NP || A.zpairs > kAdjTotal ||
+      (size_t)A.srows * A.ldY > P->spec_field || nkb > kTriCnt || P->M > kTriMaxM)
+    return cudaErrorInvalidConfiguration;
+  static std::mutex mu;
+  static int slots_a = 0, slots_c = 0;
+  cudaError_t e;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    static bool ready = false;
+    if (!ready) {
+      int unused = 0;
+      if ((e = fast_setup(k_fast_rows_fwd_div<RS, T, true, true>, RS::THREADS, RS::smem_bytes_fwd(), &slots_a)) !=
+          cudaSuccess)
+        return e;
+      if ((e = fast_setup(k_fast_rows_adj<RS, T, true>, RS::THREADS, RS::smem_bytes_adj_tri(), &slots_c)) !=
+          cudaSuccess)
+        return e;
+      if ((e = fast_setup(k_tri_carries, 32 * (kTriSeg + 1), (size_t)2 * kTriTileMaxG * kTriCols * sizeof(float2),
+                          &unused)) != cudaSuccess)
+        return e;
+      ready = true;
+    }
+  }
+  const bool one = P->block_items;
+  auto grid_for = [one](long items, int slots) { return (int)((one || items < slots) ? items : slots); };
+  prof_begin(P, 0, st);
+  k_fast_rows_fwd_div<RS, T, true, true><<<grid_for((long)nf * A.ngroups, slots_a), RS::THREADS,
+                                           RS::smem_bytes_fwd(), st>>>(gout, nullptr, bf.spec, P->twN, bf.partial, A,
+                                                                       bf.tri, P->colcoef_h);
+  prof_end(P, st);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  prof_begin(P, 1, st);
+  double* pd = reinterpret_cast<double*>(bf.partial);
+  k_adj_total<<<nf, 32, 0, st>>>(pd, A.zpairs);
+  P->prof.launches[1] += 1;  // a second launch in this pass
+  if (A.G <= kTriRegG && (size_t)kTriRegWarps * (P->M + 4) * sizeof(float) <= 48 * 1024) {
+    const int tasks = nf * nkb;
+    k_tri_carries_reg<<<(tasks + kTriRegWarps - 1) / kTriRegWarps, 32 * kTriRegWarps,
+                        (size_t)kTriRegWarps * (P->M + 4) * sizeof(float), st>>>(bf.spec, bf.tri, P->colcoef_h, pd, A,
+                                                                                nkb);
+  } else {
+    const size_t tsm = A.G <= kTriTileMaxG ? (size_t)2 * A.G * kTriCols * sizeof(float2) : 0;
+    k_tri_carries<<<dim3(nkb, nf), 32 * (kTriSeg + 1), tsm, st>>>(bf.spec, bf.tri, P->colcoef_h, P->powc_h, pd, A);
+  }
+  prof_end(P, st);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  FastArgs C = A;
+  C.ngroups = (P->H + RS::F - 1) / RS::F;  // half-bands holding output rows
+  prof_begin(P, 2, st);
+  k_fast_rows_adj<RS, T, true><<<grid_for((long)nf * C.ngroups, slots_c), RS::THREADS, RS::smem_bytes_adj_tri(),
+                                 st>>>(bf.spec, ggx, ggy, P->twN, C, bf.tri, P->colcoef_h);
+  prof_end(P, st);
+  return cudaGetLastError();
+}
+
 // MODE 0: solve from gradient, 1: from Laplacian, 2: adjoint (in0 = grad_out,
 // out0 = grad_gx, out1 = grad_gy). Solves (modes 0 and 1) on a plan with the
 // recursive column solve run pass A, the carry sweep and pass C; otherwise
@@ -1957,7 +2149,12 @@ static cudaError_t run_fast_mode(gfc_plan* P, const Bufs& bf, const T* in0, cons
                                  cudaStream_t st, const EditArgs* ed = nullptr) {
   constexpr bool kCols = !std::is_same_v<CS, NoCols>;  // column transforms compiled for this shape
   static_assert(!kCols || RS::N <= 2048, "the adjoint packing pass covers a whole row in one block");
-  static_assert(kCols || MODE != 2, "the adjoint runs the column transforms");
+  if constexpr (MODE == 2) {
+    if (P->tri) {  // the adjoint by the recursive column solve where its staging fits
+      const cudaError_t ea = run_fast_adj_tri<RS, T>(P, bf, in0, out0, out1, nf, st);
+      if (ea != cudaErrorNotSupported || !kCols) return ea;
+    }
+  }
   constexpr bool kTriMode = MODE != 2;
   const bool tri = kTriMode && P->tri;
   if (!kCols && !tri) return cudaErrorNotSupported;
@@ -1965,6 +2162,7 @@ static cudaError_t run_fast_mode(gfc_plan* P, const Bufs& bf, const T* in0, cons
   A.stage_out = 0;
   A.invM = 1.0 / (double)P->M;
   A.invN = 1.0 / (double)P->N;
+  A.adj = 0;
   A.H = P->H; A.W = P->W; A.p = P->pad; A.M = P->M; A.N = P->N; A.Nh = P->Nh; A.ldM = P->ldM;
   A.nrows = (MODE == 0) ? P->H + 1 : P->H;
   A.ncols = (MODE == 0) ? P->W + 1 : P->W;
@@ -2174,12 +2372,13 @@ static cudaError_t run_fast_mode(gfc_plan* P, const Bufs& bf, const T* in0, cons
 template <class RS>
 cudaError_t run_rows_shape(gfc_plan* P, const Bufs& bf, int mode, const void* in0, const void* in1, void* out0,
                            void* out1, int nf, cudaStream_t st, const EditArgs* ed) {
-  if (P->dtype != GFC_F32 || mode == 2 || !P->tri) return cudaErrorNotSupported;
+  if (P->dtype != GFC_F32 || !P->tri) return cudaErrorNotSupported;
   const float* a = static_cast<const float*>(in0);
   const float* b = static_cast<const float*>(in1);
   float* o0 = static_cast<float*>(out0);
   float* o1 = static_cast<float*>(out1);
   if (mode == 0) return run_fast_mode<RS, NoCols, float, 0>(P, bf, a, b, o0, o1, nf, st, ed);
+  if (mode == 2) return run_fast_mode<RS, NoCols, float, 2>(P, bf, a, b, o0, o1, nf, st);
   return run_fast_mode<RS, NoCols, float, 1>(P, bf, a, b, o0, o1, nf, st);
 }
 

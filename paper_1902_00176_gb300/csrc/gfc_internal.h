@@ -88,6 +88,9 @@ struct gfc_plan {
   size_t tri_field;  // complex elements per field of the band scratch
   float* colcoef;    // [Nh][8] column coefficients of the recursive solve
   float* powc;       // [2 triG][ldS] carry weights of the bands
+  int triGh;         // half-bands of F rows (the adjoint's recursive column solve)
+  float* colcoef_h;  // colcoef and powc for the half-bands
+  float* powc_h;
   float2* tri_buf;   // [slots][chunk][tri_field] band scratch
   bool exact; // size policy EXACT: M = H + 2p, N = W + 2p (exact.cu)
   gfc::ExactDim ex_row, ex_col;  // EXACT: the length-N and length-M transforms

@@ -288,10 +288,15 @@ gfc_status gfc_plan_create_ex(gfc_plan** out, const gfc_plan_opts* o) {
   if (p->tri) {
     const int F = fast_row_items(M, N);
     p->triG = (((o->H + 2) / 2) + F - 1) / F;
+    // the adjoint sweeps half-bands of F rows (those that start on the torus)
+    const int halves = (M - pad + F - 1) / F;
+    p->triGh = 2 * p->triG < halves ? 2 * p->triG : halves;
     // carries [G][2][ldS], band sums in 32-column tiles, column 0 of the 2 F G rows
-    // of S as floats; even, so every field's scratch stays 16-byte aligned
+    // of S as floats (G: bands, or half-bands for the adjoint, whichever is more);
+    // even, so every field's scratch stays 16-byte aligned
     const size_t nkb = (size_t)(p->ldS + 31) / 32;
-    p->tri_field = ((size_t)2 * p->triG * p->ldS + nkb * 2 * p->triG * 32 + (size_t)(2 * F * p->triG + 1) / 2 + 1) &
+    const size_t gmax = p->triGh > p->triG ? p->triGh : p->triG;
+    p->tri_field = ((size_t)2 * gmax * p->ldS + nkb * 2 * gmax * 32 + (size_t)(2 * F * p->triG + 1) / 2 + 1) &
                    ~(size_t)1;
   }
   p->stream = (cudaStream_t)o->stream;
@@ -344,6 +349,9 @@ gfc_status gfc_plan_create_ex(gfc_plan** out, const gfc_plan_opts* o) {
   if (e == cudaSuccess) e = cudaMalloc(&p->edit_t2, (size_t)fields * sizeof(float));
   if (e == cudaSuccess && p->tri) e = cudaMalloc(&p->colcoef, ((size_t)p->Nh * 8 + 2 * (size_t)p->ldS) * sizeof(float));
   if (e == cudaSuccess && p->tri) e = cudaMalloc(&p->powc, (size_t)tri_power_rows(p->triG) * p->ldS * sizeof(float));
+  if (e == cudaSuccess && p->tri)
+    e = cudaMalloc(&p->colcoef_h, ((size_t)p->Nh * 8 + 2 * (size_t)p->ldS) * sizeof(float));
+  if (e == cudaSuccess && p->tri) e = cudaMalloc(&p->powc_h, (size_t)tri_power_rows(p->triGh) * p->ldS * sizeof(float));
   // (+64 bytes: the sweep's bulk copy of a field's column 0 rounds up to 16 bytes)
   if (e == cudaSuccess && p->tri) e = cudaMalloc(&p->tri_buf, p->tri_field * chunk * nslots * sizeof(float2) + 64);
   for (int sl = 0; sl < nslots && e == cudaSuccess; ++sl) {
@@ -361,6 +369,8 @@ gfc_status gfc_plan_create_ex(gfc_plan** out, const gfc_plan_opts* o) {
   if (e == cudaSuccess && p->fast_cols) e = build_green_t(p->GT, M, N, p->Nh, p->ldM, bs);
   if (e == cudaSuccess && p->tri)
     e = build_colcoef(p->colcoef, p->powc, M, N, p->Nh, p->ldS, pad, p->triG, 2 * fast_row_items(M, N), bs);
+  if (e == cudaSuccess && p->tri)
+    e = build_colcoef(p->colcoef_h, p->powc_h, M, N, p->Nh, p->ldS, pad, p->triGh, fast_row_items(M, N), bs);
   if (e == cudaSuccess && p->exact) e = exact_setup(p, bs);
   if (e == cudaSuccess) e = cudaStreamSynchronize(bs);
   if (bs) cudaStreamDestroy(bs);
@@ -706,6 +716,8 @@ static void destroy_plan(gfc_plan* p) {
   cudaFree(p->partial);
   cudaFree(p->edit_t2);
   cudaFree(p->colcoef);
+  cudaFree(p->colcoef_h);
+  cudaFree(p->powc_h);
   cudaFree(p->powc);
   cudaFree(p->tri_buf);
   exact_release(p);

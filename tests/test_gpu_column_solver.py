@@ -169,3 +169,59 @@ def test_random_sizes_on_the_row_length_family(H, W, monkeypatch):
     assert _rel(_np(by)[0, 0], ry) <= max(REL_F32, 3.0 * _rel(ty_, ry))
     p.close()
     q.close()
+
+
+# (H, W, dtype): the benchmark torus; 800 rows, whose last band holds no row of
+# grad_out (only the divergence's extra row); tail rows; 16-bit storage
+ADJ_CASES = [(801, 1200, torch.float32), (800, 1200, torch.float32), (795, 1199, torch.float32),
+             (256, 256, torch.bfloat16), (64, 96, torch.float16), (60, 100, torch.float32)]
+
+
+@pytest.mark.parametrize("H,W,dt", ADJ_CASES)
+def test_recursive_adjoint_matches_oracle_and_column_fft_adjoint(H, W, dt):
+    """The adjoint by the recursive column solve (half-band recursions, the
+    -(sum grad_out) e_00 term carried through the sweep and column 0) against
+    the FP64 oracle's adjoint and the column-FFT adjoint of the same torus."""
+    B = 2
+    rng = np.random.default_rng(9300 + H)
+    img = np.stack([synth.gaussian_image(rng, H, W, 16, max(2.0, H / 30), max(4.0, H / 4)) for _ in range(B)])
+    gout = (img - 0.3)[:, None].astype(np.float32)  # an image-like upstream gradient with a non-zero sum
+    tg = _dev(gout, dt)
+    rec = gfc.Plan(H, W, 1, B, dtype=dt, device=DEV)
+    fft = gfc.Plan(H, W, 1, B, dtype=dt, device=DEV, column_fft=True)
+    ax, ay = rec.backward(tg)
+    bx, by = fft.backward(tg)
+    g64 = _np(tg)
+    for f in range(B):
+        rx, ry = O.backward(g64[f, 0], rec.M, rec.N, rec.pad)
+        if dt == torch.float32:
+            # the output of an image-like upstream field is large and dominated by the
+            # lowest Green bins: the bar is the FP32 conditioning limit used for every
+            # large adjoint (3x the error of a plain torch FP32 evaluation)
+            tx_, ty_ = _torch_fp32_adjoint(g64[f, 0].astype(np.float32), rec.M, rec.N, rec.pad)
+            tolx, toly = max(REL_F32, 3.0 * _rel(tx_, rx)), max(REL_F32, 3.0 * _rel(ty_, ry))
+        else:
+            tolx = toly = REL_16
+        ex, ey = _rel(_np(ax)[f, 0], rx), _rel(_np(ay)[f, 0], ry)
+        assert ex <= tolx, (f, ex, tolx)
+        assert ey <= toly, (f, ey, toly)
+        # the column-FFT adjoint of the same torus is held to the same bar
+        assert _rel(_np(bx)[f, 0], rx) <= tolx and _rel(_np(by)[f, 0], ry) <= toly
+    rec.close()
+    fft.close()
+
+
+def test_recursive_adjoint_dot_product_identity():
+    """<solve(gx, gy), g> = <gx, adj_x(g)> + <gy, adj_y(g)> on the recursive plan."""
+    H, W, B = 801, 1200, 2
+    rng = np.random.default_rng(9400)
+    gx = _dev(rng.standard_normal((B, 1, H, W)).astype(np.float32))
+    gy = _dev(rng.standard_normal((B, 1, H, W)).astype(np.float32))
+    g = _dev(rng.standard_normal((B, 1, H, W)).astype(np.float32))
+    p = gfc.Plan(H, W, 1, B, device=DEV)
+    y = p.solve_from_gradient(gx, gy)
+    bx, by = p.backward(g)
+    lhs = float((y.double() * g.double()).sum())
+    rhs = float((gx.double() * bx.double()).sum() + (gy.double() * by.double()).sum())
+    assert abs(lhs - rhs) <= 1e-4 * (abs(lhs) + abs(rhs) + 1.0), (lhs, rhs)
+    p.close()
