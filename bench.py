@@ -692,6 +692,10 @@ def _backward_workload(dev, samples):
     go = torch.from_numpy(synth.upstream_gradient((B, 1, H, W), seed=4700)).to(dev)
     gx, gy = torch.empty_like(go), torch.empty_like(go)
     p = gfc.Plan(H, W, 1, B, device=dev)
+    # the forward's tuned pipeline split (cached by the headline's tuning): the
+    # adjoint has the same three-step structure, so its sweep overlaps the other
+    # chunks' row passes the same way
+    tuned = p.autotune()
     ms_b = _time_ms(lambda: p.backward(go, gx, gy), dev, 10)
     ms_f = _time_ms(lambda: p.solve_from_gradient(go, go, gx), dev, 10)
     # per-pass device time of the adjoint (profiling hook), and its minimum bytes:
@@ -713,7 +717,7 @@ def _backward_workload(dev, samples):
              "inverse row pass (half-band solve, grad_gx, grad_gy)"]
     passes = [{"pass": names[i], "ms": prof["pass_ms"][i] / reps, "launches_per_call": prof["launches"][i] / reps}
               for i in range(3)]
-    return {"ms_forward": ms_f, "ms_backward": ms_b, "fwd_bwd_solves_per_s": B * 1000.0 / (ms_f + ms_b),
+    return {"split": tuned, "ms_forward": ms_f, "ms_backward": ms_b, "fwd_bwd_solves_per_s": B * 1000.0 / (ms_f + ms_b),
             "backward_min_bytes": min_bytes, "backward_gb_per_s": gbs, "backward_frac_of_hbm": gbs / peak,
             "peak_kind": kind, "backward_passes": passes}
 

@@ -2050,6 +2050,14 @@ static cudaError_t fast_setup(K kernel, int threads, size_t smem, int* slots) {
   return cudaSuccess;
 }
 
+}  // namespace gfc
+
+// the one-launch solve for small tori (thread-block clusters, spectrum kept in
+// shared memory), tried first by plain gradient solves below
+#include "fused_small.cuh"
+
+namespace gfc {
+
 // The adjoint on a plan with the recursive column solve (reading: the
 // transpose of the solve, z = Crop^T(grad_out) - (sum grad_out) e_00 through
 // the same Green operator, then the forward differences' transposes): the
@@ -2149,6 +2157,12 @@ static cudaError_t run_fast_mode(gfc_plan* P, const Bufs& bf, const T* in0, cons
                                  cudaStream_t st, const EditArgs* ed = nullptr) {
   constexpr bool kCols = !std::is_same_v<CS, NoCols>;  // column transforms compiled for this shape
   static_assert(!kCols || RS::N <= 2048, "the adjoint packing pass covers a whole row in one block");
+  if constexpr (MODE == 0) {
+    if (P->tri && ed == nullptr) {  // plain solves of fields whose spectrum fits a cluster's shared memory
+      const cudaError_t ef = run_fused_small<RS, T>(P, in0, in1, out0, nf, st);
+      if (ef != cudaErrorNotSupported) return ef;
+    }
+  }
   if constexpr (MODE == 2) {
     if (P->tri) {  // the adjoint by the recursive column solve where its staging fits
       const cudaError_t ea = run_fast_adj_tri<RS, T>(P, bf, in0, out0, out1, nf, st);
