@@ -250,8 +250,21 @@ typedef struct {
   double ms;          /* the winner's time per solve (0 when read from the cache) */
   int candidates;     /* candidates timed (0 when read from the cache) */
   int from_cache;     /* 1 when the choice came from the cache */
+  int l2_resident;    /* uniform plans: the winner keeps its spectrum hand-off in L2 (gfc_plan_l2_resident) */
 } gfc_tune_result;
 gfc_status gfc_plan_autotune(gfc_plan* plan, const char* cache_path, gfc_tune_result* result);
+
+/* 1 when the plan keeps the spectrum that its row pass hands to its inverse
+ * row pass in L2, else 0 (-1 for a null plan). That holds for plans with the
+ * recursive column solve whose chunk x streams x hand-off bytes per field (the
+ * row-major spectrum, the bands' sums and carries) fit 80 MB: the row pass
+ * reads the gradients with an evict-first L2 policy and writes the spectrum
+ * with an evict-last one, and the inverse row pass drops the spectrum's L2
+ * lines after reading them for the last time, so they are never written back.
+ * Results do not depend on it (a pure data-placement choice, like the chunk
+ * size; the paper has no counterpart). GFC_NO_L2RES=1 at plan creation turns
+ * it off. */
+int gfc_plan_l2_resident(const gfc_plan* plan);
 
 /* The tuning-cache key of a plan, NUL-terminated in key[capacity]. */
 gfc_status gfc_plan_tune_key(const gfc_plan* plan, char* key, int capacity);

@@ -75,6 +75,8 @@ struct FastArgs {
   int stage_out;     // inverse row pass: output rows staged in shared memory, stored by bulk copy
   double invM, invN; // 1 / M, 1 / N (FP64 divisions are slow on this part)
   int adj;           // the recursive column solve runs the adjoint (half-bands, the sum term at row 0)
+  int l2res;         // the chunks' spectrum hand-off fits the L2: evict-first streams, evict-last spectrum,
+                     // the inverse row pass drops the spectrum lines it has read
 };
 
 // Band scratch of one field (recursive column solve), complex elements:
@@ -472,8 +474,14 @@ __device__ __forceinline__ void tri_store_item(const float2* buf2, float2* __res
       const float2 d = csub(zk, zc);
       x[2 * q + 1] = cscale(make_float2(d.y, -d.x), 0.5f);
     }
+    if (!HALF && A.l2res) {  // the inverse row pass reads these rows next: last out of the L2
+      const uint64_t pol = l2_policy_evict_last();
 #pragma unroll
-    for (int r = 0; r < RW; ++r) Sr[(size_t)r * A.ldY + k] = x[r];
+      for (int r = 0; r < RW; ++r) st_global_hint(Sr + (size_t)r * A.ldY + k, x[r], pol);
+    } else {
+#pragma unroll
+      for (int r = 0; r < RW; ++r) Sr[(size_t)r * A.ldY + k] = x[r];
+    }
     if (k == 0) {
       float* c0 = tri_col0(tri, field, A) + (size_t)g * RW;
 #pragma unroll
@@ -722,8 +730,14 @@ __global__ void __launch_bounds__(S::THREADS, S::MINB_FWD) k_fast_rows_fwd_div(c
       if (nx > 0) bulk_copy(sgx, xs, (unsigned)nx * row, &bar);
     } else {
       mbar_expect_tx(&bar, (unsigned)(nx > 0 ? nx : 0) * row + (unsigned)(y1 - y0) * row);
-      if (nx > 0) bulk_copy(sgx, xs, (unsigned)nx * row, &bar);
-      bulk_copy(sgy + (size_t)(y0 - (r0 - 1)) * A.W, ys, (unsigned)(y1 - y0) * row, &bar);
+      if (A.l2res) {  // read once: first out of the L2, so that the spectrum stays
+        const uint64_t pol = l2_policy_evict_first();
+        if (nx > 0) bulk_copy_hint(sgx, xs, (unsigned)nx * row, &bar, pol);
+        bulk_copy_hint(sgy + (size_t)(y0 - (r0 - 1)) * A.W, ys, (unsigned)(y1 - y0) * row, &bar, pol);
+      } else {
+        if (nx > 0) bulk_copy(sgx, xs, (unsigned)nx * row, &bar);
+        bulk_copy(sgy + (size_t)(y0 - (r0 - 1)) * A.W, ys, (unsigned)(y1 - y0) * row, &bar);
+      }
     }
   };
   if (tid == 0) mbar_init(&bar, 1);
@@ -1550,7 +1564,10 @@ __global__ void __launch_bounds__(S::THREADS, S::MINB_INV) k_fast_rows_inv(const
         return;
       }
       mbar_expect_tx(&bar, rb + cb);
-      bulk_copy(buf, ss, rb, &bar);
+      if (A.l2res)  // the band's last read
+        bulk_copy_hint(buf, ss, rb, &bar, l2_policy_evict_first());
+      else
+        bulk_copy(buf, ss, rb, &bar);
       bulk_copy(cbuf, cs, cb, &bar);
     } else {
       const float2* ys = Y + ((size_t)field * A.H + r0) * A.ldY;
@@ -1613,6 +1630,9 @@ __global__ void __launch_bounds__(S::THREADS, S::MINB_INV) k_fast_rows_inv(const
       return;
     }
     if constexpr (TRI) {
+      if (A.l2res)  // the band's rows of S are in shared memory and dead in global memory: drop their L2 lines
+        l2_discard_range(Y + ((size_t)field * A.srows + (size_t)g * RW) * A.ldY, (size_t)RW * A.ldY * sizeof(float2),
+                         tid, blockDim.x);
       tri_solve_band<S>(buf, cbuf, cc, g, A);
       __syncthreads();
     }
@@ -2078,6 +2098,7 @@ static cudaError_t run_fast_adj_tri(gfc_plan* P, const Bufs& bf, const T* gout, 
   A.invM = 1.0 / (double)P->M;
   A.invN = 1.0 / (double)P->N;
   A.adj = 1;
+  A.l2res = 0;
   A.H = P->H; A.W = P->W; A.p = P->pad; A.M = P->M; A.N = P->N; A.Nh = P->Nh; A.ldM = P->ldM;
   A.nrows = P->H;
   A.ncols = P->W;
@@ -2177,6 +2198,7 @@ static cudaError_t run_fast_mode(gfc_plan* P, const Bufs& bf, const T* in0, cons
   A.invM = 1.0 / (double)P->M;
   A.invN = 1.0 / (double)P->N;
   A.adj = 0;
+  A.l2res = (tri && P->l2res) ? 1 : 0;
   A.H = P->H; A.W = P->W; A.p = P->pad; A.M = P->M; A.N = P->N; A.Nh = P->Nh; A.ldM = P->ldM;
   A.nrows = (MODE == 0) ? P->H + 1 : P->H;
   A.ncols = (MODE == 0) ? P->W + 1 : P->W;

@@ -434,6 +434,7 @@ static cudaError_t run_fused_small(gfc_plan* P, const T* gx, const T* gy, T* out
   A.invM = 1.0 / (double)P->M;
   A.invN = 1.0 / (double)P->N;
   A.adj = 0;
+  A.l2res = 0;
   A.H = P->H; A.W = P->W; A.p = P->pad; A.M = P->M; A.N = P->N; A.Nh = P->Nh; A.ldM = P->ldM;
   A.nrows = P->H + 1;
   A.ncols = P->W + 1;

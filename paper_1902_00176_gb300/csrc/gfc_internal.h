@@ -47,6 +47,11 @@ struct Bufs {
   float2* tri;     // band sums and carries of the recursive column solve (fast passes)
 };
 constexpr int kMaxSlots = 4;
+// L2 the spectrum hand-off of the chunks in flight may take (of the GPU's
+// 126 MB): below it, the row pass writes the spectrum with an evict-last
+// policy, gradients stream with evict-first and the inverse row pass drops the
+// spectrum lines it has read, so the hand-off need not reach HBM
+constexpr size_t kL2ResidentBytes = (size_t)80 << 20;
 constexpr int kMaxRagStreams = 8;  // streams of a ragged plan's per-item sub-plans
 constexpr int kHostBufs = 4;  // most staging buffers of the host-buffer pipeline
 
@@ -84,6 +89,7 @@ struct gfc_plan {
   bool fast_cols;  // ... and the column length has them too (column FFT path, adjoint)
   bool tri;   // fast passes with the column direction by recursive filters (gfc_column_solver)
   bool block_items;  // fast passes launch one block per item (else persistent grids)
+  bool l2res;        // recursive column solve whose spectrum hand-off (chunk x streams) fits kL2ResidentBytes
   int triG;   // bands of the recursive column solve (pass A's items)
   size_t tri_field;  // complex elements per field of the band scratch
   float* colcoef;    // [Nh][8] column coefficients of the recursive solve
@@ -220,6 +226,15 @@ gfc_status ragged_set_streams(gfc_plan* P, int k);
 
 // free the host-buffer pipeline and the profiling event pool (plan teardown)
 void release_host_state(gfc_plan* P);
+
+// spectrum hand-off bytes per field of a solve on a recursive-column-solve
+// plan: the row-major spectrum S (2F rows per band), the bands' carries and
+// sums, column 0's compact copy
+inline size_t tri_handoff_bytes(const gfc_plan* p) {
+  const size_t G = (size_t)p->triG, srows = (size_t)2 * fast_row_items(p->M, p->N) * G;
+  const size_t nkb = ((size_t)p->ldS + 31) / 32;
+  return (srows * p->ldS + 2 * G * p->ldS + nkb * 2 * G * 32) * sizeof(float2) + srows * sizeof(float);
+}
 
 }  // namespace gfc
 

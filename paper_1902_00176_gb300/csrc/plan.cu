@@ -249,6 +249,11 @@ gfc_status gfc_padded_size(int H, int W, int pad, int size_policy, int* M, int* 
   return GFC_OK;
 }
 
+int gfc_plan_l2_resident(const gfc_plan* plan) {
+  clear_error();
+  return plan ? (plan->l2res ? 1 : 0) : -1;
+}
+
 int gfc_row_lengths(int* lengths, int capacity) {
   clear_error();
   return fast_row_lengths(lengths, lengths ? capacity : 0);
@@ -337,6 +342,9 @@ gfc_status gfc_plan_create_ex(gfc_plan** out, const gfc_plan_opts* o) {
   if (nslots > nchunks) nslots = (int)nchunks;
   p->chunk = (int)chunk;
   p->nslots = nslots;
+  // the chunks in flight hand their spectra to the inverse row pass through L2
+  p->l2res = p->tri && (size_t)chunk * nslots * tri_handoff_bytes(p) <= kL2ResidentBytes &&
+             getenv("GFC_NO_L2RES") == nullptr;
 
   cudaError_t e = cudaGetDevice(&p->device);
   if (e == cudaSuccess) e = cudaMalloc(&p->G, (size_t)M * p->Nh * sizeof(float));

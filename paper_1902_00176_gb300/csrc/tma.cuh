@@ -54,6 +54,46 @@ __device__ __forceinline__ void bulk_copy(void* dst_smem, const void* src_gmem, 
       : "memory");
 }
 
+// L2 eviction policies (createpolicy): data read or written once goes first,
+// the spectrum handed from the row pass to the inverse row pass goes last
+__device__ __forceinline__ uint64_t l2_policy_evict_first() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;\n" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint64_t l2_policy_evict_last() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;\n" : "=l"(p));
+  return p;
+}
+
+// bulk_copy with an L2 eviction policy for the lines it reads
+__device__ __forceinline__ void bulk_copy_hint(void* dst_smem, const void* src_gmem, unsigned bytes, uint64_t* bar,
+                                               uint64_t policy) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;\n" ::"r"(
+          smem_addr(dst_smem)),
+      "l"(src_gmem), "r"(bytes), "r"(smem_addr(bar)), "l"(policy)
+      : "memory");
+}
+
+// 8-byte global store with an L2 eviction policy
+__device__ __forceinline__ void st_global_hint(float2* p, float2 v, uint64_t policy) {
+  asm volatile("st.global.L2::cache_hint.v2.f32 [%0], {%1, %2}, %3;\n" ::"l"(p), "f"(v.x), "f"(v.y), "l"(policy)
+               : "memory");
+}
+
+// Drop the whole 128-byte L2 lines inside [begin, begin + bytes) without
+// writing them back (their data is dead: read for the last time). Lines that
+// the range only partly covers are left alone. The calling threads split the
+// lines by `rank` of `count`.
+__device__ __forceinline__ void l2_discard_range(const void* begin, size_t bytes, int rank, int count) {
+  const uintptr_t b = reinterpret_cast<uintptr_t>(begin), e = b + bytes;
+  const uintptr_t first = (b + 127) & ~(uintptr_t)127, last = e & ~(uintptr_t)127;
+  for (uintptr_t a = first + (uintptr_t)rank * 128; a < last; a += (uintptr_t)count * 128)
+    asm volatile("discard.global.L2 [%0], 128;\n" ::"l"(a) : "memory");
+}
+
 // one thread: expect and start one copy
 __device__ __forceinline__ void bulk_load(void* dst_smem, const void* src_gmem, unsigned bytes, uint64_t* bar) {
   mbar_expect_tx(bar, bytes);

@@ -6,7 +6,10 @@
 // plan's stream and keeps the fastest:
 //   uniform plans: the column solver (recursive filters or column FFTs, where
 //                  both exist) x the pipeline split (one chunk of all fields,
-//                  or chunks sized for the L2 on two streams);
+//                  chunks sized for the L2 on two streams, halves, thirds and
+//                  quarters of the batch, and for the recursive solve the
+//                  largest chunks whose spectrum hand-off the plan keeps in L2
+//                  on 2, 3 and 4 streams);
 //   ragged plans:  the number of internal streams the per-item sub-plans are
 //                  spread over.
 // The winner is stored under a key naming the problem, the device and the
@@ -281,6 +284,20 @@ gfc_status gfc_plan_autotune(gfc_plan* plan, const char* cache_path, gfc_tune_re
         o.streams = 1;
       }
     }
+    // recursive column solve: the largest chunks whose spectrum hand-off fits
+    // the L2 budget on 2, 3 and 4 streams (the plan then keeps it in L2)
+    for (int ns = 2; si == 0 && plan->tri && ns <= 4 && ncand < 22; ++ns) {
+      const long c = (long)(kL2ResidentBytes / ((size_t)ns * tri_handoff_bytes(plan)));
+      bool dup = false;
+      for (int j = 0; j < ncand; ++j) dup = dup || (cand[j].chunk == c && cand[j].streams == ns);
+      if (c >= 1 && c < fields && !dup) {
+        o.chunk = (int)c;
+        o.streams = ns;
+        cand[ncand++] = o;
+        o.chunk = 0;
+        o.streams = 1;
+      }
+    }
     if (si == 0 && plan->fast && ncand < 24) {  // one chunk, one block per item
       o.block_items = 1;
       cand[ncand++] = o;
@@ -323,6 +340,7 @@ gfc_status gfc_plan_autotune(gfc_plan* plan, const char* cache_path, gfc_tune_re
   r.block_items = best.block_items;
   r.chunk = plan->chunk;
   r.streams = plan->nslots;
+  r.l2_resident = plan->l2res ? 1 : 0;
   r.ms = best_ms;
   r.candidates = n;
   if (cache_path && !r.from_cache && n > 0) {

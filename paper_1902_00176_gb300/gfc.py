@@ -58,7 +58,7 @@ class TuneResult(ctypes.Structure):
     """Mirror of gfc_tune_result."""
     _fields_ = [("column_solver", ctypes.c_int), ("block_items", ctypes.c_int), ("chunk", ctypes.c_int),
                 ("streams", ctypes.c_int), ("rag_streams", ctypes.c_int), ("ms", ctypes.c_double),
-                ("candidates", ctypes.c_int), ("from_cache", ctypes.c_int)]
+                ("candidates", ctypes.c_int), ("from_cache", ctypes.c_int), ("l2_resident", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -82,6 +82,7 @@ _SIGNATURES = {
     "gfc_padded_size": [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                         ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
     "gfc_row_lengths": [ctypes.POINTER(ctypes.c_int), ctypes.c_int],
+    "gfc_plan_l2_resident": [ctypes.c_void_p],
     "gfc_plan_create": [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                         ctypes.c_int],
     "gfc_plan_create_ex": [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(_Opts)],
@@ -413,6 +414,11 @@ class Plan:
 
     def tune_key(self) -> str:
         return _tune_key(self._h)
+
+    @property
+    def l2_resident(self) -> bool:
+        """Whether the plan keeps its spectrum hand-off in L2 (gfc_plan_l2_resident)."""
+        return lib().gfc_plan_l2_resident(self._h) == 1
 
     def green(self):
         """The plan's FP32 Green spectrum, M x (N/2+1), as a CPU tensor (1/(MN) folded in)."""

@@ -225,3 +225,30 @@ def test_recursive_adjoint_dot_product_identity():
     rhs = float((gx.double() * bx.double()).sum() + (gy.double() * by.double()).sum())
     assert abs(lhs - rhs) <= 1e-4 * (abs(lhs) + abs(rhs) + 1.0), (lhs, rhs)
     p.close()
+
+
+def test_l2_resident_split_is_bitwise_equal_to_one_chunk(monkeypatch):
+    """A split whose spectrum hand-off fits the L2 budget (evict-first gradients,
+    evict-last spectrum, the inverse row pass dropping the spectrum lines it has
+    read) gives the same bits as one chunk and as the same split without the
+    policies, call after call; the Laplacian entry and the corrected solve run
+    the same passes."""
+    B, H, W = 16, 801, 1200
+    gx, gy = synth.perturbed_gradient_batch(batch=B, H=H, W=W, seed=9500)
+    tx, ty = _dev(gx), _dev(gy)
+    one = gfc.Plan(H, W, 1, B, device=DEV)  # 16 fields x 5.7 MB: above the budget
+    res = gfc.Plan(H, W, 1, B, device=DEV, chunk=3, streams=4)
+    monkeypatch.setenv("GFC_NO_L2RES", "1")
+    off = gfc.Plan(H, W, 1, B, device=DEV, chunk=3, streams=4)
+    monkeypatch.delenv("GFC_NO_L2RES")
+    assert res.l2_resident and not one.l2_resident and not off.l2_resident
+    a = one.solve_from_gradient(tx, ty)
+    assert torch.equal(a, off.solve_from_gradient(tx, ty))
+    for _ in range(3):
+        assert torch.equal(a, res.solve_from_gradient(tx, ty))
+    lap = torch.roll(tx, 1, -1) - tx
+    assert torch.equal(one.solve_from_laplacian(lap), res.solve_from_laplacian(lap))
+    ref = O.solve_from_gradient(gx[5, 0].astype(np.float64), gy[5, 0].astype(np.float64), res.M, res.N, res.pad)
+    assert _rel(_np(a)[5, 0], ref) <= REL_F32
+    for p in (one, res, off):
+        p.close()
