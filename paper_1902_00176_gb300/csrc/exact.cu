@@ -20,6 +20,7 @@
 #include <cuda_fp16.h>
 
 #include <math.h>
+#include <stdlib.h>
 
 #include <vector>
 
@@ -121,6 +122,129 @@ __global__ void __launch_bounds__(kExactThreads) k_exact_cols(float2* XT, int nf
     float2* u = dft_row<+1>(z, y, d, threadIdx.x, blockDim.x);
     for (int k = threadIdx.x; k < M; k += blockDim.x) x[k] = u[k];
     __syncthreads();
+  }
+}
+
+// ---- the column direction by the recursive column solve --------------------
+// After the row DFTs, column l of Eq. 23's Green multiply (G = 1/(M N lambda),
+// lambda(k, l) = 2 cos(2 pi k / M) - b_l, b_l = 4 - 2 cos(2 pi l / N)) is, with
+// the unnormalised inverse column DFT folded in, 1/N times the inverse of the
+// cyclic tridiagonal operator S + S^-1 - b_l along the torus rows. With
+// a + 1/a = b_l, a < 1, that inverse is -a / (1 - a^2) [(1 - a S)^-1 +
+// (1 - a S^-1)^-1 - 1]: a causal and an anticausal first-order recursion
+// around the cycle. It is real, so it maps the packed pair's real and
+// imaginary parts each to its own solution, and it depends on l only through
+// min(l, N - l). Per column (FP64, rounded once): (1 - a, a,
+// C = -a / ((1 - a^2) N), 1 / (1 - a^M)); column 0 (b = 2, singular) is solved
+// exactly (k_exact_col0).
+__global__ void k_exact_colcoef(float4* cc, int M, int N, int Nh) {
+  for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < Nh; l += gridDim.x * blockDim.x) {
+    if (l == 0) {
+      cc[0] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      continue;
+    }
+    const double sn = sinpi((double)l / (double)N);
+    const double d = 4.0 * sn * sn;  // b - 2
+    const double r = sqrt(d * (4.0 + d));
+    const double a = 2.0 / (2.0 + d + r), delta = (d + r) / (2.0 + d + r);
+    cc[l] = make_float4((float)delta, (float)a, (float)(-a / (delta * (1.0 + a) * (double)N)),
+                        (float)(1.0 / (1.0 - pow(a, (double)M))));
+  }
+}
+
+// y <- x + a y as (x + y) - delta y (delta = 1 - a held to full precision)
+__device__ __forceinline__ float2 ex_step(float2 x, float2 y, float delta) {
+  return make_float2(__fmaf_rn(-delta, y.x, __fadd_rn(x.x, y.x)), __fmaf_rn(-delta, y.y, __fadd_rn(x.y, y.y)));
+}
+
+// One lane per column l >= 1 of the row-major pair torus X (M rows of N), four
+// coalesced passes down and up the rows: the causal recursion from a zero
+// carry (its last value, times 1 / (1 - a^M), is y[M-1], which closes the
+// cycle); the causal recursion from that carry, into Y; the anticausal one
+// from a zero carry (giving y'[0]); the anticausal one from its carry, with
+// U = C (y + y' - x) written over X. Grid: (32-column strips / 4, pairs).
+__global__ void __launch_bounds__(128) k_exact_cols_rec(float2* __restrict__ X, float2* __restrict__ Y, int M, int N,
+                                                        const float4* __restrict__ cc) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int l = (blockIdx.x * 4 + warp) * 32 + lane;
+  if (l == 0 || l >= N) return;  // no lane waits on another
+  const int lg = l <= N - l ? l : N - l;
+  const float4 c = __ldg(cc + lg);
+  const float delta = c.x, C = c.z, inv = c.w;
+  float2* x = X + (size_t)blockIdx.y * M * N + l;
+  float2* y = Y + (size_t)blockIdx.y * M * N + l;
+  float2 t = make_float2(0.0f, 0.0f);
+#pragma unroll 8
+  for (int r = 0; r < M; ++r) t = ex_step(x[(size_t)r * N], t, delta);
+  float2 yc = make_float2(t.x * inv, t.y * inv);  // y[M-1]
+#pragma unroll 8
+  for (int r = 0; r < M; ++r) {
+    yc = ex_step(x[(size_t)r * N], yc, delta);
+    y[(size_t)r * N] = yc;
+  }
+  float2 q = make_float2(0.0f, 0.0f);
+#pragma unroll 8
+  for (int r = M - 1; r >= 0; --r) q = ex_step(x[(size_t)r * N], q, delta);
+  float2 ya = make_float2(q.x * inv, q.y * inv);  // y'[0]
+#pragma unroll 8
+  for (int r = M - 1; r >= 0; --r) {
+    const float2 xr = x[(size_t)r * N];
+    ya = ex_step(xr, ya, delta);
+    const float2 yr = y[(size_t)r * N];
+    x[(size_t)r * N] = make_float2(C * ((yr.x + ya.x) - xr.x), C * ((yr.y + ya.y) - xr.y));
+  }
+}
+
+__device__ __forceinline__ double ex_warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double ex_warp_exscan(double v) {
+  const int lane = threadIdx.x & 31;
+  double x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const double y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  return x - v;
+}
+
+// Column 0 of each pair torus (one warp each, FP64, the real and the imaginary
+// part in turn): with d[r] = u[r+1] - u[r], (S + S^-1 - 2) u = f - mean(f)
+// reads d[r] - d[r-1] = f[r] - mean(f); periodicity fixes d[-1] = -sum_r P[r] / M
+// with P the prefix sums of f - mean(f); u[0] = 0 (a constant in column 0 is a
+// constant in the field, which Algorithm B's offset removes). Each lane walks
+// a contiguous run of rows; u / N replaces the column.
+__global__ void __launch_bounds__(32) k_exact_col0(float2* __restrict__ X, int M, int N) {
+  const int lane = threadIdx.x;
+  float2* col = X + (size_t)blockIdx.x * M * N;
+  const int run = (M + 31) / 32;
+  const int r0 = min(lane * run, M), r1 = min(r0 + run, M);
+  const double invM = 1.0 / (double)M, invN = 1.0 / (double)N;
+  for (int part = 0; part < 2; ++part) {
+    auto f = [&](int r) -> double { return part ? (double)col[(size_t)r * N].y : (double)col[(size_t)r * N].x; };
+    double s0 = 0.0;
+    for (int r = r0; r < r1; ++r) s0 += f(r);
+    const double mean = ex_warp_sum(s0) * invM;
+    const double off = ex_warp_exscan(s0 - mean * (double)(r1 - r0));
+    double Pr = off, Ps = 0.0;
+    for (int r = r0; r < r1; ++r) {
+      Pr += f(r) - mean;
+      Ps += Pr;
+    }
+    const double D = -ex_warp_sum(Ps) * invM;
+    double u = ex_warp_exscan(D * (double)(r1 - r0) + Ps);
+    Pr = off;
+    for (int r = r0; r < r1; ++r) {
+      const double fr = f(r);  // read before the row is overwritten
+      float2* cr = col + (size_t)r * N;
+      if (part) cr->y = (float)(u * invN);
+      else cr->x = (float)(u * invN);
+      Pr += fr - mean;
+      u += D + Pr;
+    }
   }
 }
 
@@ -380,16 +504,31 @@ cudaError_t run_exact(gfc_plan* P, const Bufs& bf, const T* in0, const T* in1, T
   k_exact_rows<-1><<<grow, kExactThreads, sr, st>>>(X, rows, N, dr);
   prof_end(P, st);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  const dim3 tb(32, 8);
-  k_exact_transpose<<<dim3((N + 31) / 32, (M + 31) / 32, np), tb, 0, st>>>(X, XT, M, N);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  const long long cols = (long long)np * N;
-  prof_begin(P, 1, st);
-  k_exact_cols<<<(int)(cols < 8LL * sms ? cols : 8LL * sms), kExactThreads, sc, st>>>(XT, np, M, N, P->Nh, P->G, dc);
-  prof_end(P, st);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  k_exact_transpose<<<dim3((M + 31) / 32, (N + 31) / 32, np), tb, 0, st>>>(XT, X, N, M);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (getenv("GFC_EXACT_COLUMN_DFT") == nullptr) {
+    // the column direction by the recursive column solve, in place on the
+    // row-major tori (XT holds the causal pass); column 0 exactly
+    prof_begin(P, 1, st);
+    const int strips = (N + 31) / 32;
+    k_exact_cols_rec<<<dim3((strips + 3) / 4, np), 128, 0, st>>>(X, XT, M, N,
+                                                                 reinterpret_cast<const float4*>(P->colcoef));
+    k_exact_col0<<<np, 32, 0, st>>>(X, M, N);
+    P->prof.launches[1] += 1;  // a second launch in this pass
+    prof_end(P, st);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  } else {
+    // the column DFTs (Bluestein where M is not 7-smooth) on the transposed tori
+    const dim3 tb(32, 8);
+    k_exact_transpose<<<dim3((N + 31) / 32, (M + 31) / 32, np), tb, 0, st>>>(X, XT, M, N);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const long long cols = (long long)np * N;
+    prof_begin(P, 1, st);
+    k_exact_cols<<<(int)(cols < 8LL * sms ? cols : 8LL * sms), kExactThreads, sc, st>>>(XT, np, M, N, P->Nh, P->G,
+                                                                                         dc);
+    prof_end(P, st);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_exact_transpose<<<dim3((M + 31) / 32, (N + 31) / 32, np), tb, 0, st>>>(XT, X, N, M);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
   prof_begin(P, 2, st);
   k_exact_rows<+1><<<grow, kExactThreads, sr, st>>>(X, rows, N, dr);
   prof_end(P, st);
@@ -411,6 +550,12 @@ cudaError_t run_exact(gfc_plan* P, const Bufs& bf, const T* in0, const T* in1, T
 cudaError_t exact_setup(gfc_plan* P, cudaStream_t s) {
   cudaError_t e = setup_dim(&P->ex_row, P->N, s);
   if (e == cudaSuccess) e = setup_dim(&P->ex_col, P->M, s);
+  // the recursive column solve's coefficients, [Nh] x 4 floats (freed with the plan)
+  if (e == cudaSuccess && !P->colcoef) e = cudaMalloc(&P->colcoef, (size_t)P->Nh * sizeof(float4));
+  if (e == cudaSuccess) {
+    k_exact_colcoef<<<(P->Nh + 255) / 256, 256, 0, s>>>(reinterpret_cast<float4*>(P->colcoef), P->M, P->N, P->Nh);
+    e = cudaGetLastError();
+  }
   return e;
 }
 

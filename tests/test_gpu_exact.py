@@ -1,5 +1,7 @@
 """EXACT size policy (Algorithm A's own padded size, M = H + 2p, N = W + 2p):
-parity of the Bluestein/Stockham path with the oracle run on the same torus.
+parity of the Bluestein/Stockham row DFTs and the recursive column solve with
+the oracle run on the same torus, and of the recursive column solve with the
+column DFTs (GFC_EXACT_COLUMN_DFT) on the same plan.
 
 The tolerance is the solver's: relative L2 <= 1e-5 in FP32 on image-like
 inputs, 2e-3 for 16-bit storage against the oracle on the dequantised inputs.
@@ -157,3 +159,33 @@ def test_exact_backward_is_the_transpose_and_bf16():
     rx, ry = O.backward(_np(dg)[0, 0], q.M, q.N, q.pad)
     assert _rel(_np(qx)[0, 0], rx) <= REL_16 and _rel(_np(qy)[0, 0], ry) <= REL_16
     q.close()
+
+
+@pytest.mark.parametrize("H,W,B", [(801, 1200, 3), (23, 29, 3), (64, 96, 2)])
+def test_exact_recursive_columns_match_column_dfts(H, W, B, monkeypatch):
+    """The column direction by the recursive column solve (in place on the
+    row-major pair tori, column 0 exactly in FP64) against the Bluestein column
+    DFTs with the Green multiply, for the solve and the adjoint; odd B leaves
+    the last pair torus half empty."""
+    gx, gy = synth.perturbed_gradient_batch(B, H, W, seed=7300)
+    g = (gx + 0.5 * gy).astype(np.float32)  # an image-like upstream gradient
+    p = gfc.Plan(H, W, 1, B, device=DEV, exact=True)
+    a = _np(p.solve_from_gradient(_dev(gx), _dev(gy)))
+    ax, ay = (_np(t) for t in p.backward(_dev(g)))
+    monkeypatch.setenv("GFC_EXACT_COLUMN_DFT", "1")
+    b = _np(p.solve_from_gradient(_dev(gx), _dev(gy)))
+    bx, by = (_np(t) for t in p.backward(_dev(g)))
+    monkeypatch.delenv("GFC_EXACT_COLUMN_DFT")
+    assert _rel(a, b) <= 2e-6, _rel(a, b)
+    ref = O.solve_from_gradient(gx[B - 1, 0].astype(np.float64), gy[B - 1, 0].astype(np.float64), p.M, p.N, p.pad)
+    assert _rel(a[B - 1, 0], ref) <= REL_F32
+    # the adjoint against the FP64 oracle: its output is large and dominated by
+    # the lowest Green bins, so both column methods are held to 3x the error of a
+    # plain torch FP32 evaluation, like every large adjoint
+    rx, ry = O.backward(g[0, 0].astype(np.float64), p.M, p.N, p.pad)
+    tx, ty = _torch_fp32_adjoint(g[0, 0], p.M, p.N, p.pad)
+    bar_x, bar_y = max(REL_F32, 3.0 * _rel(tx, rx)), max(REL_F32, 3.0 * _rel(ty, ry))
+    for ox, oy in ((ax, ay), (bx, by)):
+        assert _rel(ox[0, 0], rx) <= bar_x and _rel(oy[0, 0], ry) <= bar_y, (_rel(ox[0, 0], rx), bar_x,
+                                                                           _rel(oy[0, 0], ry), bar_y)
+    p.close()
