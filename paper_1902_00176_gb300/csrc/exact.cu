@@ -134,21 +134,34 @@ __global__ void __launch_bounds__(kExactThreads) k_exact_cols(float2* XT, int nf
 // (1 - a S^-1)^-1 - 1]: a causal and an anticausal first-order recursion
 // around the cycle. It is real, so it maps the packed pair's real and
 // imaginary parts each to its own solution, and it depends on l only through
-// min(l, N - l). Per column (FP64, rounded once): (1 - a, a,
-// C = -a / ((1 - a^2) N), 1 / (1 - a^M)); column 0 (b = 2, singular) is solved
-// exactly (k_exact_col0).
-__global__ void k_exact_colcoef(float4* cc, int M, int N, int Nh) {
+// min(l, N - l). The rows are cut into segments of kExSeg (the last one
+// shorter); each segment's recursions run in registers from zero carries,
+// a sweep per column folds the segments' end values around the cycle into
+// the carries, and each segment then solves with its carries.
+// Per column (FP64, rounded once): 1 - a, a, C = -a / ((1 - a^2) N),
+// 1 / (1 - a^M), a^kExSeg, a^(rows of the last segment); column 0 (b = 2,
+// singular) is solved exactly (k_exact_col0).
+constexpr int kExSeg = 16;
+
+__global__ void k_exact_colcoef(float* cc, int M, int N, int Nh) {
+  const int nseg = (M + kExSeg - 1) / kExSeg, last = M - kExSeg * (nseg - 1);
   for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < Nh; l += gridDim.x * blockDim.x) {
+    float* c = cc + (size_t)l * 8;
     if (l == 0) {
-      cc[0] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      for (int i = 0; i < 8; ++i) c[i] = 0.0f;
       continue;
     }
     const double sn = sinpi((double)l / (double)N);
     const double d = 4.0 * sn * sn;  // b - 2
     const double r = sqrt(d * (4.0 + d));
     const double a = 2.0 / (2.0 + d + r), delta = (d + r) / (2.0 + d + r);
-    cc[l] = make_float4((float)delta, (float)a, (float)(-a / (delta * (1.0 + a) * (double)N)),
-                        (float)(1.0 / (1.0 - pow(a, (double)M))));
+    c[0] = (float)delta;
+    c[1] = (float)a;
+    c[2] = (float)(-a / (delta * (1.0 + a) * (double)N));
+    c[3] = (float)(1.0 / (1.0 - pow(a, (double)M)));
+    c[4] = (float)pow(a, (double)kExSeg);
+    c[5] = (float)pow(a, (double)last);
+    c[6] = c[7] = 0.0f;
   }
 }
 
@@ -156,43 +169,103 @@ __global__ void k_exact_colcoef(float4* cc, int M, int N, int Nh) {
 __device__ __forceinline__ float2 ex_step(float2 x, float2 y, float delta) {
   return make_float2(__fmaf_rn(-delta, y.x, __fadd_rn(x.x, y.x)), __fmaf_rn(-delta, y.y, __fadd_rn(x.y, y.y)));
 }
+__device__ __forceinline__ float2 ex_fma(float T, float2 c, float2 e) {
+  return make_float2(__fmaf_rn(T, c.x, e.x), __fmaf_rn(T, c.y, e.y));
+}
 
-// One lane per column l >= 1 of the row-major pair torus X (M rows of N), four
-// coalesced passes down and up the rows: the causal recursion from a zero
-// carry (its last value, times 1 / (1 - a^M), is y[M-1], which closes the
-// cycle); the causal recursion from that carry, into Y; the anticausal one
-// from a zero carry (giving y'[0]); the anticausal one from its carry, with
-// U = C (y + y' - x) written over X. Grid: (32-column strips / 4, pairs).
-__global__ void __launch_bounds__(128) k_exact_cols_rec(float2* __restrict__ X, float2* __restrict__ Y, int M, int N,
-                                                        const float4* __restrict__ cc) {
+// Scratch of pair torus q in the (otherwise unused) transpose buffer, complex
+// elements from q M N: the segments' sums [nseg][2][N] (causal value at the
+// segment's last row, anticausal value at its first row, from zero carries),
+// then their carries [nseg][2][N] (into the segment from above, from below).
+// 4 nseg N <= M N for every M >= 4.
+
+// Segment sums, one lane per column l >= 1 (coalesced rows), the segment's
+// rows in registers. Grid: (32-column strips / 4, segments, pairs).
+__global__ void __launch_bounds__(128) k_exact_seg_sums(const float2* __restrict__ X, float2* __restrict__ XT, int M,
+                                                        int N, int nseg, const float* __restrict__ cc) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int l = (blockIdx.x * 4 + warp) * 32 + lane;
   if (l == 0 || l >= N) return;  // no lane waits on another
   const int lg = l <= N - l ? l : N - l;
-  const float4 c = __ldg(cc + lg);
-  const float delta = c.x, C = c.z, inv = c.w;
-  float2* x = X + (size_t)blockIdx.y * M * N + l;
-  float2* y = Y + (size_t)blockIdx.y * M * N + l;
+  const float delta = __ldg(cc + (size_t)lg * 8);
+  const int sg = blockIdx.y, r0 = sg * kExSeg, nr = min(kExSeg, M - r0);
+  const float2* x = X + (size_t)blockIdx.z * M * N + (size_t)r0 * N + l;
+  float2 v[kExSeg];
+#pragma unroll
+  for (int r = 0; r < kExSeg; ++r) v[r] = r < nr ? x[(size_t)r * N] : make_float2(0.0f, 0.0f);
+  float2 e = make_float2(0.0f, 0.0f), ep = e;
+#pragma unroll
+  for (int r = 0; r < kExSeg; ++r)
+    if (r < nr) e = ex_step(v[r], e, delta);
+#pragma unroll
+  for (int r = kExSeg - 1; r >= 0; --r)
+    if (r < nr) ep = ex_step(v[r], ep, delta);
+  float2* sums = XT + (size_t)blockIdx.z * M * N;
+  sums[(size_t)(2 * sg) * N + l] = e;
+  sums[(size_t)(2 * sg + 1) * N + l] = ep;
+}
+
+// The sweep, one thread per column l >= 1: the causal sums folded down the
+// torus from a zero carry give y[M-1] = fold / (1 - a^M), which is the carry
+// into segment 0 (row 0 follows row M-1); the carries follow segment by
+// segment. The anticausal sums folded up give y'[0], the carry from below the
+// last segment. Grid: (columns / 128, pairs).
+__global__ void __launch_bounds__(128) k_exact_seg_sweep(float2* __restrict__ XT, int M, int N, int nseg,
+                                                         const float* __restrict__ cc) {
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l == 0 || l >= N) return;
+  const int lg = l <= N - l ? l : N - l;
+  const float inv = __ldg(cc + (size_t)lg * 8 + 3), Ts = __ldg(cc + (size_t)lg * 8 + 4),
+              Tl = __ldg(cc + (size_t)lg * 8 + 5);
+  const float2* sums = XT + (size_t)blockIdx.y * M * N + l;
+  float2* car = XT + (size_t)blockIdx.y * M * N + (size_t)2 * nseg * N + l;
   float2 t = make_float2(0.0f, 0.0f);
-#pragma unroll 8
-  for (int r = 0; r < M; ++r) t = ex_step(x[(size_t)r * N], t, delta);
-  float2 yc = make_float2(t.x * inv, t.y * inv);  // y[M-1]
-#pragma unroll 8
-  for (int r = 0; r < M; ++r) {
-    yc = ex_step(x[(size_t)r * N], yc, delta);
-    y[(size_t)r * N] = yc;
+#pragma unroll 4
+  for (int sg = 0; sg < nseg; ++sg) t = ex_fma(sg == nseg - 1 ? Tl : Ts, t, sums[(size_t)(2 * sg) * N]);
+  float2 c = make_float2(t.x * inv, t.y * inv);  // y[M-1]: the carry into segment 0
+#pragma unroll 4
+  for (int sg = 0; sg < nseg; ++sg) {
+    car[(size_t)(2 * sg) * N] = c;
+    c = ex_fma(sg == nseg - 1 ? Tl : Ts, c, sums[(size_t)(2 * sg) * N]);
   }
   float2 q = make_float2(0.0f, 0.0f);
-#pragma unroll 8
-  for (int r = M - 1; r >= 0; --r) q = ex_step(x[(size_t)r * N], q, delta);
-  float2 ya = make_float2(q.x * inv, q.y * inv);  // y'[0]
-#pragma unroll 8
-  for (int r = M - 1; r >= 0; --r) {
-    const float2 xr = x[(size_t)r * N];
-    ya = ex_step(xr, ya, delta);
-    const float2 yr = y[(size_t)r * N];
-    x[(size_t)r * N] = make_float2(C * ((yr.x + ya.x) - xr.x), C * ((yr.y + ya.y) - xr.y));
+#pragma unroll 4
+  for (int sg = nseg - 1; sg >= 0; --sg) q = ex_fma(sg == nseg - 1 ? Tl : Ts, q, sums[(size_t)(2 * sg + 1) * N]);
+  c = make_float2(q.x * inv, q.y * inv);  // y'[0]: the carry from below the last segment
+#pragma unroll 4
+  for (int sg = nseg - 1; sg >= 0; --sg) {
+    car[(size_t)(2 * sg + 1) * N] = c;
+    c = ex_fma(sg == nseg - 1 ? Tl : Ts, c, sums[(size_t)(2 * sg + 1) * N]);
   }
+}
+
+// Each segment with its carries: the causal recursion down, the anticausal one
+// up, U = C (y + y' - x) written over X. Grid as k_exact_seg_sums.
+__global__ void __launch_bounds__(128) k_exact_seg_solve(float2* __restrict__ X, const float2* __restrict__ XT, int M,
+                                                         int N, int nseg, const float* __restrict__ cc) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int l = (blockIdx.x * 4 + warp) * 32 + lane;
+  if (l == 0 || l >= N) return;
+  const int lg = l <= N - l ? l : N - l;
+  const float delta = __ldg(cc + (size_t)lg * 8), C = __ldg(cc + (size_t)lg * 8 + 2);
+  const int sg = blockIdx.y, r0 = sg * kExSeg, nr = min(kExSeg, M - r0);
+  float2* x = X + (size_t)blockIdx.z * M * N + (size_t)r0 * N + l;
+  const float2* car = XT + (size_t)blockIdx.z * M * N + (size_t)2 * nseg * N + l;
+  float2 v[kExSeg], y[kExSeg];
+#pragma unroll
+  for (int r = 0; r < kExSeg; ++r) v[r] = r < nr ? x[(size_t)r * N] : make_float2(0.0f, 0.0f);
+  float2 yc = car[(size_t)(2 * sg) * N], ya = car[(size_t)(2 * sg + 1) * N];
+#pragma unroll
+  for (int r = 0; r < kExSeg; ++r) {
+    yc = ex_step(v[r], yc, delta);
+    y[r] = yc;
+  }
+#pragma unroll
+  for (int r = kExSeg - 1; r >= 0; --r)
+    if (r < nr) {
+      ya = ex_step(v[r], ya, delta);
+      x[(size_t)r * N] = make_float2(C * ((y[r].x + ya.x) - v[r].x), C * ((y[r].y + ya.y) - v[r].y));
+    }
 }
 
 __device__ __forceinline__ double ex_warp_sum(double v) {
@@ -508,11 +581,13 @@ cudaError_t run_exact(gfc_plan* P, const Bufs& bf, const T* in0, const T* in1, T
     // the column direction by the recursive column solve, in place on the
     // row-major tori (XT holds the causal pass); column 0 exactly
     prof_begin(P, 1, st);
-    const int strips = (N + 31) / 32;
-    k_exact_cols_rec<<<dim3((strips + 3) / 4, np), 128, 0, st>>>(X, XT, M, N,
-                                                                 reinterpret_cast<const float4*>(P->colcoef));
+    const int strips = (N + 31) / 32, nseg = (M + kExSeg - 1) / kExSeg;
+    const dim3 sgrid((strips + 3) / 4, nseg, np);
+    k_exact_seg_sums<<<sgrid, 128, 0, st>>>(X, XT, M, N, nseg, P->colcoef);
+    k_exact_seg_sweep<<<dim3((N + 127) / 128, np), 128, 0, st>>>(XT, M, N, nseg, P->colcoef);
+    k_exact_seg_solve<<<sgrid, 128, 0, st>>>(X, XT, M, N, nseg, P->colcoef);
     k_exact_col0<<<np, 32, 0, st>>>(X, M, N);
-    P->prof.launches[1] += 1;  // a second launch in this pass
+    P->prof.launches[1] += 3;  // four launches in this pass
     prof_end(P, st);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   } else {
@@ -550,10 +625,10 @@ cudaError_t run_exact(gfc_plan* P, const Bufs& bf, const T* in0, const T* in1, T
 cudaError_t exact_setup(gfc_plan* P, cudaStream_t s) {
   cudaError_t e = setup_dim(&P->ex_row, P->N, s);
   if (e == cudaSuccess) e = setup_dim(&P->ex_col, P->M, s);
-  // the recursive column solve's coefficients, [Nh] x 4 floats (freed with the plan)
-  if (e == cudaSuccess && !P->colcoef) e = cudaMalloc(&P->colcoef, (size_t)P->Nh * sizeof(float4));
+  // the recursive column solve's coefficients, [Nh] x 8 floats (freed with the plan)
+  if (e == cudaSuccess && !P->colcoef) e = cudaMalloc(&P->colcoef, (size_t)P->Nh * 8 * sizeof(float));
   if (e == cudaSuccess) {
-    k_exact_colcoef<<<(P->Nh + 255) / 256, 256, 0, s>>>(reinterpret_cast<float4*>(P->colcoef), P->M, P->N, P->Nh);
+    k_exact_colcoef<<<(P->Nh + 255) / 256, 256, 0, s>>>(P->colcoef, P->M, P->N, P->Nh);
     e = cudaGetLastError();
   }
   return e;
