@@ -24,6 +24,7 @@
 
 #include <vector>
 
+#include "fft_reg.cuh"
 #include "gfc_internal.h"
 
 namespace gfc {
@@ -122,6 +123,111 @@ __global__ void __launch_bounds__(kExactThreads) k_exact_cols(float2* XT, int nf
     float2* u = dft_row<+1>(z, y, d, threadIdx.x, blockDim.x);
     for (int k = threadIdx.x; k < M; k += blockDim.x) x[k] = u[k];
     __syncthreads();
+  }
+}
+
+// ---- Bluestein rows with L = 2430 = 45 x 54, in registers ---------------------
+// The same identity as dft_row on the register-resident schedule of the row
+// passes: a block takes F = 2 rows of the pair tori at a time (persistent),
+// T = 54 threads per row. Element m = t + 54 r of the chirp-multiplied row
+// (zero past n) lands in thread t's registers; a length-45 DFT, one exchange,
+// then threads j < 45 take the length-54 DFTs over r with twiddles w_L^(r j),
+// giving A[j + 45 q]. Times the chirp filter's transform (1/L folded in), the
+// spectrum goes back to shared memory in natural order, and the same two
+// stages with conjugate twiddles give the unnormalised inverse; times the
+// chirp, it replaces the row. Rows of length n with 2n - 1 <= 2430 whose
+// Bluestein length is 2430 (n = 1202 .. 1215, e.g. 1208 for a 1200-wide image)
+// take it; other lengths run the shared-memory engine.
+struct ExRegRows {
+  static constexpr int L = 2430, R1 = 45, R2 = 54, F = 2, T = R2;
+  static constexpr int R1P = R1 + 2;  // odd R1: the exchange stride R1 + 2 spreads 8-byte words over the banks
+  static constexpr int NP = (L / R1) * R1P;  // per-row exchange (also holds the spectrum in natural order)
+  static constexpr int THREADS = ((F * T + 31) / 32) * 32;
+  static_assert(R1 * R2 == L && R1 < R2 && NP >= L, "schedule");
+  static constexpr size_t smem_bytes() { return (size_t)(R1 * R2 + F * NP) * sizeof(float2); }
+};
+
+template <int DIR>
+__global__ void __launch_bounds__(ExRegRows::THREADS, 2) k_exact_rows_reg(float2* X, long long rows, int ld,
+                                                                         DimArgs d) {
+  using S = ExRegRows;
+  extern __shared__ __align__(16) float2 sm[];
+  float2* tw2 = sm;                  // [R1][R2]: w_L^(r j)
+  float2* buf = sm + S::R1 * S::R2;  // [F][NP]
+  const int tid = threadIdx.x, f = tid / S::T, t = tid - f * S::T;
+  const bool act = f < S::F, act2 = act && t < S::R1;
+  for (int i = tid; i < S::R1 * S::R2; i += blockDim.x) {
+    const int j = i / S::R2, r = i - j * S::R2;
+    tw2[i] = d.tw[r * j];
+  }
+  float2* mybuf = buf + (act ? f : 0) * S::NP;
+  const long long items = (rows + S::F - 1) / S::F;
+  __syncthreads();
+#pragma unroll 1
+  for (long long w = blockIdx.x; w < items; w += gridDim.x) {
+    const long long row = w * S::F + f;
+    const bool vr = act && row < rows;
+    float2* x = X + (vr ? row : 0) * (long long)ld;
+    float2 v[S::R1];
+#pragma unroll
+    for (int r = 0; r < S::R1; ++r) {
+      const int m = t + S::R2 * r;
+      float2 a = make_float2(0.0f, 0.0f);
+      if (vr && m < d.n) {
+        float2 xm = x[m];
+        if (DIR > 0) xm = cconj(xm);
+        a = cmul(xm, __ldg(d.chirp + m));
+      }
+      v[r] = a;
+    }
+    if (act) {
+      dft_reg<S::R1, -1>(v);
+#pragma unroll
+      for (int s2 = 0; s2 < S::R1; ++s2) mybuf[t * S::R1P + s2] = v[s2];
+    }
+    __syncthreads();
+    float2 u[S::R2];
+    if (act2) {
+      u[0] = mybuf[t];
+#pragma unroll
+      for (int r = 1; r < S::R2; ++r) u[r] = cmul(mybuf[t + S::R1P * r], tw2[t * S::R2 + r]);
+      dft_reg<S::R2, -1>(u);
+#pragma unroll
+      for (int s2 = 0; s2 < S::R2; ++s2) u[s2] = cmul(u[s2], __ldg(d.cf + t + S::R1 * s2));
+    }
+    __syncthreads();  // the exchange read: it takes the spectrum in natural order
+    if (act2) {
+#pragma unroll
+      for (int s2 = 0; s2 < S::R2; ++s2) mybuf[t + S::R1 * s2] = u[s2];
+    }
+    __syncthreads();
+    if (act) {
+#pragma unroll
+      for (int r = 0; r < S::R1; ++r) v[r] = mybuf[t + S::R2 * r];
+      dft_reg<S::R1, +1>(v);
+    }
+    __syncthreads();  // the spectrum read: the exchange again
+    if (act) {
+#pragma unroll
+      for (int s2 = 0; s2 < S::R1; ++s2) mybuf[t * S::R1P + s2] = v[s2];
+    }
+    __syncthreads();
+    if (act2) {
+      u[0] = mybuf[t];
+#pragma unroll
+      for (int r = 1; r < S::R2; ++r) u[r] = cmul(mybuf[t + S::R1P * r], cconj(tw2[t * S::R2 + r]));
+      dft_reg<S::R2, +1>(u);
+#pragma unroll
+      for (int s2 = 0; s2 < S::R2; ++s2) {
+        const int k = t + S::R1 * s2;
+        if (vr && k < d.n) {
+          float2 y = cmul(u[s2], __ldg(d.chirp + k));
+          if (DIR > 0) y = cconj(y);
+          x[k] = y;
+        }
+      }
+    }
+    __syncthreads();  // the exchange free for the next rows
   }
 }
 
@@ -573,8 +679,19 @@ cudaError_t run_exact(gfc_plan* P, const Bufs& bf, const T* in0, const T* in1, T
   if ((e = raise_smem(k_exact_rows<-1>, sr)) != cudaSuccess) return e;
   if ((e = raise_smem(k_exact_rows<+1>, sr)) != cudaSuccess) return e;
   if ((e = raise_smem(k_exact_cols, sc)) != cudaSuccess) return e;
+  // rows whose Bluestein length is the register schedule's run on it
+  const bool reg_rows = P->ex_row.L == ExRegRows::L && getenv("GFC_EXACT_GENERIC_ROWS") == nullptr;
+  const int greg = (int)(((rows + ExRegRows::F - 1) / ExRegRows::F) < 2LL * sms ? (rows + ExRegRows::F - 1) / ExRegRows::F
+                                                                                 : 2LL * sms);
+  if (reg_rows) {
+    if ((e = raise_smem(k_exact_rows_reg<-1>, ExRegRows::smem_bytes())) != cudaSuccess) return e;
+    if ((e = raise_smem(k_exact_rows_reg<+1>, ExRegRows::smem_bytes())) != cudaSuccess) return e;
+  }
   prof_begin(P, 0, st);
-  k_exact_rows<-1><<<grow, kExactThreads, sr, st>>>(X, rows, N, dr);
+  if (reg_rows)
+    k_exact_rows_reg<-1><<<greg, ExRegRows::THREADS, ExRegRows::smem_bytes(), st>>>(X, rows, N, dr);
+  else
+    k_exact_rows<-1><<<grow, kExactThreads, sr, st>>>(X, rows, N, dr);
   prof_end(P, st);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (getenv("GFC_EXACT_COLUMN_DFT") == nullptr) {
@@ -605,7 +722,10 @@ cudaError_t run_exact(gfc_plan* P, const Bufs& bf, const T* in0, const T* in1, T
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   prof_begin(P, 2, st);
-  k_exact_rows<+1><<<grow, kExactThreads, sr, st>>>(X, rows, N, dr);
+  if (reg_rows)
+    k_exact_rows_reg<+1><<<greg, ExRegRows::THREADS, ExRegRows::smem_bytes(), st>>>(X, rows, N, dr);
+  else
+    k_exact_rows<+1><<<grow, kExactThreads, sr, st>>>(X, rows, N, dr);
   prof_end(P, st);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   {

@@ -189,3 +189,33 @@ def test_exact_recursive_columns_match_column_dfts(H, W, B, monkeypatch):
         assert _rel(ox[0, 0], rx) <= bar_x and _rel(oy[0, 0], ry) <= bar_y, (_rel(ox[0, 0], rx), bar_x,
                                                                            _rel(oy[0, 0], ry), bar_y)
     p.close()
+
+
+@pytest.mark.parametrize("H,W,B", [(801, 1200, 3), (37, 1195, 2)])
+def test_exact_register_rows_match_generic_rows(H, W, B, monkeypatch):
+    """Rows whose Bluestein length is 2430 (n = 1208 and 1203 here) run on the
+    register schedule 45 x 54; the shared-memory engine on the same plan
+    (GFC_EXACT_GENERIC_ROWS) agrees within FP32 rounding for the solve, and
+    both adjoints are held to the oracle with the bar of a large FP32 adjoint."""
+    gx, gy = synth.perturbed_gradient_batch(B, H, W, seed=7600)
+    g = (gx + 0.5 * gy).astype(np.float32)
+    p = gfc.Plan(H, W, 1, B, device=DEV, exact=True)
+    assert p.N == W + 8
+    a = _np(p.solve_from_gradient(_dev(gx), _dev(gy)))
+    ax, ay = (_np(t) for t in p.backward(_dev(g)))
+    monkeypatch.setenv("GFC_EXACT_GENERIC_ROWS", "1")
+    b = _np(p.solve_from_gradient(_dev(gx), _dev(gy)))
+    bx, by = (_np(t) for t in p.backward(_dev(g)))
+    monkeypatch.delenv("GFC_EXACT_GENERIC_ROWS")
+    assert _rel(a, b) <= 5e-6, _rel(a, b)  # two FP32 evaluations of the same transforms
+    for f in range(B):
+        ref = O.solve_from_gradient(gx[f, 0].astype(np.float64), gy[f, 0].astype(np.float64), p.M, p.N, p.pad)
+        assert _rel(a[f, 0], ref) <= REL_F32 and _rel(b[f, 0], ref) <= REL_F32, (f, _rel(a[f, 0], ref),
+                                                                                 _rel(b[f, 0], ref))
+    rx, ry = O.backward(g[0, 0].astype(np.float64), p.M, p.N, p.pad)
+    tx, ty = _torch_fp32_adjoint(g[0, 0], p.M, p.N, p.pad)
+    bar_x, bar_y = max(REL_F32, 3.0 * _rel(tx, rx)), max(REL_F32, 3.0 * _rel(ty, ry))
+    for ox, oy in ((ax, ay), (bx, by)):
+        assert _rel(ox[0, 0], rx) <= bar_x and _rel(oy[0, 0], ry) <= bar_y, (_rel(ox[0, 0], rx), bar_x,
+                                                                           _rel(oy[0, 0], ry), bar_y)
+    p.close()
