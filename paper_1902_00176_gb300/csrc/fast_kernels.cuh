@@ -102,6 +102,15 @@ __device__ __forceinline__ float* tri_col0(float2* tri, int field, const FastArg
   const size_t nkb = (size_t)(A.ldY + kTriCols - 1) / kTriCols;
   return reinterpret_cast<float*>(tri_sums(tri, field, A) + nkb * 2 * A.G * kTriCols);
 }
+// s + v with its rounding error added to err (Knuth's TwoSum, explicitly
+// rounded so the compiler cannot reassociate it); returns the rounded sum
+__device__ __forceinline__ float two_sum_acc(float s, float v, float& err) {
+  const float t = __fadd_rn(s, v);
+  const float bp = __fsub_rn(t, s);
+  err = __fadd_rn(err, __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(v, bp)));
+  return t;
+}
+
 // one step of y <- x + a y with a = 1 - delta, as (x + y) - delta y: delta is
 // held to full relative precision, so the pole near DC is not rounded away
 __device__ __forceinline__ float2 tri_step(float2 x, float2 y, float delta) {
@@ -696,7 +705,7 @@ __global__ void __launch_bounds__(S::THREADS, S::MINB_FWD) k_fast_rows_fwd_div(c
   T* sgx = reinterpret_cast<T*>(buf);  // gx rows (ADJ: grad_out rows) r0 .. r0 + RW - 1
   T* sgy = sgx + (size_t)RW * A.W;     // gy rows r0 - 1 .. r0 + RW - 1
   __shared__ __align__(8) uint64_t bar;
-  __shared__ double red[ADJ ? S::F * S::T : 1];  // ADJ: per-thread sums of the item's row pairs
+  __shared__ float2 red[ADJ ? S::F * S::T : 1];  // ADJ: per-thread compensated sums (sum, error) of the row pairs
   const int tid = threadIdx.x;
   const int f = tid / S::T, t = tid - f * S::T;
   const bool act = f < S::F;
@@ -808,13 +817,13 @@ __global__ void __launch_bounds__(S::THREADS, S::MINB_FWD) k_fast_rows_fwd_div(c
     if (ADJ && act) {
       // z = Crop^T(grad_out): rows ia, ib at torus rows p + ia, p + ib, columns
       // j < W at p + j; and the row pair's sum for the (sum grad_out) e_00 term,
-      // in FP32 over chunks of 10 values, then FP64
+      // compensated in FP32 (Knuth's TwoSum: the sum and the exact rounding
+      // errors), so no FP64 work (scarce on this part) runs per value
       const int ia = g * RW + 2 * f, ib = ia + 1;
       const bool ha = ia < A.H, hb = ib < A.H;
       const T* xa = sgx + (size_t)(2 * f) * A.W;
       const T* xb = xa + A.W;
-      double acc = 0.0;
-      float chunk = 0.0f;
+      float sum = 0.0f, err = 0.0f;
 #pragma unroll
       for (int r = 0; r < S::R1; ++r) {
         const int j = t + S::R2 * r - kP;
@@ -822,13 +831,10 @@ __global__ void __launch_bounds__(S::THREADS, S::MINB_FWD) k_fast_rows_fwd_div(c
         const bool c1 = sure || (j >= 0 && j < A.W);
         const float a = (ha && c1) ? f_to_f(xa[j]) : 0.0f, b = (hb && c1) ? f_to_f(xb[j]) : 0.0f;
         v[r] = make_float2(a, b);
-        chunk += a + b;
-        if (r % 10 == 9 || r == S::R1 - 1) {
-          acc += (double)chunk;
-          chunk = 0.0f;
-        }
+        sum = two_sum_acc(sum, a, err);
+        sum = two_sum_acc(sum, b, err);
       }
-      red[tid] = acc;
+      red[tid] = make_float2(sum, err);
     } else if (act) {
       const int r0 = g * RW, ia = r0 + 2 * f, ib = ia + 1;
       const bool ha = ia < A.H, hb = ib < A.H, hm = ia >= 1;  // rows present (ia - 1 < H always)
@@ -856,10 +862,14 @@ __global__ void __launch_bounds__(S::THREADS, S::MINB_FWD) k_fast_rows_fwd_div(c
     }
     __syncthreads();  // every staged row read: the buffers become the exchange buffers
     if (ADJ && act && t == 0) {
-      // the row pair's FP64 sum, threads in order
-      double sp = 0.0;
-      for (int k = 0; k < S::T; ++k) sp += red[f * S::T + k];
-      reinterpret_cast<double*>(partial)[(size_t)field * (kMaxRowBlocks / 2) + g * S::F + f] = sp;
+      // the row pair's sum over its threads in order (compensated), stored in FP64
+      float sp = 0.0f, ep = 0.0f;
+      for (int k = 0; k < S::T; ++k) {
+        const float2 e = red[f * S::T + k];
+        sp = two_sum_acc(sp, e.x, ep);
+        ep = __fadd_rn(ep, e.y);
+      }
+      reinterpret_cast<double*>(partial)[(size_t)field * (kMaxRowBlocks / 2) + g * S::F + f] = (double)sp + (double)ep;
     }
     if (act) {
       dft_reg<S::R1, -1>(v);
