@@ -508,6 +508,17 @@ def oracle_errors(samples):
     return res
 
 
+def _launches_per_call(plan, fn):
+    """Kernel launches one call makes (the library's profiling hook counts them;
+    a small torus whose launch fits the GPU at once runs as one fused kernel)."""
+    plan.profile(reset=True)
+    plan.set_profiling(True)
+    fn()
+    pr = plan.profile(reset=True)
+    plan.set_profiling(False)
+    return int(sum(pr["launches"]))
+
+
 def extra_workloads(dev, samples):
     """The other workload shapes of the method, each timed on this GPU (inputs resident);
     a few fields of each are recorded in ``samples`` for the oracle-error leg."""
@@ -526,7 +537,8 @@ def extra_workloads(dev, samples):
     g = gfc.Graph(p, "gradient", tx, ty, out)
     msg = _time_ms(g.launch, dev, 200)
     res["single_64x96_fp32"] = {"ms_per_solve": ms, "ms_per_solve_graph": msg, "solves_per_s": 1000.0 / ms,
-                                "solves_per_s_graph": 1000.0 / msg}
+                                "solves_per_s_graph": 1000.0 / msg, "launches_per_solve": _launches_per_call(
+                                    p, lambda: p.solve_from_gradient(tx, ty, out))}
     _sample(samples, "single_64x96_fp32", "grad", _h(out[0, 0]), p.M, p.N, gx=_h(tx[0, 0]), gy=_h(ty[0, 0]))
     g.close()
     p.close()
@@ -540,7 +552,8 @@ def extra_workloads(dev, samples):
     g = gfc.Graph(p, "gradient", tx, ty, out)
     msg = _time_ms(g.launch, dev, 100)
     res["single_801x1200_fp32"] = {"ms_per_solve": ms, "ms_per_solve_graph": msg, "solves_per_s": 1000.0 / ms,
-                                   "solves_per_s_graph": 1000.0 / msg}
+                                   "solves_per_s_graph": 1000.0 / msg, "launches_per_solve": _launches_per_call(
+                                       p, lambda: p.solve_from_gradient(tx, ty, out))}
     _sample(samples, "single_801x1200_fp32", "grad", _h(out[0, 0]), p.M, p.N, gx=_h(tx[0, 0]), gy=_h(ty[0, 0]))
     g.close()
     p.close()
