@@ -67,9 +67,10 @@ typedef enum {
  * 7-smooth size >= W + 2p. Either way the torus is at least Algorithm A's
  * padded size and the extra zero rows and columns go to the bottom and right:
  * the same least-squares problem on a slightly larger torus. GFC_SIZE_EXACT: Algorithm A's own size,
- * M = H + 2p, N = W + 2p, whatever their prime factors (Bluestein's chirp-z
- * for lengths that are not 7-smooth); H + 2p and W + 2p <= 2048, uniform plans;
- * solves, edited solves and the adjoint (gfc_backward) on that torus. */
+ * M = H + 2p, N = W + 2p, whatever their prime factors: row DFTs by
+ * Bluestein's chirp-z for lengths that are not 7-smooth, the column direction
+ * by the recursive column solve (any M); H + 2p and W + 2p <= 2048, uniform
+ * plans; solves, edited solves and the adjoint (gfc_backward) on that torus. */
 typedef enum { GFC_SIZE_SMOOTH = 0, GFC_SIZE_EXACT = 1 } gfc_size_policy;
 
 /* How the column direction of Eq. 23's Green multiply is applied on the
@@ -206,8 +207,10 @@ gfc_status gfc_fft_c2c(int n, int count, int dir, const void* in, void* out, voi
 gfc_status gfc_solve_from_gradient_host(gfc_plan* plan, const void* gx, const void* gy, void* out);
 
 /* Per-pass device time and launch counts, for tracing. pass index 0 = row
- * pass (divergence + row transforms), 1 = column pass (column transforms and
- * Green multiply), 2 = inverse row pass (offset, crop, cast), 3 = other. */
+ * pass (divergence + row transforms; a one-launch solve of a small torus
+ * counts here alone), 1 = column direction (the carry sweep of the recursive
+ * column solve, or the column transforms and Green multiply), 2 = inverse row
+ * pass (offset, crop, cast), 3 = other. */
 typedef struct {
   double pass_ms[4];  /* device time summed over launches (only while profiling is on) */
   long launches[4];   /* kernel launches issued (always counted) */
