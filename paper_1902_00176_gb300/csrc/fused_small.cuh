@@ -13,8 +13,9 @@
 // fold, in the same order, in every CTA of the cluster) to get the carries into
 // and below its own bands and u[0,0]; warp 0 solves column 0 exactly in FP64.
 // gx and gy are read once and out written once: the minimum bytes of the path.
-// Used where a field's spectrum fits the shared memory of a cluster of at most
-// eight CTAs (short rows: 270 x 270, 72 x 108 and the like).
+// It applies where a field's spectrum fits the shared memory of a cluster of
+// at most eight CTAs (short rows); by default it is taken for latency-bound
+// launches of tori of at most 8 bands (one band per CTA: 72 x 108 and the like).
 #pragma once
 
 #include <cooperative_groups.h>
@@ -405,12 +406,14 @@ static int fused_small_cluster(const gfc_plan* P, int nf, int sms, int* gc_out, 
   *gc_out = (G + cl - 1) / cl;
   *smem_out = L::bytes(P->W, *gc_out, srows, P->M);
   // Each CTA runs its bands one after another with the field's spectrum held
-  // in shared memory (two CTAs per SM at most), so the fused solve wins where
-  // the launch is latency-bound: all its CTAs resident at once. Larger batches
-  // run the three persistent launches, which keep more warps per SM busy.
-  // GFC_FUSED_SMALL=1 takes the fused solve whenever it applies.
+  // in shared memory (two CTAs per SM at most). Measured against the three
+  // persistent launches, the fused solve wins only where every CTA holds a
+  // single band (at most 8 bands: 72 x 108, 16.5 against 24 us for one field)
+  // and the launch is latency-bound (its CTAs take at most 7/8 of the GPU's
+  // slots); with 2 to 4 bands per CTA it loses (270 x 270: 41 against 32 us).
+  // GFC_FUSED_SMALL=1 takes the fused solve wherever it applies.
   const int per_sm = *smem_out <= kFusedSmemTwoPerSM ? 2 : 1;
-  if ((long)nf * cl > (long)per_sm * sms && getenv("GFC_FUSED_SMALL") == nullptr) return 0;
+  if ((*gc_out > 1 || (long)nf * cl * 8 > (long)per_sm * sms * 7) && getenv("GFC_FUSED_SMALL") == nullptr) return 0;
   return cl;
 }
 

@@ -112,16 +112,19 @@ def test_fused_small_chunked_streams_and_layer_shape(monkeypatch):
 
 
 def test_fused_small_taken_for_latency_bound_launches_only():
-    """One 64 x 96 field runs as one launch; the layer's 2048 fields of 256 x 256
-    (more CTAs than fit the GPU at once) run the three persistent launches."""
-    gx, gy = synth.perturbed_gradient_batch(batch=1, H=64, W=96, seed=12900)
-    p = gfc.Plan(64, 96, 1, 1, device=DEV)
-    _, launches = _launches(p, lambda: p.solve_from_gradient(torch.from_numpy(gx).to(DEV),
-                                                            torch.from_numpy(gy).to(DEV)))
-    assert sum(launches) == 1, launches
-    p.close()
-    x = torch.zeros((32, 64, 256, 256), device=DEV, dtype=torch.bfloat16)
-    q = gfc.Plan(256, 256, 64, 32, dtype=torch.bfloat16, device=DEV)
-    _, launches = _launches(q, lambda: q.solve_from_gradient(x, x))
-    assert sum(launches) >= 3, launches
-    q.close()
+    """The default takes the fused solve where each CTA of a field's cluster holds
+    one band (tori of at most 8 bands) and the launch is latency-bound: one and
+    64 fields of 64 x 96 (72 x 108 torus, 4 bands) run as one launch; 76 fields
+    (every CTA slot of the GPU) and a 270 x 270 torus (19 bands, 3 per CTA)
+    run the three launches, which measured faster there."""
+    def launches(H, W, B, dt=torch.float32):
+        x = torch.zeros((B, 1, H, W), device=DEV, dtype=dt)
+        p = gfc.Plan(H, W, 1, B, dtype=dt, device=DEV)
+        _, n = _launches(p, lambda: p.solve_from_gradient(x, x))
+        p.close()
+        return sum(n)
+    assert launches(64, 96, 1) == 1
+    assert launches(64, 96, 64) == 1
+    assert launches(64, 96, 76) >= 3
+    assert launches(256, 256, 1, torch.bfloat16) >= 3
+    assert launches(256, 256, 2048, torch.bfloat16) >= 3
