@@ -422,12 +422,19 @@ static int fused_small_cluster(const gfc_plan* P, int nf, int sms, int* gc_out, 
 // three-step path) or when GFC_UNFUSED_SMALL is set.
 template <class RS, typename T>
 static cudaError_t run_fused_small(gfc_plan* P, const T* gx, const T* gy, T* out, int nf, cudaStream_t st) {
-  if (getenv("GFC_UNFUSED_SMALL") != nullptr || !P->tri || P->pad != kP) return cudaErrorNotSupported;
+  if (!P->tri || P->pad != kP || getenv("GFC_UNFUSED_SMALL") != nullptr) return cudaErrorNotSupported;
+  // by default only tori of at most 8 bands qualify (one band per CTA, see
+  // fused_small_cluster): most plans stop here, before any runtime call
+  if (P->triG > kFusedMaxCluster && getenv("GFC_FUSED_SMALL") == nullptr) return cudaErrorNotSupported;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  int sms = 0;
-  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  static int sms_of[64] = {};  // SM count per device, read once (relaxed atomics: every writer stores the same value)
+  int sms = dev < 64 ? __atomic_load_n(&sms_of[dev], __ATOMIC_RELAXED) : 0;
+  if (sms == 0) {
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if (dev < 64) __atomic_store_n(&sms_of[dev], sms, __ATOMIC_RELAXED);
+  }
   int gc = 0;
   size_t smem = 0;
   const int cl = fused_small_cluster<RS, T>(P, nf, sms, &gc, &smem);
